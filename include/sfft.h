@@ -1,0 +1,198 @@
+/*
+ * sfft.h -- C ABI of the B300 TT-SFFT Carr-Madan pricer.
+ *
+ * Prices European calls on a log-strike grid of M = 2^n points with the
+ * Carr-Madan discrete Fourier transform (Sec. 2.1 of Hauck & Turkalj,
+ * "Classical Tensor Train and Quantum Fourier Transform Approaches for
+ * Large-Scale Carr-Madan Option Pricing"), evaluated as the tensor-train
+ * Superfast Fourier Transform of Sec. 4: the integrand x_j (Eq. x, or its
+ * Simpson-weighted variant) is held as a quantics tensor train of n binary
+ * cores, the bit-reversed Fourier operator Q_n (Sec. 4.2) is applied as a
+ * matrix-product operator, the result is rounded by QR/SVD sweeps, and prices
+ * are read out in bit-reversed site order (Sec. 4.3, Eq. discretization_dft).
+ * No length-M vector is formed on that path. A dense-FFT Carr-Madan baseline
+ * (Sec. 5.1's FFT route) is exposed with the same calling convention.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns sfft_status; nothing throws across the ABI.
+ *   - Pointers marked "device" are CUDA device pointers of the context's
+ *     device (for example torch.cuda tensors' data_ptr()); pointers marked
+ *     "host" are ordinary host memory. The caller owns every buffer it passes.
+ *   - Device work is stream-ordered on the stream set with sfft_set_stream
+ *     (default: the legacy default stream). Calls that return per-instance
+ *     status synchronise that stream before returning.
+ *   - Invalid arguments are rejected on the host before any launch
+ *     (SFFT_EINVAL); the text of the last error is sfft_last_error(ctx).
+ *   - A context is used by one host thread at a time.
+ *   - Complex numbers are stored as interleaved double pairs (re, im).
+ *   - A tensor train (TT) crossing the ABI is "packed": core l (1-based) of
+ *     shape (r_{l-1}, d, r_l) is stored row-major (last index fastest) at
+ *     complex offset sum_{i<l} r_{i-1} d r_i; ranks[0] = ranks[n] = 1.
+ *     Site 1 carries the most significant bit of the grid index, as in
+ *     Eq. discretized_x: j = sum_l lambda_l 2^(n-l).
+ *   - An MPO crossing the ABI is a packed TT with d = 4 whose physical index
+ *     is 2*mu + lambda (mu = output bit, lambda = input bit of Eq. tto_format).
+ */
+#ifndef SFFT_H
+#define SFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SFFT_OK = 0,
+  SFFT_EINVAL = 1,   /* invalid argument (shape, range, NaN, unsupported mode) */
+  SFFT_EMOMENT = 2,  /* E[S_T^(alpha+1)] is infinite: Eq. damping_moment_condition fails */
+  SFFT_ENOMEM = 3,   /* device or host allocation failed */
+  SFFT_ECUDA = 4,    /* a CUDA runtime call failed (text in sfft_last_error) */
+  SFFT_ERANK = 5,    /* a TT or MPO rank would exceed the cap */
+  SFFT_ENOCONV = 6,  /* integrand builder did not reach the tolerance */
+  SFFT_ETIMEOUT = 7  /* a bounded device-side wait expired */
+} sfft_status;
+
+/* Characteristic-function models of log(S_T/S0). Sec. 2 gives Black-Scholes
+ * and names Heston, Merton and Variance-Gamma; parameter slots p[]:
+ *   SFFT_GBM    p = {sigma}
+ *   SFFT_HESTON p = {kappa, theta, sigma_v, rho, v0}  (Heston 1993, "little
+ *                   trap" form of Albrecher et al. 2007)
+ *   SFFT_MERTON p = {sigma, lambda, mu_J, delta_J}     (Merton 1976)
+ *   SFFT_VG     p = {sigma, nu, theta}                 (Madan-Carr-Chang 1998) */
+typedef enum { SFFT_GBM = 0, SFFT_HESTON = 1, SFFT_MERTON = 2, SFFT_VG = 3 } sfft_model;
+
+/* Quadrature of the Fourier integral (Eq. C_k_integral):
+ *   SFFT_QUAD_SIMPSON_CM99: v_j = eta j, Simpson weights (1/3, 4/3, 2/3, ...),
+ *     strikes k'_u = -pi/eta + 2 pi u/(M eta) -- the "higher-order quadrature
+ *     weights incorporated into x_j" that the paper allows after
+ *     Eq. discretization_dft.
+ *   SFFT_QUAD_RECT_SYM: the paper's symmetric rectangle rule, Eqs.
+ *     Ck_from_psi, x, discretization_dft; Delta_v = eta, or pi/sqrt(N) when
+ *     eta <= 0 (the grid of Sec. 5), Delta_k = pi/(N Delta_v),
+ *     k'_0 = -N Delta_k/2. */
+typedef enum { SFFT_QUAD_SIMPSON_CM99 = 0, SFFT_QUAD_RECT_SYM = 1 } sfft_quad;
+
+typedef struct {
+  int32_t model;    /* sfft_model */
+  int32_t quad;     /* sfft_quad */
+  int32_t n;        /* grid exponent, M = 2^n, 1 <= n <= SFFT_MAX_N */
+  int32_t max_rank; /* cap on TT ranks; 0 -> SFFT_DEFAULT_MAX_RANK */
+  double p[8];      /* model parameters, see sfft_model */
+  double S0;        /* spot, > 0 */
+  double r;         /* risk-free rate */
+  double T;         /* maturity, > 0 */
+  double alpha;     /* damping of Eq. damping_moment_condition; alpha < -1 prices puts */
+  double eta;       /* frequency step (see sfft_quad) */
+  double tol;       /* relative Frobenius truncation tolerance of the TT steps */
+  double k0;        /* must be NaN (default grid start); reserved */
+} sfft_problem;
+
+/* Per-instance diagnostics. */
+typedef struct {
+  int32_t status;    /* sfft_status of this instance */
+  int32_t int_rank;  /* max rank of the integrand TT */
+  int32_t mpo_rank;  /* max rank of the Q_n MPO */
+  int32_t out_rank;  /* max rank of the rounded output TT */
+  int64_t tt_bytes;  /* bytes of the output TT cores (complex128) */
+} sfft_info;
+
+#define SFFT_MAX_N 48
+#define SFFT_DEFAULT_MAX_RANK 32
+#define SFFT_MAX_RANK 32
+#define SFFT_MAX_MPO_RANK 32
+#define SFFT_MAX_STRIKES 65536
+
+typedef struct sfft_ctx sfft_ctx;
+
+/* Create a context on CUDA device `device` (owns the MPO cache and device
+ * workspaces). Returns SFFT_ECUDA if the device cannot be used. */
+sfft_status sfft_create(sfft_ctx **ctx, int device);
+
+/* Release the context and all device memory it owns (host call; synchronises
+ * the context's stream first). NULL is accepted. */
+sfft_status sfft_destroy(sfft_ctx *ctx);
+
+/* Make all later device work of this context run on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream). */
+sfft_status sfft_set_stream(sfft_ctx *ctx, void *cuda_stream);
+
+/* Strike selection helper (host only, no device work). For grid indices
+ * u in [0, M) with log-moneyness k'_u in [lo_logm, hi_logm], returns the
+ * first index l_begin, a power-of-two stride and the count q <= qmax of the
+ * set {l_begin + i*stride}; l_begin is a multiple of stride. */
+sfft_status sfft_strike_window(const sfft_problem *prob, double lo_logm,
+                               double hi_logm, int32_t qmax, int64_t *l_begin,
+                               int64_t *stride, int32_t *q);
+
+/* Price `count` instances with the TT-SFFT path (Sec. 4.3).
+ *   probs[count]              host  problem statements
+ *   l_begin, stride, q        host  per-instance strike sets on the 2^n grid:
+ *                                   u = l_begin + i*stride, i < q; stride a
+ *                                   power of two, l_begin a multiple of it,
+ *                                   u < 2^n, q <= SFFT_MAX_STRIKES
+ *   prices, log_strikes       device, sum(q) doubles each, instance i's
+ *                                   outputs start at sum_{k<i} q[k]; prices in
+ *                                   currency units, log_strikes = log K
+ *   inst_status[count]        host  per-instance sfft_status (may be NULL)
+ *   info[count]               host  per-instance diagnostics (may be NULL)
+ * A failing instance does not stop the batch: its prices are NaN and its
+ * status says why; the call then returns the first such status. The MPO of
+ * each distinct (n, tol) is built once and cached in the context. */
+sfft_status sfft_price_batch(sfft_ctx *ctx, const sfft_problem *probs, int32_t count,
+                             const int64_t *l_begin, const int64_t *stride,
+                             const int32_t *q, double *prices, double *log_strikes,
+                             int32_t *inst_status, sfft_info *info);
+
+/* Same contract, dense-FFT Carr-Madan baseline: samples all M = 2^n integrand
+ * values, runs an M-point FFT in device memory and gathers the requested
+ * strikes. n <= SFFT_DENSE_MAX_N; needs 32*M bytes of device workspace. */
+#define SFFT_DENSE_MAX_N 32
+sfft_status sfft_dense_price_batch(sfft_ctx *ctx, const sfft_problem *probs, int32_t count,
+                                   const int64_t *l_begin, const int64_t *stride,
+                                   const int32_t *q, double *prices, double *log_strikes,
+                                   int32_t *inst_status, sfft_info *info);
+
+/* ---- lower-level entry points (one pipeline step each; used by tests) ---- */
+
+/* Integrand samples x_j (Eq. x or the Simpson variant) at `count` grid
+ * indices j (device int64) into x (device, count complex). */
+sfft_status sfft_sample_integrand(sfft_ctx *ctx, const sfft_problem *prob,
+                                  const int64_t *j, int64_t count, double *x);
+
+/* Integrand TT of one problem (Sec. 4.1/4.3: TT-SVD of the sampled support
+ * block). ranks (host, n+1) receives the ranks, cores (device) the packed
+ * cores; cap = capacity of `cores` in complex elements. */
+sfft_status sfft_integrand_tt(sfft_ctx *ctx, const sfft_problem *prob, int32_t *ranks,
+                              double *cores, int64_t cap);
+
+/* The MPO of Q_n (Sec. 4.2) compressed to relative Frobenius tolerance tol,
+ * copied packed (d = 4) into cores (device, capacity cap complex); ranks
+ * (host, n+1). */
+sfft_status sfft_mpo(sfft_ctx *ctx, int32_t n, double tol, int32_t *ranks, double *cores,
+                     int64_t cap);
+
+/* TT rounding (Oseledets' QR + truncated-SVD sweeps) of a packed TT with
+ * physical dimension d in {2, 4}: in_ranks/in_cores in, out_ranks (host)
+ * and out_cores (device, capacity cap) out. */
+sfft_status sfft_tt_round(sfft_ctx *ctx, int32_t n, int32_t d, const int32_t *in_ranks,
+                          const double *in_cores, double tol, int32_t max_rank,
+                          int32_t *out_ranks, double *out_cores, int64_t cap);
+
+/* y = Q_n x for a packed TT x (d = 2): zip-up MPO x TT contraction followed
+ * by the rounding sweep at tolerance tol. Output TT in bit-reversed site
+ * order: site l carries bit l-1 of the output index u. */
+sfft_status sfft_tt_apply_qft(sfft_ctx *ctx, int32_t n, const int32_t *in_ranks,
+                              const double *in_cores, double tol, int32_t max_rank,
+                              int32_t *out_ranks, double *out_cores, int64_t cap);
+
+/* Static strings; never NULL. */
+const char *sfft_status_string(sfft_status s);
+const char *sfft_last_error(const sfft_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFFT_H */

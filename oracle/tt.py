@@ -159,3 +159,12 @@ def rank1_exp_tt(gamma, n):
         G[0, 1, 0] = np.exp(gamma * 2.0 ** (-l))
         cores.append(G)
     return cores
+
+
+def tt_entry(cores, bits):
+    """One entry of a TT: the product of the core slices selected by the
+    physical indices `bits` (site 1 first)."""
+    v = np.ones((1,), dtype=np.complex128)
+    for G, b in zip(cores, bits):
+        v = v @ np.asarray(G)[:, int(b), :]
+    return complex(v[0])

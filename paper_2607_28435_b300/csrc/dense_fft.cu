@@ -1,0 +1,92 @@
+// Dense-FFT Carr-Madan baseline (the FFT route of Sec. 5.1): every integrand
+// value x_j, j < M = 2^n, is sampled into device memory, an in-place M-point
+// FFT runs as a sequence of radix-2^R decimation-in-frequency passes, and the
+// requested strikes are gathered and priced (Eq. discretization_dft).
+//
+// Pass with sub-transform length L = 2^R * Lp: for every sub-transform b and
+// offset s < Lp the 2^R elements x[bL + s + r Lp] are transformed,
+// X_k = sum_r x_r exp(-2 pi i r k / 2^R), twiddled by exp(-2 pi i s k / L) and
+// stored back at bL + s + k Lp. After all passes the output of frequency u sits
+// at the digit-reversed position sum_p k_p Lp_p, k_p the p-th digit of u
+// (least significant first).
+#include "kernels.cuh"
+
+__global__ void k_dense_sample(InstParams prm, cd* __restrict__ x, long long M) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < M;
+       j += (long long)gridDim.x * blockDim.x)
+    x[j] = integrand(prm, j);
+}
+
+__device__ __forceinline__ cd unit_root(long long t, long long L) {
+  // exp(-2 pi i t / L) with the argument formed exactly (L a power of two)
+  double sn, cs;
+  sincospi(2.0 * (double)t / (double)L, &sn, &cs);
+  return mkc(cs, -sn);
+}
+
+__global__ void k_fft_pass(cd* __restrict__ x, long long M, long long Lp, int R, int cols) {
+  extern __shared__ double4 smem_raw[];
+  cd* sm = reinterpret_cast<cd*>(smem_raw);
+  const int Rn = 1 << R;
+  cd* tw = sm + (size_t)Rn * cols;
+  for (int i = threadIdx.x; i < Rn; i += blockDim.x) tw[i] = unit_root(i, Rn);
+  const long long L = Lp * Rn;
+  const long long per_sub = Lp / cols;
+  const long long nblk = (M / L) * per_sub;
+  for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const long long b = blk / per_sub;
+    const long long s0 = (blk - b * per_sub) * cols;
+    const long long base = b * L + s0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < Rn * cols; e += blockDim.x) {
+      const int r = e / cols, c = e - r * cols;
+      sm[e] = x[base + (long long)r * Lp + c];
+    }
+    __syncthreads();
+    for (int span = Rn; span >= 2; span >>= 1) {
+      const int half = span >> 1;
+      const int stride_tw = Rn / span;
+      for (int bf = threadIdx.x; bf < (Rn >> 1) * cols; bf += blockDim.x) {
+        const int c = bf % cols, j = bf / cols;
+        const int g = j / half, i = j - g * half;
+        const int r0 = g * span + i, r1 = r0 + half;
+        const cd a = sm[r0 * cols + c], bb = sm[r1 * cols + c];
+        sm[r0 * cols + c] = cadd(a, bb);
+        sm[r1 * cols + c] = cmul(csub(a, bb), tw[i * stride_tw]);
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < Rn * cols; e += blockDim.x) {
+      const int k = e / cols, c = e - k * cols;
+      const int kr = (int)(__brev((unsigned)k) >> (32 - R));
+      const cd v = sm[kr * cols + c];
+      const long long s = s0 + c;
+      const long long t = (s * k) & (L - 1);
+      x[base + (long long)k * Lp + c] = (t == 0) ? v : cmul(v, unit_root(t, L));
+    }
+  }
+}
+
+__global__ void k_dense_gather(InstParams prm, const cd* __restrict__ y, int n,
+                               const int* __restrict__ digits, int ndig, long long l_begin,
+                               int tbits, int q, double* __restrict__ prices,
+                               double* __restrict__ logk) {
+  const double inv_sqM = 1.0 / (ldexp(1.0, n / 2) * ((n & 1) ? 1.4142135623730951 : 1.0));
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < q; i += gridDim.x * blockDim.x) {
+    const long long u = l_begin + ((long long)i << tbits);
+    long long pos = 0, rem = u;
+    int used = 0;
+    for (int p = 0; p < ndig; ++p) {
+      const int R = digits[p];
+      used += R;
+      const long long k = rem & ((1LL << R) - 1);
+      rem >>= R;
+      pos += k << (n - used);
+    }
+    const cd v = y[pos];
+    double sgn;
+    const double f = price_factor(prm, u, &sgn);
+    prices[i] = prm.S0 * f * sgn * v.x * inv_sqM;
+    logk[i] = log(prm.S0) + prm.k0 + prm.dk * (double)u;
+  }
+}

@@ -1,0 +1,54 @@
+// Kernel declarations and device-side limits shared by the SFFT kernels and
+// the host runtime.
+#pragma once
+#include "cplx.cuh"
+#include "la.cuh"
+#include "model.cuh"
+
+#define SFFT_MAXN_DEV 48
+#define SFFT_SLOT_RANK_DEV 32                 // rank capacity of a core slot
+#define SFFT_CORE_STRIDE_D2 (SFFT_SLOT_RANK_DEV * 2 * SFFT_SLOT_RANK_DEV)
+#define SFFT_CORE_STRIDE_D4 (SFFT_SLOT_RANK_DEV * 4 * SFFT_SLOT_RANK_DEV)
+// zip-up scratch: carry (q x k), D (r' s 2 r) and the panel Z (s r x 2 r')
+#define SFFT_ZIP_CH_DEV (SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV)
+#define SFFT_ZIP_D_DEV (2 * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV)
+#define SFFT_ZIP_Z_DEV (2 * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV)
+#define SFFT_ZIP_SCRATCH (SFFT_ZIP_CH_DEV + SFFT_ZIP_D_DEV + SFFT_ZIP_Z_DEV)
+#define SFFT_ROUND_SCRATCH (5 * SFFT_CORE_STRIDE_D4)
+#define READOUT_TREE_BITS 5                   // low bits expanded as a tree in the readout
+#define SFFT_READOUT_SCRATCH (2 * 2112 * SFFT_SLOT_RANK_DEV)
+#define SFFT_MPO_NODES 24                     // Chebyshev nodes of the MPO construction
+
+// status codes (same values as sfft_status)
+#define SFFT_EINVAL_DEV 1
+#define SFFT_ERANK_DEV 5
+#define SFFT_ENOCONV_DEV 6
+
+__global__ void k_sample(const InstParams* P, const long long* j, long long count, cd* x);
+__global__ void k_support_probe(const InstParams* P, int count, double probe_tol, int m_min,
+                                int* m_out);
+__global__ void k_integrand_ttsvd(const InstParams* P, const int* m_arr, int count, cd* scratch,
+                                  long long scratch_stride, cd* tt, const long long* tt_off,
+                                  int core_stride, int* ranks_all, int* status, int hb);
+__global__ void k_mpo_interp(int n, int P, cd* W, int core_stride, int* ranks);
+__global__ void k_tt_round(int count, const int* n_arr, int d, int left_orth, const double* tol_arr,
+                           const int* maxrank_arr, cd* tt, const long long* tt_off,
+                           int core_stride, int* ranks_all, cd* scratch,
+                           long long scratch_stride, int* status, int hb);
+__global__ void k_zipup(int count, const int* n_arr, const double* tol_arr, const int* maxrank_arr,
+                        const cd* A, const long long* a_off, const int* a_ranks_all,
+                        const cd* Wmpo, const long long* w_off, const int* w_ranks_all, cd* B,
+                        const long long* b_off, int* b_ranks_all, int core_stride_a,
+                        int core_stride_w, int core_stride_b, cd* scratch,
+                        long long scratch_stride, int* status, int hb);
+__global__ void k_readout(int count, const InstParams* P, const cd* B, const long long* b_off,
+                          const int* b_ranks_all, int core_stride, const long long* l_begin,
+                          const int* tbits, const int* qarr, const long long* out_off,
+                          double* prices, double* logk, const int* status, cd* scratch,
+                          long long scratch_stride);
+
+// dense-FFT baseline
+__global__ void k_dense_sample(InstParams prm, cd* x, long long M);
+__global__ void k_fft_pass(cd* x, long long M, long long Lp, int R, int cols_per_block);
+__global__ void k_dense_gather(InstParams prm, const cd* y, int n, const int* digits, int ndig,
+                               long long l_begin, int tbits, int q, double* prices, double* logk);

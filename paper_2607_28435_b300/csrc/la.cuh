@@ -1,0 +1,250 @@
+// CTA-cooperative dense linear algebra on small complex FP64 matrices, the
+// building blocks of every TT step (TT-SVD, zip-up MPO x TT contraction,
+// rounding): Householder QR (LAPACK zlarfg convention), one-sided Jacobi SVD
+// (Hestenes' method), and the "tall-skinny SVD" that combines them.
+//
+// Every function here must be called by all threads of the block; matrices
+// passed as "smem" live in shared memory, column-major with a leading
+// dimension; "Z" inputs are row-major with leading dimension p and may live in
+// global memory (they are read only).
+#pragma once
+#include "cplx.cuh"
+
+#define LA_MAXP 64  // most columns a tall-skinny factorisation handles
+
+namespace la {
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+__device__ __forceinline__ int n_warps() { return blockDim.x >> 5; }
+
+// Householder QR in place. W: h x p, column-major (leading dim ld). On return
+// the upper triangle of the leading min(h,p) rows holds R (W = Q R); the
+// strictly lower part holds the reflectors v (v_0 = 1 implicit) and must not
+// be read as R. Reflector k: H_k = I - tau_k v v^H with
+// H_k^H (a0; x) = (beta; 0), beta real (LAPACK zlarfg); Q = H_0 H_1 ... .
+// taus[k] (smem, min(h,p) entries) receives tau_k.
+static __device__ void qr_inplace(cd* W, int ld, int h, int p, cd* taus) {
+  const int lane = lane_id(), warp = warp_id(), nw = n_warps();
+  const int kmax = min(h, p);
+  for (int k = 0; k < kmax; ++k) {
+    cd* col = W + (size_t)k * ld;
+    if (warp == 0) {
+      double s = 0.0;
+      for (int i = k + 1 + lane; i < h; i += 32) s += cabs2(col[i]);
+      s = warp_sum(s);
+      const cd a0 = col[k];
+      __syncwarp();  // every lane has read the pivot before lane 0 rewrites it
+      cd tau = mkc(0.0, 0.0);
+      if (!(s == 0.0 && a0.y == 0.0)) {
+        const double beta = -copysign(sqrt(a0.x * a0.x + a0.y * a0.y + s), a0.x);
+        tau = mkc((beta - a0.x) / beta, -a0.y / beta);
+        const cd scal = cdiv(mkc(1.0, 0.0), mkc(a0.x - beta, a0.y));
+        for (int i = k + 1 + lane; i < h; i += 32) col[i] = cmul(col[i], scal);
+        if (lane == 0) col[k] = mkc(beta, 0.0);
+      }
+      if (lane == 0) taus[k] = tau;
+    }
+    __syncthreads();
+    const cd tau = taus[k];
+    if (tau.x != 0.0 || tau.y != 0.0) {
+      const cd ctau = cconj(tau);
+      for (int j = k + 1 + warp; j < p; j += nw) {
+        cd* cj = W + (size_t)j * ld;
+        cd dot = (lane == 0) ? cj[k] : mkc(0.0, 0.0);
+        for (int i = k + 1 + lane; i < h; i += 32) dot = cfmac(col[i], cj[i], dot);
+        dot = warp_csum(dot);
+        const cd f = cmul(ctau, dot);
+        if (lane == 0) cj[k] = csub(cj[k], f);
+        for (int i = k + 1 + lane; i < h; i += 32) cj[i] = csub(cj[i], cmul(col[i], f));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Explicit Q (h x kq, column-major, leading dim ldq; any address space) of a
+// factorisation left by qr_inplace: Q = H_0 ... H_{kq-1} [I; 0], built by
+// applying the reflectors in reverse order to the identity columns.
+static __device__ void form_q(const cd* W, int ld, int h, int kq, const cd* taus, cd* Q, int ldq) {
+  const int lane = lane_id(), warp = warp_id(), nw = n_warps();
+  for (int idx = threadIdx.x; idx < h * kq; idx += blockDim.x) {
+    const int j = idx / h, i = idx - j * h;
+    Q[(size_t)j * ldq + i] = mkc(i == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int k = kq - 1; k >= 0; --k) {
+    const cd tau = taus[k];
+    if (tau.x != 0.0 || tau.y != 0.0) {
+      const cd* v = W + (size_t)k * ld;
+      for (int j = k + warp; j < kq; j += nw) {
+        cd* qj = Q + (size_t)j * ldq;
+        cd dot = (lane == 0) ? qj[k] : mkc(0.0, 0.0);
+        for (int i = k + 1 + lane; i < h; i += 32) dot = cfmac(v[i], qj[i], dot);
+        dot = warp_csum(dot);
+        const cd f = cmul(tau, dot);
+        __syncwarp();
+        if (lane == 0) qj[k] = csub(qj[k], f);
+        for (int i = k + 1 + lane; i < h; i += 32) qj[i] = csub(qj[i], cmul(v[i], f));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One-sided Jacobi (Hestenes): rotates the m columns of L (p rows, column
+// major, leading dim ld) until every pair is orthogonal to working precision,
+// |l_a^H l_b| <= tol * ||l_a|| ||l_b||. Columns are visited in round-robin
+// tournament order, one pair per warp. Returns the number of sweeps used, or
+// -1 if max_sweeps did not reach convergence.
+static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int* sh_flag) {
+  const int lane = lane_id(), warp = warp_id(), nw = n_warps();
+  if (m < 2) return 0;
+  const int mp = m + (m & 1);
+  const double tol = 2.3e-16 * (double)max(p, 8);
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) *sh_flag = 0;
+    __syncthreads();
+    for (int t = 0; t < mp - 1; ++t) {
+      for (int e = warp; e < mp / 2; e += nw) {
+        int a, b;
+        if (e == 0) {
+          a = t;
+          b = mp - 1;
+        } else {
+          a = (t + e) % (mp - 1);
+          b = (t - e + mp - 1) % (mp - 1);
+        }
+        if (a >= m || b >= m) continue;
+        cd* ca = L + (size_t)a * ld;
+        cd* cb = L + (size_t)b * ld;
+        double al = 0.0, be = 0.0;
+        cd g = mkc(0.0, 0.0);
+        for (int i = lane; i < p; i += 32) {
+          const cd x = ca[i], y = cb[i];
+          al += cabs2(x);
+          be += cabs2(y);
+          g = cfmac(x, y, g);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        g = warp_csum(g);
+        const double ga = cabsd(g);
+        if (ga > tol * sqrt(al) * sqrt(be) && ga > 1e-300) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + tt * tt);
+          const double s = c * tt;
+          const cd ph = mkc(g.x / ga, -g.y / ga);  // exp(-i arg g)
+          for (int i = lane; i < p; i += 32) {
+            const cd x = ca[i];
+            const cd y = cmul(cb[i], ph);
+            ca[i] = mkc(c * x.x - s * y.x, c * x.y - s * y.y);
+            cb[i] = mkc(s * x.x + c * y.x, s * x.y + c * y.y);
+          }
+          if (lane == 0) atomicOr(sh_flag, 1);
+        }
+      }
+      __syncthreads();
+    }
+    const int any = *sh_flag;
+    __syncthreads();
+    if (!any) return sweep + 1;
+  }
+  return -1;
+}
+
+// Shared-memory layout needed by ts_svd for p columns and row blocks of hb.
+__host__ __device__ inline size_t ts_svd_smem_bytes(int p, int hb) {
+  return sizeof(cd) * ((size_t)(p + hb) * p + (size_t)p * p + p) + sizeof(double) * p + 64;
+}
+
+struct TsSvd {
+  int m;          // number of singular triplets = min(q, p)
+  int sweeps;     // Jacobi sweeps (-1: not converged)
+};
+
+// Right singular vectors of a tall-skinny Z (q x p, row-major, leading dim
+// ldz, read only; any address space). Streaming Householder QR over row blocks
+// of hb rows gives R (Z = Q R); the columns of L = R^H are then orthogonalised
+// by Hestenes' method, so L W = Y with Y/||Y|| the left singular vectors of
+// R^H, i.e. the right singular vectors of Z.
+// Output: V (p x m, column-major, leading dim p) in smem, sig[m] in
+// descending order, with V[:, i] the vector of sig[i].
+// W: smem work of wcap >= (p + 1) * p + p elements; row blocks are as tall
+// as W allows (hb = wcap / p - p rows below the running R).
+static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, int wcap, cd* V,
+                        double* sig, cd* taus, int* sh_flag) {
+  const int hb = wcap / p - p;
+  const int ldw = p + hb;
+  int nR = 0;  // rows of R currently held at the top of W
+  for (long long r0 = 0; r0 < q || (r0 == 0 && q == 0); r0 += hb) {
+    const int b = (int)min((long long)hb, q - r0);
+    // load block rows r0..r0+b below R
+    for (int idx = threadIdx.x; idx < b * p; idx += blockDim.x) {
+      const int i = idx / p, j = idx - i * p;
+      W[(size_t)j * ldw + nR + i] = Z[(size_t)(r0 + i) * ldz + j];
+    }
+    __syncthreads();
+    const int h = nR + b;
+    qr_inplace(W, ldw, h, p, taus);
+    nR = min(h, p);
+    // clear below the diagonal of R (reflector storage)
+    for (int idx = threadIdx.x; idx < nR * p; idx += blockDim.x) {
+      const int j = idx / nR, i = idx - j * nR;
+      if (i > j) W[(size_t)j * ldw + i] = mkc(0.0, 0.0);
+    }
+    __syncthreads();
+    if (q == 0) break;
+  }
+  const int m = nR;
+  // L = R^H (p x m) into V
+  for (int idx = threadIdx.x; idx < p * m; idx += blockDim.x) {
+    const int c = idx / p, i = idx - c * p;
+    V[(size_t)c * p + i] = (i >= c) ? cconj(W[(size_t)i * ldw + c]) : mkc(0.0, 0.0);
+  }
+  __syncthreads();
+  TsSvd out;
+  out.m = m;
+  out.sweeps = hestenes(V, p, p, m, 60, sh_flag);
+  // column norms
+  double* nrm = reinterpret_cast<double*>(W);  // W is free now
+  for (int c = warp_id(); c < m; c += n_warps()) {
+    double s = 0.0;
+    for (int i = lane_id(); i < p; i += 32) s += cabs2(V[(size_t)c * p + i]);
+    s = warp_sum(s);
+    if (lane_id() == 0) nrm[c] = sqrt(s);
+  }
+  __syncthreads();
+  // sort descending (stable by index), normalise into W after the norms
+  cd* Vs = W + p;  // p*m elements, fits in (p+hb)*p - p
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    int rank = 0;
+    const double sc = nrm[c];
+    for (int o = 0; o < m; ++o) {
+      const double so = nrm[o];
+      rank += (so > sc) || (so == sc && o < c);
+    }
+    sig[rank] = sc;
+    const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+    for (int i = 0; i < p; ++i) Vs[(size_t)rank * p + i] = cscale(V[(size_t)c * p + i], inv);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < p * m; idx += blockDim.x) V[idx] = Vs[idx];
+  __syncthreads();
+  return out;
+}
+
+// Smallest k >= 1 with sqrt(sum_{i >= k} sig_i^2) <= delta (sig descending);
+// evaluated redundantly by every thread.
+__device__ __forceinline__ int trunc_rank(const double* sig, int m, double delta) {
+  double tail = 0.0;
+  int k = m;
+  for (int i = m - 1; i >= 0; --i) {
+    tail += sig[i] * sig[i];
+    if (sqrt(tail) <= delta) k = i; else break;
+  }
+  return max(k, 1);
+}
+
+}  // namespace la

@@ -1,0 +1,894 @@
+// Host runtime and C ABI of the TT-SFFT pricer (include/sfft.h): context,
+// validation, grid planning (the scalars of Sec. 2.1), the damping-moment
+// check (Eq. damping_moment_condition), the Q_n MPO cache and the stream-
+// ordered launch sequence of the pricing path.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <deque>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/sfft.h"
+#include "kernels.cuh"
+
+static_assert(SFFT_MAX_N == SFFT_MAXN_DEV, "rank array stride");
+static_assert(SFFT_MAX_RANK == SFFT_SLOT_RANK_DEV, "slot rank");
+
+namespace {
+
+const int kThreads = 256;
+const int kHb = 32;  // row-block height reserved next to the 64-column panel
+const int kMaxBlockBits = 22;  // largest support block 2^m sampled for TT-SVD
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+struct MpoEntry {
+  int idx;        // slot index in the pool
+  int n;
+  double tol;
+  long long off;  // complex offset in the MPO pool
+  std::vector<int> ranks;
+};
+
+}  // namespace
+
+struct sfft_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // MPO cache (pool of fixed-size slots)
+  DevBuf mpo_pool;
+  DevBuf mpo_ranks_dev;  // (SFFT_MAX_N+1) per cached MPO
+  int mpo_slots = 0;
+  std::deque<MpoEntry> mpos;  // stable addresses across push_back
+  // batch workspaces (grow only)
+  std::map<std::string, DevBuf> bufs;
+  std::vector<char> pinned_dummy;
+};
+
+namespace {
+
+sfft_status set_err(sfft_ctx* ctx, sfft_status s, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return set_err(ctx, e_ == cudaErrorMemoryAllocation ? SFFT_ENOMEM : SFFT_ECUDA,     \
+                     "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,    \
+                     __LINE__);                                                           \
+  } while (0)
+
+sfft_status ensure(sfft_ctx* ctx, const char* name, size_t bytes, void** out) {
+  DevBuf& b = ctx->bufs[name];
+  if (b.bytes < bytes) {
+    if (b.p) {
+      cudaError_t e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return set_err(ctx, SFFT_ECUDA, "sync: %s", cudaGetErrorString(e));
+    }
+    b.release();
+    size_t nb = std::max(bytes, (size_t)256);
+    cudaError_t e = cudaMalloc(&b.p, nb);
+    if (e != cudaSuccess) {
+      b.p = nullptr;
+      return set_err(ctx, SFFT_ENOMEM, "cudaMalloc(%zu) for %s: %s", nb, name,
+                     cudaGetErrorString(e));
+    }
+    b.bytes = nb;
+  }
+  *out = b.p;
+  return SFFT_OK;
+}
+
+bool finite(double x) { return isfinite(x) != 0; }
+
+// Andersen-Piterbarg moment-explosion time of E[S_T^p] under Heston.
+double heston_explosion_time(double kappa, double sv, double rho, double p) {
+  const double b = kappa - rho * sv * p;
+  const double D2 = b * b - sv * sv * p * (p - 1.0);
+  if (D2 >= 0.0) {
+    const double d = sqrt(D2);
+    if (p * (p - 1.0) <= 0.0 || b >= 0.0) return INFINITY;
+    if (d == 0.0) return -2.0 / b;
+    const double g = (b - d) / (b + d);
+    return log(g) / d;
+  }
+  const double dl = sqrt(-D2);
+  if (b == 0.0) return M_PI / dl;
+  return 2.0 / dl * ((b < 0.0 ? M_PI : 0.0) + atan(dl / b));
+}
+
+// Validation and planning of one problem (host side, before any launch).
+sfft_status plan(sfft_ctx* ctx, const sfft_problem& pr, InstParams* out) {
+  if (pr.model < 0 || pr.model > 3) return set_err(ctx, SFFT_EINVAL, "model %d", pr.model);
+  if (pr.quad < 0 || pr.quad > 1) return set_err(ctx, SFFT_EINVAL, "quad %d", pr.quad);
+  if (pr.n < 1 || pr.n > SFFT_MAX_N) return set_err(ctx, SFFT_EINVAL, "n=%d out of [1,%d]", pr.n, SFFT_MAX_N);
+  if (!(pr.S0 > 0.0) || !finite(pr.S0)) return set_err(ctx, SFFT_EINVAL, "S0 must be finite and > 0");
+  if (!(pr.T > 0.0) || !finite(pr.T)) return set_err(ctx, SFFT_EINVAL, "T must be finite and > 0");
+  if (!finite(pr.r)) return set_err(ctx, SFFT_EINVAL, "r must be finite");
+  if (!finite(pr.alpha) || pr.alpha == 0.0 || pr.alpha == -1.0)
+    return set_err(ctx, SFFT_EINVAL, "alpha must be finite, not 0 or -1");
+  if (!(pr.tol > 0.0 && pr.tol < 1.0)) return set_err(ctx, SFFT_EINVAL, "tol must be in (0,1)");
+  if (!isnan(pr.k0)) return set_err(ctx, SFFT_EINVAL, "k0 must be NaN (default grid start)");
+  if (pr.max_rank < 0 || pr.max_rank > SFFT_MAX_RANK)
+    return set_err(ctx, SFFT_EINVAL, "max_rank %d out of [0,%d]", pr.max_rank, SFFT_MAX_RANK);
+  if (pr.quad == SFFT_QUAD_SIMPSON_CM99 && !(pr.eta > 0.0 && finite(pr.eta)))
+    return set_err(ctx, SFFT_EINVAL, "eta must be > 0 for Simpson");
+  if (pr.quad == SFFT_QUAD_RECT_SYM && !finite(pr.eta)) return set_err(ctx, SFFT_EINVAL, "eta not finite");
+  for (int i = 0; i < 8; ++i)
+    if (!finite(pr.p[i])) return set_err(ctx, SFFT_EINVAL, "parameter p[%d] not finite", i);
+  const double* p = pr.p;
+  const double a1 = pr.alpha + 1.0;
+  memset(out, 0, sizeof *out);
+  switch (pr.model) {
+    case SFFT_GBM:
+      if (!(p[0] > 0.0)) return set_err(ctx, SFFT_EINVAL, "GBM sigma must be > 0");
+      break;
+    case SFFT_HESTON:
+      if (!(p[0] > 0.0 && p[1] > 0.0 && p[2] > 0.0 && p[3] >= -1.0 && p[3] <= 1.0 && p[4] >= 0.0))
+        return set_err(ctx, SFFT_EINVAL, "Heston needs kappa,theta,sigma_v > 0, |rho|<=1, v0>=0");
+      if (!(heston_explosion_time(p[0], p[2], p[3], a1) > pr.T))
+        return set_err(ctx, SFFT_EMOMENT, "Heston moment of order alpha+1 explodes before T");
+      break;
+    case SFFT_MERTON:
+      if (!(p[0] > 0.0 && p[1] >= 0.0 && p[3] >= 0.0))
+        return set_err(ctx, SFFT_EINVAL, "Merton needs sigma > 0, lambda >= 0, delta_J >= 0");
+      out->kbar = exp(p[2] + 0.5 * p[3] * p[3]) - 1.0;
+      break;
+    case SFFT_VG: {
+      if (!(p[0] > 0.0 && p[1] > 0.0)) return set_err(ctx, SFFT_EINVAL, "VG needs sigma, nu > 0");
+      const double c1 = 1.0 - p[2] * p[1] - 0.5 * p[0] * p[0] * p[1];
+      if (!(c1 > 0.0)) return set_err(ctx, SFFT_EINVAL, "VG: 1 - theta nu - sigma^2 nu/2 must be > 0");
+      const double cp = 1.0 - p[2] * p[1] * a1 - 0.5 * p[0] * p[0] * p[1] * a1 * a1;
+      if (!(cp > 0.0)) return set_err(ctx, SFFT_EMOMENT, "VG moment of order alpha+1 is infinite");
+      out->omega = log(c1) / p[1];
+      break;
+    }
+  }
+  out->model = pr.model;
+  out->quad = pr.quad;
+  out->n = pr.n;
+  out->max_rank = pr.max_rank ? pr.max_rank : SFFT_DEFAULT_MAX_RANK;
+  for (int i = 0; i < 8; ++i) out->p[i] = pr.p[i];
+  out->S0 = pr.S0;
+  out->r = pr.r;
+  out->T = pr.T;
+  out->alpha = pr.alpha;
+  out->tol = pr.tol;
+  out->disc = exp(-pr.r * pr.T);
+  const double M = ldexp(1.0, pr.n);
+  if (pr.quad == SFFT_QUAD_SIMPSON_CM99) {
+    out->dv = pr.eta;
+    out->dk = 2.0 * M_PI / (M * pr.eta);
+    out->k0 = -M_PI / pr.eta;
+    out->N = 0;
+  } else {
+    const long long N = 1LL << (pr.n - 1);
+    out->N = N;
+    out->dv = pr.eta > 0.0 ? pr.eta : M_PI / sqrt((double)N);
+    out->dk = M_PI / ((double)N * out->dv);
+    out->k0 = -(double)N * out->dk / 2.0;
+  }
+  return SFFT_OK;
+}
+
+sfft_status check_strikes(sfft_ctx* ctx, int n, long long lb, long long stride, int q, int* tbits) {
+  if (q < 0 || q > SFFT_MAX_STRIKES) return set_err(ctx, SFFT_EINVAL, "q=%d out of range", q);
+  if (stride < 1 || (stride & (stride - 1))) return set_err(ctx, SFFT_EINVAL, "stride must be a power of two");
+  if (lb < 0 || (lb & (stride - 1))) return set_err(ctx, SFFT_EINVAL, "l_begin must be a non-negative multiple of stride");
+  int t = 0;
+  while ((1LL << t) < stride) ++t;
+  const long long M = 1LL << n;
+  if (q > 0) {
+    if (lb >= M) return set_err(ctx, SFFT_EINVAL, "l_begin beyond the grid");
+    if (q > 1 && (t > n || lb + (long long)(q - 1) * stride >= M))
+      return set_err(ctx, SFFT_EINVAL, "strike set runs beyond the grid");
+  }
+  *tbits = t;
+  return SFFT_OK;
+}
+
+int blocks_per_sm(const void* fn, size_t smem) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kThreads, smem) != cudaSuccess) b = 1;
+  return std::max(b, 1);
+}
+
+size_t svd_smem() { return la::ts_svd_smem_bytes(LA_MAXP, kHb) + 256; }
+
+sfft_status set_smem_attrs(sfft_ctx* ctx) {
+  const int sm = (int)svd_smem();
+  CK(cudaFuncSetAttribute(k_integrand_ttsvd, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_tt_round, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_zipup, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fft_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+  return SFFT_OK;
+}
+
+// MPO of Q_n at tolerance tol: cached; built by k_mpo_interp + k_tt_round.
+sfft_status get_mpo(sfft_ctx* ctx, int n, double tol, const MpoEntry** out) {
+  for (const auto& e : ctx->mpos)
+    if (e.n == n && e.tol == tol) {
+      *out = &e;
+      return SFFT_OK;
+    }
+  const long long slot = (long long)SFFT_MAX_N * SFFT_CORE_STRIDE_D4;
+  if ((int)ctx->mpos.size() >= ctx->mpo_slots) {
+    // grow the pool (copy existing entries)
+    const int nslots = std::max(16, ctx->mpo_slots * 2);
+    void* np = nullptr;
+    void* nr = nullptr;
+    CK(cudaMalloc(&np, sizeof(cd) * slot * nslots));
+    CK(cudaMalloc(&nr, sizeof(int) * (SFFT_MAX_N + 1) * nslots));
+    if (ctx->mpo_slots) {
+      CK(cudaMemcpyAsync(np, ctx->mpo_pool.p, sizeof(cd) * slot * ctx->mpo_slots,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(nr, ctx->mpo_ranks_dev.p, sizeof(int) * (SFFT_MAX_N + 1) * ctx->mpo_slots,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
+    ctx->mpo_pool.release();
+    ctx->mpo_ranks_dev.release();
+    ctx->mpo_pool.p = np;
+    ctx->mpo_pool.bytes = sizeof(cd) * slot * nslots;
+    ctx->mpo_ranks_dev.p = nr;
+    ctx->mpo_ranks_dev.bytes = sizeof(int) * (SFFT_MAX_N + 1) * nslots;
+    ctx->mpo_slots = nslots;
+  }
+  const int idx = (int)ctx->mpos.size();
+  MpoEntry e;
+  e.idx = idx;
+  e.n = n;
+  e.tol = tol;
+  e.off = slot * idx;
+  cd* W = reinterpret_cast<cd*>(ctx->mpo_pool.p) + e.off;
+  int* rk = reinterpret_cast<int*>(ctx->mpo_ranks_dev.p) + (SFFT_MAX_N + 1) * idx;
+  k_mpo_interp<<<n, kThreads, 0, ctx->stream>>>(n, SFFT_MPO_NODES, W, SFFT_CORE_STRIDE_D4, rk);
+  CK(cudaGetLastError());
+  // round: one instance, d = 4, with left orthogonalisation
+  struct H {
+    int n;
+    double tol;
+    int maxr;
+    long long off;
+  } h = {n, tol, SFFT_SLOT_RANK_DEV, 0};
+  void* hb;
+  sfft_status s = ensure(ctx, "mpo_args", 64, &hb);
+  if (s) return s;
+  char* a = reinterpret_cast<char*>(hb);
+  CK(cudaMemcpyAsync(a, &h.n, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(a + 8, &h.tol, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(a + 16, &h.maxr, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(a + 24, &h.off, sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+  void* scr;
+  s = ensure(ctx, "mpo_scratch", sizeof(cd) * SFFT_ROUND_SCRATCH, &scr);
+  if (s) return s;
+  k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(
+      1, reinterpret_cast<int*>(a), 4, 1, reinterpret_cast<double*>(a + 8),
+      reinterpret_cast<int*>(a + 16), W, reinterpret_cast<long long*>(a + 24), SFFT_CORE_STRIDE_D4,
+      rk, reinterpret_cast<cd*>(scr), SFFT_ROUND_SCRATCH, nullptr, kHb);
+  CK(cudaGetLastError());
+  e.ranks.resize(SFFT_MAX_N + 1);
+  CK(cudaMemcpyAsync(e.ranks.data(), rk, sizeof(int) * (SFFT_MAX_N + 1), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i <= n; ++i)
+    if (e.ranks[i] < 1 || e.ranks[i] > SFFT_SLOT_RANK_DEV)
+      return set_err(ctx, SFFT_ERANK, "MPO rank %d at bond %d", e.ranks[i], i);
+  ctx->mpos.push_back(e);
+  *out = &ctx->mpos.back();
+  return SFFT_OK;
+}
+
+template <class T>
+sfft_status upload(sfft_ctx* ctx, const char* name, const std::vector<T>& v, T** out) {
+  void* p;
+  sfft_status s = ensure(ctx, name, sizeof(T) * std::max<size_t>(v.size(), 1), &p);
+  if (s) return s;
+  if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, ctx->stream));
+  *out = reinterpret_cast<T*>(p);
+  return SFFT_OK;
+}
+
+// Device-side state of one batch of valid instances through the TT path.
+struct Batch {
+  int count = 0;
+  InstParams* P = nullptr;
+  int* n_arr = nullptr;
+  double* tol_arr = nullptr;
+  int* maxr_arr = nullptr;
+  int* status = nullptr;
+  cd* A = nullptr;
+  long long* a_off = nullptr;
+  int* a_ranks = nullptr;
+  cd* B = nullptr;
+  int* b_ranks = nullptr;
+  long long* w_off = nullptr;
+  int* w_ranks = nullptr;
+  std::vector<int> mpo_max;
+};
+
+// Integrand TT -> zip-up -> rounding, for `valid` problems (host vectors of
+// planned parameters). Leaves the output TTs in b.B.
+sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch& b,
+                        const std::vector<const MpoEntry*>* mpos_in, bool apply) {
+  const int cnt = (int)prm.size();
+  b.count = cnt;
+  sfft_status s;
+  std::vector<int> n_arr(cnt), maxr(cnt);
+  std::vector<double> tol(cnt);
+  std::vector<long long> off(cnt);
+  long long tot = 0;
+  for (int i = 0; i < cnt; ++i) {
+    n_arr[i] = prm[i].n;
+    maxr[i] = prm[i].max_rank;
+    tol[i] = prm[i].tol;
+    off[i] = tot;
+    tot += (long long)prm[i].n * SFFT_CORE_STRIDE_D2;
+  }
+  if ((s = upload(ctx, "P", prm, &b.P))) return s;
+  if ((s = upload(ctx, "n_arr", n_arr, &b.n_arr))) return s;
+  if ((s = upload(ctx, "tol_arr", tol, &b.tol_arr))) return s;
+  if ((s = upload(ctx, "maxr_arr", maxr, &b.maxr_arr))) return s;
+  if ((s = upload(ctx, "a_off", off, &b.a_off))) return s;
+  void* p;
+  if ((s = ensure(ctx, "A", sizeof(cd) * std::max(tot, 1LL), &p))) return s;
+  b.A = reinterpret_cast<cd*>(p);
+  if ((s = ensure(ctx, "B", sizeof(cd) * std::max(tot, 1LL), &p))) return s;
+  b.B = reinterpret_cast<cd*>(p);
+  const size_t rk = sizeof(int) * (SFFT_MAX_N + 1) * std::max(cnt, 1);
+  if ((s = ensure(ctx, "a_ranks", rk, &p))) return s;
+  b.a_ranks = reinterpret_cast<int*>(p);
+  if ((s = ensure(ctx, "b_ranks", rk, &p))) return s;
+  b.b_ranks = reinterpret_cast<int*>(p);
+  if ((s = ensure(ctx, "w_ranks", rk, &p))) return s;
+  b.w_ranks = reinterpret_cast<int*>(p);
+  if ((s = ensure(ctx, "status", sizeof(int) * std::max(cnt, 1), &p))) return s;
+  b.status = reinterpret_cast<int*>(p);
+  CK(cudaMemsetAsync(b.status, 0, sizeof(int) * std::max(cnt, 1), ctx->stream));
+  if (cnt == 0) return SFFT_OK;
+
+  // support probe -> block exponent m
+  int* m_dev;
+  if ((s = ensure(ctx, "m_arr", sizeof(int) * cnt, &p))) return s;
+  m_dev = reinterpret_cast<int*>(p);
+  k_support_probe<<<cnt, 64, 0, ctx->stream>>>(b.P, cnt, 1e-2, 4, m_dev);
+  CK(cudaGetLastError());
+  std::vector<int> m_host(cnt), st_host(cnt, 0);
+  CK(cudaMemcpyAsync(m_host.data(), m_dev, sizeof(int) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int mmax = 1;
+  for (int i = 0; i < cnt; ++i) {
+    if (m_host[i] > kMaxBlockBits) {
+      // support too wide for the TT-SVD block: not built
+      m_host[i] = -1;
+      st_host[i] = SFFT_ENOCONV;
+      continue;
+    }
+    mmax = std::max(mmax, m_host[i]);
+  }
+  CK(cudaMemcpyAsync(m_dev, m_host.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(b.status, st_host.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, ctx->stream));
+  const size_t smem = svd_smem();
+  int grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem));
+  const long long sstride = 2LL << mmax;
+  if ((s = ensure(ctx, "build_scratch", sizeof(cd) * sstride * grid, &p))) return s;
+  k_integrand_ttsvd<<<grid, kThreads, smem, ctx->stream>>>(b.P, m_dev, cnt, reinterpret_cast<cd*>(p),
+                                                           sstride, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
+                                                           b.a_ranks, b.status, kHb);
+  CK(cudaGetLastError());
+  if (!apply) return SFFT_OK;
+
+  // MPO per instance
+  std::vector<long long> w_off(cnt);
+  std::vector<int> w_ranks((size_t)cnt * (SFFT_MAX_N + 1));
+  for (int i = 0; i < cnt; ++i) {
+    const MpoEntry* e = (*mpos_in)[i];
+    w_off[i] = e->off;
+    std::copy(e->ranks.begin(), e->ranks.end(), w_ranks.begin() + (size_t)i * (SFFT_MAX_N + 1));
+  }
+  if ((s = upload(ctx, "w_off", w_off, &b.w_off))) return s;
+  CK(cudaMemcpyAsync(b.w_ranks, w_ranks.data(), sizeof(int) * w_ranks.size(), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, smem));
+  if ((s = ensure(ctx, "zip_scratch", sizeof(cd) * (size_t)SFFT_ZIP_SCRATCH * grid, &p))) return s;
+  k_zipup<<<grid, kThreads, smem, ctx->stream>>>(
+      cnt, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
+      reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
+      SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
+      SFFT_ZIP_SCRATCH, b.status, kHb);
+  CK(cudaGetLastError());
+  grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, smem));
+  if ((s = ensure(ctx, "round_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * grid, &p))) return s;
+  k_tt_round<<<grid, kThreads, smem, ctx->stream>>>(cnt, b.n_arr, 2, 0, b.tol_arr, b.maxr_arr, b.B,
+                                                    b.a_off, SFFT_CORE_STRIDE_D2, b.b_ranks,
+                                                    reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH,
+                                                    b.status, kHb);
+  CK(cudaGetLastError());
+  return SFFT_OK;
+}
+
+sfft_status copy_tt_out(sfft_ctx* ctx, const cd* base, const int* ranks_dev, int n, int d,
+                        int core_stride, int* ranks_host, double* out, long long cap) {
+  std::vector<int> r(SFFT_MAX_N + 1);
+  CK(cudaMemcpyAsync(r.data(), ranks_dev, sizeof(int) * (SFFT_MAX_N + 1), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  long long need = 0;
+  for (int s = 0; s < n; ++s) need += (long long)r[s] * d * r[s + 1];
+  for (int s = 0; s <= n; ++s) ranks_host[s] = r[s];
+  if (need > cap) return set_err(ctx, SFFT_EINVAL, "output capacity %lld < %lld", cap, need);
+  long long o = 0;
+  for (int s = 0; s < n; ++s) {
+    const long long sz = (long long)r[s] * d * r[s + 1];
+    CK(cudaMemcpyAsync(reinterpret_cast<cd*>(out) + o, base + (size_t)s * core_stride, sizeof(cd) * sz,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+    o += sz;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SFFT_OK;
+}
+
+sfft_status copy_tt_in(sfft_ctx* ctx, const double* in, const int* ranks, int n, int d,
+                       int core_stride, cd* base, int* ranks_dev) {
+  for (int s = 0; s <= n; ++s)
+    if (ranks[s] < 1 || ranks[s] > SFFT_SLOT_RANK_DEV || (d == 4 && ranks[s] > SFFT_SLOT_RANK_DEV))
+      return set_err(ctx, SFFT_EINVAL, "rank %d at bond %d out of [1,%d]", ranks[s], s, SFFT_SLOT_RANK_DEV);
+  if (ranks[0] != 1 || ranks[n] != 1) return set_err(ctx, SFFT_EINVAL, "boundary ranks must be 1");
+  long long o = 0;
+  for (int s = 0; s < n; ++s) {
+    const long long sz = (long long)ranks[s] * d * ranks[s + 1];
+    CK(cudaMemcpyAsync(base + (size_t)s * core_stride, reinterpret_cast<const cd*>(in) + o,
+                       sizeof(cd) * sz, cudaMemcpyDeviceToDevice, ctx->stream));
+    o += sz;
+  }
+  std::vector<int> r(SFFT_MAX_N + 1, 1);
+  for (int s = 0; s <= n; ++s) r[s] = ranks[s];
+  CK(cudaMemcpyAsync(ranks_dev, r.data(), sizeof(int) * (SFFT_MAX_N + 1), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SFFT_OK;
+}
+
+sfft_status finish_status(sfft_ctx* ctx, int count, const std::vector<int>& valid_idx,
+                          const std::vector<int>& host_status, const int* dev_status,
+                          int32_t* inst_status, sfft_info* info, const Batch* b,
+                          const std::vector<const MpoEntry*>* mpos) {
+  std::vector<int> st(count, 0);
+  for (int i = 0; i < count; ++i) st[i] = host_status[i];
+  std::vector<int> ds(valid_idx.size());
+  std::vector<int> ar, br;
+  if (!valid_idx.empty()) {
+    CK(cudaMemcpyAsync(ds.data(), dev_status, sizeof(int) * ds.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    if (info && b) {
+      ar.resize(valid_idx.size() * (SFFT_MAX_N + 1));
+      br.resize(ar.size());
+      CK(cudaMemcpyAsync(ar.data(), b->a_ranks, sizeof(int) * ar.size(), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(br.data(), b->b_ranks, sizeof(int) * br.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (size_t k = 0; k < valid_idx.size(); ++k) st[valid_idx[k]] = ds[k];
+  sfft_status first = SFFT_OK;
+  for (int i = 0; i < count; ++i) {
+    if (inst_status) inst_status[i] = st[i];
+    if (info) {
+      info[i].status = st[i];
+      info[i].int_rank = info[i].mpo_rank = info[i].out_rank = 0;
+      info[i].tt_bytes = 0;
+    }
+    if (st[i] != SFFT_OK && first == SFFT_OK) first = (sfft_status)st[i];
+  }
+  if (info && b) {
+    for (size_t k = 0; k < valid_idx.size(); ++k) {
+      const int i = valid_idx[k];
+      const int* a = ar.data() + k * (SFFT_MAX_N + 1);
+      const int* c = br.data() + k * (SFFT_MAX_N + 1);
+      info[i].int_rank = *std::max_element(a, a + SFFT_MAX_N + 1);
+      info[i].out_rank = *std::max_element(c, c + SFFT_MAX_N + 1);
+      if (mpos && (*mpos)[k]) {
+        const auto& rr = (*mpos)[k]->ranks;
+        info[i].mpo_rank = *std::max_element(rr.begin(), rr.end());
+      }
+    }
+  }
+  if (first != SFFT_OK && ctx->err.empty()) set_err(ctx, first, "instance failed: %s", sfft_status_string(first));
+  return first;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* sfft_status_string(sfft_status s) {
+  switch (s) {
+    case SFFT_OK: return "ok";
+    case SFFT_EINVAL: return "invalid argument";
+    case SFFT_EMOMENT: return "damping moment E[S^(alpha+1)] is infinite";
+    case SFFT_ENOMEM: return "out of memory";
+    case SFFT_ECUDA: return "CUDA error";
+    case SFFT_ERANK: return "rank cap reached";
+    case SFFT_ENOCONV: return "integrand builder did not converge";
+    case SFFT_ETIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* sfft_last_error(const sfft_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+sfft_status sfft_create(sfft_ctx** out, int device) {
+  if (!out) return SFFT_EINVAL;
+  *out = nullptr;
+  sfft_ctx* ctx = new sfft_ctx();
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return SFFT_ECUDA;
+  }
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return SFFT_ECUDA;
+  }
+  ctx->num_sms = prop.multiProcessorCount;
+  sfft_status s = set_smem_attrs(ctx);
+  if (s) {
+    delete ctx;
+    return s;
+  }
+  *out = ctx;
+  return SFFT_OK;
+}
+
+sfft_status sfft_destroy(sfft_ctx* ctx) {
+  if (!ctx) return SFFT_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->bufs) kv.second.release();
+  ctx->mpo_pool.release();
+  ctx->mpo_ranks_dev.release();
+  delete ctx;
+  return SFFT_OK;
+}
+
+sfft_status sfft_set_stream(sfft_ctx* ctx, void* stream) {
+  if (!ctx) return SFFT_EINVAL;
+  ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+  return SFFT_OK;
+}
+
+sfft_status sfft_strike_window(const sfft_problem* prob, double lo, double hi, int32_t qmax,
+                               int64_t* l_begin, int64_t* stride, int32_t* q) {
+  if (!prob || !l_begin || !stride || !q || qmax < 1 || !(lo <= hi)) return SFFT_EINVAL;
+  InstParams P;
+  sfft_status s = plan(nullptr, *prob, &P);
+  if (s != SFFT_OK && s != SFFT_EMOMENT) return s;
+  const long long M = 1LL << P.n;
+  long long u_lo = (long long)ceil((lo - P.k0) / P.dk - 1e-9);
+  long long u_hi = (long long)floor((hi - P.k0) / P.dk + 1e-9);
+  u_lo = std::max(u_lo, 0LL);
+  u_hi = std::min(u_hi, M - 1);
+  long long st = 1;
+  for (;;) {
+    const long long first = ((u_lo + st - 1) / st) * st;
+    const long long cnt = (u_hi >= first) ? (u_hi - first) / st + 1 : 0;
+    if (cnt <= qmax) {
+      *l_begin = first;
+      *stride = st;
+      *q = (int32_t)cnt;
+      return SFFT_OK;
+    }
+    st *= 2;
+  }
+}
+
+sfft_status sfft_sample_integrand(sfft_ctx* ctx, const sfft_problem* prob, const int64_t* j,
+                                  int64_t count, double* x) {
+  if (!ctx || !prob || count < 0 || (count > 0 && (!j || !x))) return set_err(ctx, SFFT_EINVAL, "bad arguments");
+  ctx->err.clear();
+  CK(cudaSetDevice(ctx->device));
+  InstParams P;
+  sfft_status s = plan(ctx, *prob, &P);
+  if (s) return s;
+  if (count == 0) return SFFT_OK;
+  void* pd;
+  if ((s = ensure(ctx, "sample_P", sizeof(InstParams), &pd))) return s;
+  CK(cudaMemcpyAsync(pd, &P, sizeof P, cudaMemcpyHostToDevice, ctx->stream));
+  const int grid = (int)std::min<long long>((count + kThreads - 1) / kThreads, 148LL * 16);
+  k_sample<<<grid, kThreads, 0, ctx->stream>>>(reinterpret_cast<InstParams*>(pd),
+                                               reinterpret_cast<const long long*>(j), count,
+                                               reinterpret_cast<cd*>(x));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SFFT_OK;
+}
+
+sfft_status sfft_mpo(sfft_ctx* ctx, int32_t n, double tol, int32_t* ranks, double* cores, int64_t cap) {
+  if (!ctx || n < 1 || n > SFFT_MAX_N || !(tol > 0.0 && tol < 1.0) || !ranks || !cores)
+    return set_err(ctx, SFFT_EINVAL, "bad arguments");
+  ctx->err.clear();
+  CK(cudaSetDevice(ctx->device));
+  const MpoEntry* e;
+  sfft_status s = get_mpo(ctx, n, tol, &e);
+  if (s) return s;
+  const int idx = e->idx;
+  return copy_tt_out(ctx, reinterpret_cast<const cd*>(ctx->mpo_pool.p) + e->off,
+                     reinterpret_cast<const int*>(ctx->mpo_ranks_dev.p) + (SFFT_MAX_N + 1) * idx, n, 4,
+                     SFFT_CORE_STRIDE_D4, ranks, cores, cap);
+}
+
+sfft_status sfft_integrand_tt(sfft_ctx* ctx, const sfft_problem* prob, int32_t* ranks, double* cores,
+                              int64_t cap) {
+  if (!ctx || !prob || !ranks || !cores) return set_err(ctx, SFFT_EINVAL, "bad arguments");
+  ctx->err.clear();
+  CK(cudaSetDevice(ctx->device));
+  std::vector<InstParams> prm(1);
+  sfft_status s = plan(ctx, *prob, &prm[0]);
+  if (s) return s;
+  Batch b;
+  if ((s = run_tt_path(ctx, prm, b, nullptr, false))) return s;
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, b.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (st) return set_err(ctx, (sfft_status)st, "integrand TT: %s", sfft_status_string((sfft_status)st));
+  return copy_tt_out(ctx, b.A, b.a_ranks, prm[0].n, 2, SFFT_CORE_STRIDE_D2, ranks, cores, cap);
+}
+
+sfft_status sfft_tt_round(sfft_ctx* ctx, int32_t n, int32_t d, const int32_t* in_ranks,
+                          const double* in_cores, double tol, int32_t max_rank, int32_t* out_ranks,
+                          double* out_cores, int64_t cap) {
+  if (!ctx || n < 1 || n > SFFT_MAX_N || (d != 2 && d != 4) || !in_ranks || !in_cores || !out_ranks ||
+      !out_cores || !(tol > 0.0 && tol < 1.0) || max_rank < 0 || max_rank > SFFT_MAX_RANK)
+    return set_err(ctx, SFFT_EINVAL, "bad arguments");
+  ctx->err.clear();
+  CK(cudaSetDevice(ctx->device));
+  void* p;
+  sfft_status s;
+  const int stride = (d == 2) ? SFFT_CORE_STRIDE_D2 : SFFT_CORE_STRIDE_D4;
+  if ((s = ensure(ctx, "rt_tt", sizeof(cd) * (size_t)n * stride, &p))) return s;
+  cd* T = reinterpret_cast<cd*>(p);
+  void* rd;
+  if ((s = ensure(ctx, "rt_ranks", sizeof(int) * (SFFT_MAX_N + 1), &rd))) return s;
+  if ((s = copy_tt_in(ctx, in_cores, in_ranks, n, d, stride, T, reinterpret_cast<int*>(rd)))) return s;
+  std::vector<int> nv(1, n), mr(1, max_rank ? max_rank : SFFT_DEFAULT_MAX_RANK), st0(1, 0);
+  std::vector<double> tv(1, tol);
+  std::vector<long long> off(1, 0);
+  int *nd, *md, *sd;
+  double* td;
+  long long* od;
+  if ((s = upload(ctx, "rt_n", nv, &nd)) || (s = upload(ctx, "rt_m", mr, &md)) ||
+      (s = upload(ctx, "rt_tol", tv, &td)) || (s = upload(ctx, "rt_off", off, &od)) ||
+      (s = upload(ctx, "rt_st", st0, &sd)))
+    return s;
+  void* scr;
+  if ((s = ensure(ctx, "rt_scratch", sizeof(cd) * SFFT_ROUND_SCRATCH, &scr))) return s;
+  k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(1, nd, d, 1, td, md, T, od, stride,
+                                                      reinterpret_cast<int*>(rd), reinterpret_cast<cd*>(scr),
+                                                      SFFT_ROUND_SCRATCH, sd, kHb);
+  CK(cudaGetLastError());
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, sd, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (st) return set_err(ctx, (sfft_status)st, "rounding: %s", sfft_status_string((sfft_status)st));
+  return copy_tt_out(ctx, T, reinterpret_cast<int*>(rd), n, d, stride, out_ranks, out_cores, cap);
+}
+
+sfft_status sfft_tt_apply_qft(sfft_ctx* ctx, int32_t n, const int32_t* in_ranks, const double* in_cores,
+                              double tol, int32_t max_rank, int32_t* out_ranks, double* out_cores,
+                              int64_t cap) {
+  if (!ctx || n < 1 || n > SFFT_MAX_N || !in_ranks || !in_cores || !out_ranks || !out_cores ||
+      !(tol > 0.0 && tol < 1.0) || max_rank < 0 || max_rank > SFFT_MAX_RANK)
+    return set_err(ctx, SFFT_EINVAL, "bad arguments");
+  ctx->err.clear();
+  CK(cudaSetDevice(ctx->device));
+  const MpoEntry* e;
+  sfft_status s = get_mpo(ctx, n, tol, &e);
+  if (s) return s;
+  void* p;
+  if ((s = ensure(ctx, "ap_A", sizeof(cd) * (size_t)n * SFFT_CORE_STRIDE_D2, &p))) return s;
+  cd* A = reinterpret_cast<cd*>(p);
+  if ((s = ensure(ctx, "ap_B", sizeof(cd) * (size_t)n * SFFT_CORE_STRIDE_D2, &p))) return s;
+  cd* B = reinterpret_cast<cd*>(p);
+  void *ra, *rb, *rw;
+  if ((s = ensure(ctx, "ap_ra", sizeof(int) * (SFFT_MAX_N + 1), &ra)) ||
+      (s = ensure(ctx, "ap_rb", sizeof(int) * (SFFT_MAX_N + 1), &rb)) ||
+      (s = ensure(ctx, "ap_rw", sizeof(int) * (SFFT_MAX_N + 1), &rw)))
+    return s;
+  if ((s = copy_tt_in(ctx, in_cores, in_ranks, n, 2, SFFT_CORE_STRIDE_D2, A, reinterpret_cast<int*>(ra))))
+    return s;
+  CK(cudaMemcpyAsync(rw, e->ranks.data(), sizeof(int) * (SFFT_MAX_N + 1), cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<int> nv(1, n), mr(1, max_rank ? max_rank : SFFT_DEFAULT_MAX_RANK), st0(1, 0);
+  std::vector<double> tv(1, tol);
+  std::vector<long long> off(1, 0), woff(1, e->off);
+  int *nd, *md, *sd;
+  double* td;
+  long long *od, *wd;
+  if ((s = upload(ctx, "ap_n", nv, &nd)) || (s = upload(ctx, "ap_m", mr, &md)) ||
+      (s = upload(ctx, "ap_tol", tv, &td)) || (s = upload(ctx, "ap_off", off, &od)) ||
+      (s = upload(ctx, "ap_woff", woff, &wd)) || (s = upload(ctx, "ap_st", st0, &sd)))
+    return s;
+  void* scr;
+  if ((s = ensure(ctx, "ap_scratch", sizeof(cd) * (size_t)(SFFT_ZIP_SCRATCH + SFFT_ROUND_SCRATCH), &scr)))
+    return s;
+  k_zipup<<<1, kThreads, svd_smem(), ctx->stream>>>(
+      1, nd, td, md, A, od, reinterpret_cast<int*>(ra), reinterpret_cast<const cd*>(ctx->mpo_pool.p), wd,
+      reinterpret_cast<int*>(rw), B, od, reinterpret_cast<int*>(rb), SFFT_CORE_STRIDE_D2,
+      SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(scr), SFFT_ZIP_SCRATCH, sd, kHb);
+  CK(cudaGetLastError());
+  k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(1, nd, 2, 0, td, md, B, od, SFFT_CORE_STRIDE_D2,
+                                                      reinterpret_cast<int*>(rb), reinterpret_cast<cd*>(scr),
+                                                      SFFT_ROUND_SCRATCH, sd, kHb);
+  CK(cudaGetLastError());
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, sd, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (st) return set_err(ctx, (sfft_status)st, "apply: %s", sfft_status_string((sfft_status)st));
+  return copy_tt_out(ctx, B, reinterpret_cast<int*>(rb), n, 2, SFFT_CORE_STRIDE_D2, out_ranks, out_cores, cap);
+}
+
+static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_t count,
+                                const int64_t* l_begin, const int64_t* stride, const int32_t* q,
+                                double* prices, double* log_strikes, int32_t* inst_status,
+                                sfft_info* info, bool dense) {
+  if (!ctx || count < 0 || (count > 0 && (!probs || !l_begin || !stride || !q)))
+    return set_err(ctx, SFFT_EINVAL, "bad arguments");
+  ctx->err.clear();
+  CK(cudaSetDevice(ctx->device));
+  std::vector<int> host_status(count, 0), tbits(count, 0);
+  std::vector<long long> out_off(count, 0);
+  long long tot_q = 0;
+  for (int i = 0; i < count; ++i) {
+    out_off[i] = tot_q;
+    tot_q += std::max(q[i], 0);
+  }
+  if (tot_q > 0 && (!prices || !log_strikes)) return set_err(ctx, SFFT_EINVAL, "output buffers are NULL");
+  std::vector<InstParams> prm;
+  std::vector<int> valid;
+  std::vector<long long> lb_v, off_v;
+  std::vector<int> tb_v, q_v;
+  for (int i = 0; i < count; ++i) {
+    InstParams P;
+    sfft_status s = plan(ctx, probs[i], &P);
+    if (s == SFFT_OK) s = check_strikes(ctx, probs[i].n, l_begin[i], stride[i], q[i], &tbits[i]);
+    if (s == SFFT_OK && dense && probs[i].n > SFFT_DENSE_MAX_N)
+      s = set_err(ctx, SFFT_EINVAL, "dense baseline limited to n <= %d", SFFT_DENSE_MAX_N);
+    host_status[i] = s;
+    if (s != SFFT_OK) continue;
+    valid.push_back(i);
+    prm.push_back(P);
+    lb_v.push_back(l_begin[i]);
+    off_v.push_back(out_off[i]);
+    tb_v.push_back(tbits[i]);
+    q_v.push_back(q[i]);
+  }
+  // prices of rejected instances are NaN
+  {
+    std::vector<std::pair<long long, int>> bad;
+    for (int i = 0; i < count; ++i)
+      if (host_status[i] != SFFT_OK && q[i] > 0) bad.push_back({out_off[i], q[i]});
+    if (!bad.empty()) {
+      std::vector<double> nanv(65536, NAN);
+      for (auto& bq : bad)
+        CK(cudaMemcpyAsync(prices + bq.first, nanv.data(), sizeof(double) * bq.second,
+                           cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
+  }
+  const int cnt = (int)prm.size();
+  if (cnt == 0) return finish_status(ctx, count, valid, host_status, nullptr, inst_status, info, nullptr, nullptr);
+  sfft_status s;
+  if (dense) {
+    // one instance at a time, whole GPU per instance
+    int maxn = 1;
+    for (auto& P : prm) maxn = std::max(maxn, P.n);
+    void* xb;
+    if ((s = ensure(ctx, "dense_x", sizeof(cd) * (1ULL << maxn), &xb))) return s;
+    int* st_dev;
+    void* p;
+    if ((s = ensure(ctx, "status", sizeof(int) * cnt, &p))) return s;
+    st_dev = reinterpret_cast<int*>(p);
+    CK(cudaMemsetAsync(st_dev, 0, sizeof(int) * cnt, ctx->stream));
+    void* dg;
+    if ((s = ensure(ctx, "dense_digits", sizeof(int) * 16, &dg))) return s;
+    for (int k = 0; k < cnt; ++k) {
+      const InstParams& P = prm[k];
+      const long long M = 1LL << P.n;
+      cd* x = reinterpret_cast<cd*>(xb);
+      k_dense_sample<<<ctx->num_sms * 8, kThreads, 0, ctx->stream>>>(P, x, M);
+      CK(cudaGetLastError());
+      const int npass = (P.n + 7) / 8;
+      std::vector<int> dig(npass);
+      int left = P.n;
+      for (int pp = 0; pp < npass; ++pp) {
+        dig[pp] = (left + (npass - pp) - 1) / (npass - pp);
+        left -= dig[pp];
+      }
+      long long L = M;
+      for (int pp = 0; pp < npass; ++pp) {
+        const int R = dig[pp];
+        const long long Lp = L >> R;
+        const int cols = (int)std::min<long long>(Lp, std::max(1, 4096 >> R));
+        const size_t smem = sizeof(cd) * ((size_t)(1 << R) * cols + (1 << R));
+        const long long nblk = (M / L) * (Lp / cols);
+        const int grid = (int)std::min<long long>(nblk, (long long)ctx->num_sms * 8);
+        k_fft_pass<<<grid, kThreads, smem, ctx->stream>>>(x, M, Lp, R, cols);
+        CK(cudaGetLastError());
+        L = Lp;
+      }
+      CK(cudaMemcpyAsync(dg, dig.data(), sizeof(int) * npass, cudaMemcpyHostToDevice, ctx->stream));
+      if (q_v[k] > 0) {
+        k_dense_gather<<<(q_v[k] + kThreads - 1) / kThreads, kThreads, 0, ctx->stream>>>(
+            P, x, P.n, reinterpret_cast<int*>(dg), npass, lb_v[k], tb_v[k], q_v[k], prices + off_v[k],
+            log_strikes + off_v[k]);
+        CK(cudaGetLastError());
+      }
+    }
+    return finish_status(ctx, count, valid, host_status, st_dev, inst_status, info, nullptr, nullptr);
+  }
+  std::vector<const MpoEntry*> mp(cnt);
+  for (int k = 0; k < cnt; ++k) {
+    if ((s = get_mpo(ctx, prm[k].n, prm[k].tol, &mp[k]))) return s;
+  }
+  Batch b;
+  if ((s = run_tt_path(ctx, prm, b, &mp, true))) return s;
+  long long* lb_d;
+  long long* off_d;
+  int *tb_d, *q_d;
+  if ((s = upload(ctx, "lb", lb_v, &lb_d)) || (s = upload(ctx, "outoff", off_v, &off_d)) ||
+      (s = upload(ctx, "tb", tb_v, &tb_d)) || (s = upload(ctx, "qv", q_v, &q_d)))
+    return s;
+  void* p;
+  const int grid = std::min(cnt, ctx->num_sms * 4);
+  if ((s = ensure(ctx, "readout_scratch", sizeof(cd) * (size_t)SFFT_READOUT_SCRATCH * grid, &p))) return s;
+  k_readout<<<grid, kThreads, 0, ctx->stream>>>(cnt, b.P, b.B, b.a_off, b.b_ranks, SFFT_CORE_STRIDE_D2,
+                                                lb_d, tb_d, q_d, off_d, prices, log_strikes, b.status,
+                                                reinterpret_cast<cd*>(p), SFFT_READOUT_SCRATCH);
+  CK(cudaGetLastError());
+  return finish_status(ctx, count, valid, host_status, b.status, inst_status, info, &b, &mp);
+}
+
+sfft_status sfft_price_batch(sfft_ctx* ctx, const sfft_problem* probs, int32_t count, const int64_t* l_begin,
+                             const int64_t* stride, const int32_t* q, double* prices, double* log_strikes,
+                             int32_t* inst_status, sfft_info* info) {
+  return price_common(ctx, probs, count, l_begin, stride, q, prices, log_strikes, inst_status, info, false);
+}
+
+sfft_status sfft_dense_price_batch(sfft_ctx* ctx, const sfft_problem* probs, int32_t count,
+                                   const int64_t* l_begin, const int64_t* stride, const int32_t* q,
+                                   double* prices, double* log_strikes, int32_t* inst_status,
+                                   sfft_info* info) {
+  return price_common(ctx, probs, count, l_begin, stride, q, prices, log_strikes, inst_status, info, true);
+}
+
+}  // extern "C"

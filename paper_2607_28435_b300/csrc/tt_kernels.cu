@@ -1,0 +1,658 @@
+// TT-SFFT kernels for sm_103a: integrand TT (TT-SVD of the sampled support
+// block), Q_n MPO generator, zip-up MPO x TT contraction, TT rounding and the
+// bit-reversed readout of prices (Sec. 4 of the paper).
+//
+// Storage: each TT (or MPO, d = 4) of an instance occupies n "core slots" of
+// core_stride complex elements; core s (0-based site, site s+1 of the paper)
+// of shape (r_s, d, r_{s+1}) is stored compactly, index [a][sigma][b] at
+// a*d*r_{s+1} + sigma*r_{s+1} + b. Ranks live in an int array of n+1 entries.
+// Site s carries bit (n-1-s) of the input index j (most significant first,
+// Eq. discretized_x) and bit s of the output index u after Q_n (Sec. 4.2).
+//
+// One CTA works on one instance at a time (grid-stride over the batch); the
+// site sweeps are sequential, the dense algebra inside a site is spread over
+// the CTA. Large per-site panels live in a per-CTA global scratch slice, which
+// stays resident in L2.
+#include "kernels.cuh"
+
+using namespace la;
+
+namespace {
+
+__device__ __forceinline__ cd* core_ptr(cd* base, int core_stride, int s) {
+  return base + (size_t)s * core_stride;
+}
+
+#define SVD_WCAP(hb) ((LA_MAXP + (hb)) * LA_MAXP)
+
+struct SvdSmem {
+  cd* W;
+  cd* V;
+  double* sig;
+  cd* tau;
+  int* flag;
+  int* misc;
+};
+
+__device__ SvdSmem carve_svd_smem(void* raw, int p, int hb) {
+  SvdSmem s;
+  char* c = reinterpret_cast<char*>(raw);
+  s.W = reinterpret_cast<cd*>(c);
+  c += sizeof(cd) * (size_t)(p + hb) * p;
+  s.V = reinterpret_cast<cd*>(c);
+  c += sizeof(cd) * (size_t)p * p;
+  s.sig = reinterpret_cast<double*>(c);
+  c += sizeof(double) * p;
+  s.tau = reinterpret_cast<cd*>(c);
+  c += sizeof(cd) * p;
+  s.flag = reinterpret_cast<int*>(c);
+  s.misc = s.flag + 1;
+  return s;
+}
+
+// out (q x k, row-major) = Z (q x p, row-major) * V[:, :k] (V column-major p x *)
+__device__ void gemm_zv(const cd* Z, long long q, int p, const cd* V, int k, cd* out) {
+  const long long tot = q * (long long)k;
+  for (long long idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const long long i = idx / k;
+    const int c = (int)(idx - i * k);
+    const cd* zr = Z + (size_t)i * p;
+    const cd* vc = V + (size_t)c * p;
+    cd acc = mkc(0.0, 0.0);
+    for (int j = 0; j < p; ++j) acc = cfma(zr[j], vc[j], acc);
+    out[idx] = acc;
+  }
+}
+
+__device__ double cta_norm2(const cd* x, long long len, double* red) {
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < len; i += blockDim.x) s += cabs2(x[i]);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double tot = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+  __syncthreads();
+  return tot;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// K1: integrand samples at listed indices
+// ---------------------------------------------------------------------------
+__global__ void k_sample(const InstParams* __restrict__ P, const long long* __restrict__ j,
+                         long long count, cd* __restrict__ x) {
+  const InstParams prm = *P;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = integrand(prm, j[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Support probe: smallest m such that the integrand beyond 2^m is negligible.
+// Probes j = 2^i (1 + k/4), k < 4; m is the smallest exponent for which every
+// probe at or beyond 2^m has |x_j| * j <= probe_tol * max |x|.
+// ---------------------------------------------------------------------------
+__global__ void k_support_probe(const InstParams* __restrict__ P, int count, double probe_factor,
+                                int m_min, int* __restrict__ m_out) {
+  const int inst = blockIdx.x;
+  if (inst >= count) return;
+  const InstParams prm = P[inst];
+  const double probe_tol = probe_factor * prm.tol;
+  __shared__ double mag[4 * 64];
+  __shared__ double jv[4 * 64];
+  const int n = prm.n;
+  const int nprobe = 4 * n;
+  for (int t = threadIdx.x; t < nprobe; t += blockDim.x) {
+    const int i = t >> 2, k = t & 3;
+    long long j = (1LL << i) + ((1LL << i) >> 2) * k;
+    if (j >= (1LL << n)) j = (1LL << n) - 1;
+    const cd x = integrand(prm, j);
+    mag[t] = cabsd(x);
+    jv[t] = (double)j;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int t = 0; t < nprobe; ++t) mx = fmax(mx, mag[t]);
+    {
+      const cd x0 = integrand(prm, 0);
+      mx = fmax(mx, cabsd(x0));
+    }
+    int m = n;
+    if (prm.quad == Q_SIMPSON) {
+      // scan from the top: find the lowest exponent whose probes beyond are small
+      int mm = n;
+      for (int e = n - 1; e >= 0; --e) {
+        bool ok = true;
+        for (int k = 0; k < 4; ++k) {
+          const int t = 4 * e + k;
+          if (mag[t] * jv[t] > probe_tol * mx) ok = false;
+        }
+        if (!ok) break;
+        mm = e;
+      }
+      m = max(mm + 1, min(m_min, n));
+      m = min(m, n);
+    }
+    m_out[inst] = m;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: integrand TT by TT-SVD of the support block (Sec. 4.1; Oseledets 2011)
+// ---------------------------------------------------------------------------
+// The block x_j, j < 2^m, is swept from its least significant bit: at step t
+// the carried matrix Z (2^(m-t-1) rows = remaining high bits, 2 r columns =
+// (lambda, rank)) is factorised Z = U S V^H; V^H becomes core n-1-t and Z V
+// the next carry. Sites above the block (Simpson grid, m < n) hold the
+// rank-one core delta_{lambda,0}.
+__global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* __restrict__ m_arr,
+                                  int count, cd* __restrict__ scratch, long long scratch_stride,
+                                  cd* __restrict__ tt, const long long* __restrict__ tt_off,
+                                  int core_stride, int* __restrict__ ranks_all,
+                                  int* __restrict__ status, int hb) {
+  extern __shared__ double4 smem_raw[];
+  SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
+  for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
+    const InstParams prm = P[inst];
+    const int n = prm.n;
+    const int m = m_arr[inst];
+    if (m < 0) continue;  // not built (status already set)
+    const int rmax = prm.max_rank;
+    int* ranks = ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
+    cd* base = tt + tt_off[inst];
+    cd* bufA = scratch + (size_t)blockIdx.x * scratch_stride;
+    cd* bufB = bufA + (1LL << m);
+    const long long Mb = 1LL << m;
+    for (long long j = threadIdx.x; j < Mb; j += blockDim.x) bufA[j] = integrand(prm, j);
+    __syncthreads();
+    int st = 0;
+    cd* Z = bufA;
+    cd* O = bufB;
+    long long q = Mb >> 1;
+    int rprev = 1;
+    double delta = 0.0;
+    int site = n - 1;
+    for (int t = 0; t < m; ++t, --site) {
+      const int p = 2 * rprev;
+      cd* G = core_ptr(base, core_stride, site);
+      if (q == 1) {
+        // top of the block: the carry itself is the core (1, 2, rprev)
+        for (int idx = threadIdx.x; idx < p; idx += blockDim.x) G[idx] = Z[idx];
+        if (threadIdx.x == 0) {
+          ranks[site] = 1;
+          ranks[site + 1] = rprev;
+        }
+        __syncthreads();
+        break;
+      }
+      TsSvd sv = ts_svd(Z, q, p, p, sm.W, SVD_WCAP(hb), sm.V, sm.sig, sm.tau, sm.flag);
+      if (sv.sweeps < 0) st = SFFT_ENOCONV_DEV;
+      if (t == 0) {
+        double s2 = 0.0;
+        for (int i = 0; i < sv.m; ++i) s2 += sm.sig[i] * sm.sig[i];
+        delta = prm.tol * sqrt(s2) / sqrt((double)max(n - 1, 1));
+      }
+      int k = trunc_rank(sm.sig, sv.m, delta);
+      if (k > rmax) {
+        st = SFFT_ERANK_DEV;
+        k = rmax;
+      }
+      // core (k, 2, rprev): G[c][lam][b] = conj(V[(lam, b), c])
+      for (int idx = threadIdx.x; idx < k * p; idx += blockDim.x) {
+        const int c = idx / p, rem = idx - c * p;
+        G[idx] = cconj(sm.V[(size_t)c * p + rem]);
+      }
+      if (threadIdx.x == 0) {
+        ranks[site] = k;
+        ranks[site + 1] = rprev;
+      }
+      gemm_zv(Z, q, p, sm.V, k, O);
+      __syncthreads();
+      cd* tmp = Z;
+      Z = O;
+      O = tmp;
+      q >>= 1;
+      rprev = k;
+    }
+    // sites above the block
+    for (int s = 0; s < n - m; ++s) {
+      cd* G = core_ptr(base, core_stride, s);
+      if (threadIdx.x == 0) {
+        G[0] = mkc(1.0, 0.0);
+        G[1] = mkc(0.0, 0.0);
+        ranks[s] = 1;
+      }
+    }
+    if (threadIdx.x == 0) {
+      ranks[0] = 1;
+      ranks[n] = 1;
+      status[inst] = st;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3: Q_n MPO by barycentric Chebyshev interpolation of the bond variable
+// ---------------------------------------------------------------------------
+// Q_n = M^{-1/2} prod_l exp(-i pi mu_l (lambda_l + B_l)) with
+// B_l = sum_{l' > l} lambda_l' 2^(l - l') in [0, 1) (the product form of the
+// bit-reversed DFT, Sec. 4.2). The dependence of sites 1..l on B_l is an
+// entire function exp(-2 pi i A B_l), A in [0,1), so it is carried across
+// bond l by its values at P Chebyshev nodes b_q of [0,1]; B_{l-1} =
+// (lambda_l + B_l)/2 gives the transfer core
+//   W_l[p, mu, lambda, q] = 2^{-1/2} L_p((lambda + b_q)/2) exp(-i pi mu (lambda + b_q)),
+// with the first core at p = 0 alone and the last at B_n = 0. Rounding then
+// compresses the bonds to the requested tolerance.
+__device__ __forceinline__ double cheb_node(int q, int P) {
+  return 0.5 * (1.0 - cospi((2.0 * q + 1.0) / (2.0 * P)));
+}
+__device__ __forceinline__ double cheb_bw(int q, int P) {
+  return ((q & 1) ? -1.0 : 1.0) * sinpi((2.0 * q + 1.0) / (2.0 * P));
+}
+// Lagrange basis L_p(x) at nodes b_q, barycentric form of the second kind
+__device__ double lagrange(int p, double x, int P) {
+  double den = 0.0, num = 0.0;
+  for (int q = 0; q < P; ++q) {
+    const double d = x - cheb_node(q, P);
+    if (d == 0.0) return q == p ? 1.0 : 0.0;
+    const double t = cheb_bw(q, P) / d;
+    den += t;
+    if (q == p) num = t;
+  }
+  return num / den;
+}
+
+__global__ void k_mpo_interp(int n, int P, cd* __restrict__ W, int core_stride,
+                             int* __restrict__ ranks) {
+  const double s2 = 0.70710678118654752;
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    const int r0 = (s == 0) ? 1 : P;
+    const int r1 = (s == n - 1) ? 1 : P;
+    cd* G = W + (size_t)s * core_stride;
+    const int tot = r0 * 4 * r1;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      const int a = idx / (4 * r1);
+      const int rem = idx - a * 4 * r1;
+      const int sg = rem / r1, b = rem - sg * r1;
+      const int mu = sg >> 1, lam = sg & 1;
+      const double bq = (s == n - 1) ? 0.0 : cheb_node(b, P);
+      const double x = 0.5 * (lam + bq);
+      const double lp = (s == 0) ? 1.0 : lagrange(a, x, P);
+      double ph_re = 1.0, ph_im = 0.0;
+      if (mu) {
+        // exp(-i pi (lam + bq))
+        double sn, cs;
+        sincospi(lam + bq, &sn, &cs);
+        ph_re = cs;
+        ph_im = -sn;
+      }
+      G[idx] = mkc(s2 * lp * ph_re, s2 * lp * ph_im);
+    }
+    if (threadIdx.x == 0) {
+      ranks[s] = r0;
+      if (s == n - 1) ranks[n] = 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K5: TT rounding (Oseledets 2011): optional left-to-right orthogonalisation
+// by Householder QR, then a right-to-left sweep of truncated SVDs with
+// delta = tol ||A|| / sqrt(n-1). Works in place on a slot TT with d in {2,4}.
+// ---------------------------------------------------------------------------
+// Right-to-left step at site s, X = G_s as r_s x (d r_{s+1}) = U S V^H:
+// the SVD of Z = X^H gives U and S; with k kept, Y = Z U_k = V_k S_k is
+// re-orthonormalised by QR, Y = Q_V R_V, so that X ~= (U_k R_V^H) Q_V^H exactly
+// up to the truncation, with Q_V^H right-orthonormal to machine precision
+// (no division by small singular values).
+__global__ void k_tt_round(int count, const int* __restrict__ n_arr, int d, int left_orth,
+                           const double* __restrict__ tol_arr, const int* __restrict__ maxrank_arr,
+                           cd* __restrict__ tt, const long long* __restrict__ tt_off, int core_stride,
+                           int* __restrict__ ranks_all, cd* __restrict__ scratch,
+                           long long scratch_stride, int* __restrict__ status, int hb) {
+  extern __shared__ double4 smem_raw[];
+  SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
+  __shared__ double red[32];
+  for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
+    const int n = n_arr[inst];
+    const double tol = tol_arr[inst];
+    const int rmax = maxrank_arr[inst];
+    int* r = ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
+    cd* base = tt + tt_off[inst];
+    cd* tmp = scratch + (size_t)blockIdx.x * scratch_stride;
+    int st = 0;
+    if (status && status[inst] != 0) continue;
+    if (left_orth) {
+      for (int s = 0; s + 1 < n; ++s) {
+        const int r0 = r[s], r1 = r[s + 1], r2 = r[s + 2];
+        cd* G = core_ptr(base, core_stride, s);
+        cd* H = core_ptr(base, core_stride, s + 1);
+        const int q = r0 * d;
+        const int kq = min(q, r1);
+        // G (q x r1, row-major) -> W column-major
+        for (int idx = threadIdx.x; idx < q * r1; idx += blockDim.x) {
+          const int i = idx / r1, j = idx - i * r1;
+          sm.W[(size_t)j * q + i] = G[idx];
+        }
+        __syncthreads();
+        qr_inplace(sm.W, q, q, r1, sm.tau);
+        form_q(sm.W, q, q, kq, sm.tau, sm.V, q);
+        // G <- Q (q x kq); H <- R H with R = upper kq x r1 of W
+        for (int idx = threadIdx.x; idx < q * kq; idx += blockDim.x) {
+          const int i = idx / kq, c = idx - i * kq;
+          G[idx] = sm.V[(size_t)c * q + i];
+        }
+        const int cols = d * r2;
+        for (int idx = threadIdx.x; idx < kq * cols; idx += blockDim.x) {
+          const int c = idx / cols, col = idx - c * cols;
+          cd acc = mkc(0.0, 0.0);
+          for (int a = c; a < r1; ++a) acc = cfma(sm.W[(size_t)a * q + c], H[(size_t)a * cols + col], acc);
+          tmp[idx] = acc;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kq * cols; idx += blockDim.x) H[idx] = tmp[idx];
+        if (threadIdx.x == 0) r[s + 1] = kq;
+        __syncthreads();
+      }
+    }
+    // norm of the tensor = norm of the last core (cores before it are left-orthonormal)
+    {
+      cd* G = core_ptr(base, core_stride, n - 1);
+      const double nn = cta_norm2(G, (long long)r[n - 1] * d * r[n], red);
+      const double delta = tol * sqrt(nn) / sqrt((double)max(n - 1, 1));
+      for (int s = n - 1; s >= 1; --s) {
+        const int r0 = r[s], r1 = r[s + 1], rm = r[s - 1];
+        cd* Gs = core_ptr(base, core_stride, s);
+        cd* Gp = core_ptr(base, core_stride, s - 1);
+        const int q = d * r1;
+        // Z = X^H with X = Gs as r0 x (d r1): Z[(sig,b), a] = conj(Gs[a][sig][b])
+        cd* Zt = tmp;
+        cd* Y = tmp + (size_t)q * r0;
+        cd* QV = Y + (size_t)q * r0;
+        for (int idx = threadIdx.x; idx < q * r0; idx += blockDim.x) {
+          const int row = idx / r0, a = idx - row * r0;
+          Zt[idx] = cconj(Gs[(size_t)a * q + row]);
+        }
+        __syncthreads();
+        TsSvd sv = ts_svd(Zt, q, r0, r0, sm.W, SVD_WCAP(hb), sm.V, sm.sig, sm.tau, sm.flag);
+        if (sv.sweeps < 0) st = SFFT_ENOCONV_DEV;
+        int k = trunc_rank(sm.sig, sv.m, delta);
+        if (k > rmax) {
+          st = SFFT_ERANK_DEV;
+          k = rmax;
+        }
+        // Y = Z U_k (q x k), then QR: Y = Q_V R_V
+        gemm_zv(Zt, q, r0, sm.V, k, Y);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < q * k; idx += blockDim.x) {
+          const int i = idx / k, j = idx - i * k;
+          sm.W[(size_t)j * q + i] = Y[idx];
+        }
+        __syncthreads();
+        qr_inplace(sm.W, q, q, k, sm.tau);
+        const int kk = min(q, k);
+        form_q(sm.W, q, q, kk, sm.tau, QV, q);
+        // Gs <- Q_V^H (kk x q)
+        for (int idx = threadIdx.x; idx < kk * q; idx += blockDim.x) {
+          const int c = idx / q, row = idx - c * q;
+          Gs[idx] = cconj(QV[(size_t)c * q + row]);
+        }
+        // T1 = U_k R_V^H (r0 x kk) into Y (free now), then Gp <- Gp T1
+        for (int idx = threadIdx.x; idx < r0 * kk; idx += blockDim.x) {
+          const int a = idx / kk, c = idx - a * kk;
+          cd acc = mkc(0.0, 0.0);
+          // (R_V^H)[j, c] = conj(R_V[c, j]), nonzero for j >= c
+          for (int j = c; j < k; ++j) acc = cfma(sm.V[(size_t)j * r0 + a], cconj(sm.W[(size_t)j * q + c]), acc);
+          Y[idx] = acc;
+        }
+        __syncthreads();
+        const int rows = rm * d;
+        cd* out = QV + (size_t)q * kk;
+        for (int idx = threadIdx.x; idx < rows * kk; idx += blockDim.x) {
+          const int row = idx / kk, c = idx - row * kk;
+          cd acc = mkc(0.0, 0.0);
+          for (int a = 0; a < r0; ++a) acc = cfma(Gp[(size_t)row * r0 + a], Y[(size_t)a * kk + c], acc);
+          out[idx] = acc;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < rows * kk; idx += blockDim.x) Gp[idx] = out[idx];
+        if (threadIdx.x == 0) r[s] = kk;
+        __syncthreads();
+      }
+    }
+    if (threadIdx.x == 0 && status) status[inst] = max(status[inst], st);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4: zip-up MPO x TT contraction (Stoudenmire & White 2010), left to right.
+// ---------------------------------------------------------------------------
+// Carry C (r' x s r) from the previous site is stored as CH = C^H. At site s:
+//   Dt[c][a][lam][b'] = sum_b CH[(a,b), c] conj(A[b][lam][b'])         (= conj D)
+//   Z[(a',b'), (c,mu)] = sum_{a,lam} Dt[c][a][lam][b'] conj(W[a][2mu+lam][a'])
+// so Z = T^H with T = C (W . A) the (r' 2) x (s' r') panel. The right singular
+// vectors V of Z are the left singular vectors of T: V becomes the output core
+// B_s[c][mu][c''] and Z V = T^H V the next carry CH. Singular values below
+// ztol * ||T|| are dropped; the final rounding sweep sets the ranks.
+__global__ void k_zipup(int count, const int* __restrict__ n_arr, const double* __restrict__ tol_arr,
+                        const int* __restrict__ maxrank_arr, const cd* __restrict__ A,
+                        const long long* __restrict__ a_off, const int* __restrict__ a_ranks_all,
+                        const cd* __restrict__ Wmpo, const long long* __restrict__ w_off,
+                        const int* __restrict__ w_ranks_all, cd* __restrict__ B,
+                        const long long* __restrict__ b_off, int* __restrict__ b_ranks_all,
+                        int core_stride_a, int core_stride_w, int core_stride_b,
+                        cd* __restrict__ scratch, long long scratch_stride,
+                        int* __restrict__ status, int hb) {
+  extern __shared__ double4 smem_raw[];
+  SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
+  for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
+    const int n = n_arr[inst];
+    const double ztol = 0.1 * tol_arr[inst] / sqrt((double)max(n - 1, 1));
+    const int rmax = maxrank_arr[inst];
+    const int* ra = a_ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
+    const int* rw = w_ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
+    int* rb = b_ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
+    const cd* Ab = A + a_off[inst];
+    const cd* Wb = Wmpo + w_off[inst];
+    cd* Bb = B + b_off[inst];
+    cd* CH = scratch + (size_t)blockIdx.x * scratch_stride;
+    cd* Dt = CH + SFFT_ZIP_CH_DEV;
+    cd* Z = Dt + SFFT_ZIP_D_DEV;
+    int st = 0;
+    if (status[inst] != 0) continue;
+    if (threadIdx.x == 0) {
+      CH[0] = mkc(1.0, 0.0);
+      rb[0] = 1;
+      rb[n] = 1;
+    }
+    __syncthreads();
+    int rc = 1;
+    for (int s = 0; s < n; ++s) {
+      const int rA0 = ra[s], rA1 = ra[s + 1], s0 = rw[s], s1 = rw[s + 1];
+      const cd* As = Ab + (size_t)s * core_stride_a;
+      const cd* Ws = Wb + (size_t)s * core_stride_w;
+      // Dt
+      const int nd = rc * s0 * 2 * rA1;
+      for (int idx = threadIdx.x; idx < nd; idx += blockDim.x) {
+        int rem = idx;
+        const int bp = rem % rA1; rem /= rA1;
+        const int lam = rem & 1; rem >>= 1;
+        const int a = rem % s0; const int c = rem / s0;
+        cd acc = mkc(0.0, 0.0);
+        for (int b = 0; b < rA0; ++b)
+          acc = cfma(CH[(size_t)(a * rA0 + b) * rc + c], cconj(As[(size_t)b * 2 * rA1 + lam * rA1 + bp]), acc);
+        Dt[idx] = acc;
+      }
+      __syncthreads();
+      const int q = s1 * rA1, p = 2 * rc;
+      for (int idx = threadIdx.x; idx < q * p; idx += blockDim.x) {
+        const int row = idx / p, col = idx - row * p;
+        const int ap = row / rA1, bp = row - ap * rA1;
+        const int c = col >> 1, mu = col & 1;
+        cd acc = mkc(0.0, 0.0);
+        for (int a = 0; a < s0; ++a) {
+#pragma unroll
+          for (int lam = 0; lam < 2; ++lam) {
+            const cd d = Dt[(((size_t)c * s0 + a) * 2 + lam) * rA1 + bp];
+            const cd w = Ws[(size_t)a * 4 * s1 + (2 * mu + lam) * s1 + ap];
+            acc = cfma(d, cconj(w), acc);
+          }
+        }
+        Z[idx] = acc;
+      }
+      __syncthreads();
+      cd* Bs = Bb + (size_t)s * core_stride_b;
+      if (s == n - 1) {
+        // q == 1: B[c][mu][0] = conj(Z[0, (c, mu)])
+        for (int idx = threadIdx.x; idx < p; idx += blockDim.x) Bs[idx] = cconj(Z[idx]);
+        __syncthreads();
+        break;
+      }
+      TsSvd sv = ts_svd(Z, q, p, p, sm.W, SVD_WCAP(hb), sm.V, sm.sig, sm.tau, sm.flag);
+      if (sv.sweeps < 0) st = SFFT_ENOCONV_DEV;
+      double s2 = 0.0;
+      for (int i = 0; i < sv.m; ++i) s2 += sm.sig[i] * sm.sig[i];
+      int k = trunc_rank(sm.sig, sv.m, ztol * sqrt(s2));
+      if (k > SFFT_SLOT_RANK_DEV) {
+        st = SFFT_ERANK_DEV;
+        k = SFFT_SLOT_RANK_DEV;
+      }
+      (void)rmax;
+      // B_s[c][mu][c''] = V[(c, mu), c'']
+      for (int idx = threadIdx.x; idx < p * k; idx += blockDim.x) {
+        const int row = idx / k, cc = idx - row * k;
+        Bs[idx] = sm.V[(size_t)cc * p + row];
+      }
+      gemm_zv(Z, q, p, sm.V, k, CH);
+      if (threadIdx.x == 0) rb[s + 1] = k;
+      __syncthreads();
+      rc = k;
+    }
+    if (threadIdx.x == 0) status[inst] = max(status[inst], st);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K6: readout in bit-reversed site order (Sec. 4.3, Eq. discretization_dft)
+// ---------------------------------------------------------------------------
+// Requested outputs u = l_begin + i*2^t, i < q. Sites 0..t-1 carry the fixed
+// low bits: a row vector v. Sites t..t+h-1 carry the next h bits: a tree of
+// 2^h row vectors v B[...]. Sites t+h..n-1: column vectors R_s[prefix] for the
+// contiguous range of prefixes u >> s, built from the top. Then
+// y_u = Lv[(u >> t) mod 2^h] . R_{t+h}[u >> (t+h)].
+__global__ void k_readout(int count, const InstParams* __restrict__ P, const cd* __restrict__ B,
+                          const long long* __restrict__ b_off, const int* __restrict__ b_ranks_all,
+                          int core_stride, const long long* __restrict__ l_begin,
+                          const int* __restrict__ tbits, const int* __restrict__ qarr,
+                          const long long* __restrict__ out_off, double* __restrict__ prices,
+                          double* __restrict__ logk, const int* __restrict__ status,
+                          cd* __restrict__ scratch, long long scratch_stride) {
+  __shared__ cd Lv[(1 << READOUT_TREE_BITS) * SFFT_SLOT_RANK_DEV];
+  __shared__ cd Lv2[(1 << READOUT_TREE_BITS) * SFFT_SLOT_RANK_DEV];
+  for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
+    const InstParams prm = P[inst];
+    const int n = prm.n;
+    const int* rb = b_ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
+    const cd* Bb = B + b_off[inst];
+    const long long lb = l_begin[inst];
+    const int q = qarr[inst];
+    const int t = min(tbits[inst], n);
+    const long long u_last = lb + ((long long)(q - 1) << tbits[inst]);
+    double* pr = prices + out_off[inst];
+    double* lk = logk + out_off[inst];
+    if (status[inst] != 0 || q <= 0) {
+      for (int i = threadIdx.x; i < q; i += blockDim.x) {
+        pr[i] = __longlong_as_double(0x7ff8000000000000ULL);
+        const long long u = lb + ((long long)i << tbits[inst]);
+        lk[i] = log(prm.S0) + prm.k0 + prm.dk * (double)u;
+      }
+      continue;
+    }
+    const int h = min(READOUT_TREE_BITS, n - t);
+    // 1. fixed low bits
+    if (threadIdx.x == 0) Lv[0] = mkc(1.0, 0.0);
+    __syncthreads();
+    for (int s = 0; s < t; ++s) {
+      const int r0 = rb[s], r1 = rb[s + 1];
+      const int bit = (int)((lb >> s) & 1);
+      const cd* G = Bb + (size_t)s * core_stride;
+      for (int b = threadIdx.x; b < r1; b += blockDim.x) {
+        cd acc = mkc(0.0, 0.0);
+        for (int a = 0; a < r0; ++a) acc = cfma(Lv[a], G[(size_t)a * 2 * r1 + bit * r1 + b], acc);
+        Lv2[b] = acc;
+      }
+      __syncthreads();
+      for (int b = threadIdx.x; b < r1; b += blockDim.x) Lv[b] = Lv2[b];
+      __syncthreads();
+    }
+    // 2. tree over h bits: after level k there are 2^k vectors (index = low k bits)
+    for (int k = 0; k < h; ++k) {
+      const int s = t + k;
+      const int r0 = rb[s], r1 = rb[s + 1];
+      const cd* G = Bb + (size_t)s * core_stride;
+      const int nv = 1 << k;
+      for (int idx = threadIdx.x; idx < 2 * nv * r1; idx += blockDim.x) {
+        const int b = idx % r1;
+        const int cidx = idx / r1;  // new index: old c plus bit k
+        const int c = cidx & (nv - 1), bit = cidx >> k;
+        cd acc = mkc(0.0, 0.0);
+        for (int a = 0; a < r0; ++a) acc = cfma(Lv[c * SFFT_SLOT_RANK_DEV + a], G[(size_t)a * 2 * r1 + bit * r1 + b], acc);
+        Lv2[cidx * SFFT_SLOT_RANK_DEV + b] = acc;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < 2 * nv * SFFT_SLOT_RANK_DEV; idx += blockDim.x) Lv[idx] = Lv2[idx];
+      __syncthreads();
+    }
+    // 3. right vectors for prefixes at sites n-1 .. t+h
+    const int sh = t + h;
+    cd* R0 = scratch + (size_t)blockIdx.x * scratch_stride;
+    const long long rcap = scratch_stride / 2;
+    cd* R1 = R0 + rcap;
+    if (threadIdx.x == 0) R0[0] = mkc(1.0, 0.0);  // R_n[0] = [1]
+    __syncthreads();
+    long long pmin_prev = 0;
+    for (int s = n - 1; s >= sh; --s) {
+      const int r0 = rb[s], r1 = rb[s + 1];
+      const cd* G = Bb + (size_t)s * core_stride;
+      const long long pmin = lb >> s, pmax = u_last >> s;
+      const long long cnt = pmax - pmin + 1;
+      for (long long idx = threadIdx.x; idx < cnt * r0; idx += blockDim.x) {
+        const long long pi = idx / r0;
+        const int a = (int)(idx - pi * r0);
+        const long long pre = pmin + pi;
+        const int bit = (int)(pre & 1);
+        const long long par = (pre >> 1) - pmin_prev;
+        const cd* Rp = R0 + par * r1;
+        cd acc = mkc(0.0, 0.0);
+        for (int b = 0; b < r1; ++b) acc = cfma(G[(size_t)a * 2 * r1 + bit * r1 + b], Rp[b], acc);
+        R1[pi * r0 + a] = acc;
+      }
+      __syncthreads();
+      cd* tmp = R0;
+      R0 = R1;
+      R1 = tmp;
+      pmin_prev = pmin;
+    }
+    // 4. combine and price
+    const int rmid = rb[sh];
+    const long long pbase = (sh < n) ? (lb >> sh) : 0;
+    for (int i = threadIdx.x; i < q; i += blockDim.x) {
+      const long long u = lb + ((long long)i << tbits[inst]);
+      const int c = (int)((u >> t) & ((1 << h) - 1));
+      const long long pi = (sh < n) ? ((u >> sh) - pbase) : 0;
+      cd acc = mkc(0.0, 0.0);
+      for (int a = 0; a < rmid; ++a) acc = cfma(Lv[c * SFFT_SLOT_RANK_DEV + a], R0[pi * rmid + a], acc);
+      double sgn;
+      const double f = price_factor(prm, u, &sgn);
+      pr[i] = prm.S0 * f * sgn * acc.x;
+      lk[i] = log(prm.S0) + prm.k0 + prm.dk * (double)u;
+    }
+    __syncthreads();
+  }
+}

@@ -1,0 +1,268 @@
+"""Python binding of the C ABI in include/sfft.h (ctypes, argument marshalling
+only). Device buffers are torch CUDA tensors; every computation runs in the
+CUDA library. There is no fallback: if libsfft.so is missing or no CUDA device
+is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsfft.so")
+
+c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+SFFT_OK, SFFT_EINVAL, SFFT_EMOMENT, SFFT_ENOMEM, SFFT_ECUDA, SFFT_ERANK, SFFT_ENOCONV, SFFT_ETIMEOUT = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "EMOMENT", "ENOMEM", "ECUDA", "ERANK", "ENOCONV", "ETIMEOUT"]
+MAX_N = 48
+MAX_RANK = 32
+MAX_STRIKES = 65536
+DENSE_MAX_N = 32
+
+
+class SfftProblem(ctypes.Structure):
+    _fields_ = [("model", c_int32), ("quad", c_int32), ("n", c_int32), ("max_rank", c_int32),
+                ("p", c_double * 8), ("S0", c_double), ("r", c_double), ("T", c_double),
+                ("alpha", c_double), ("eta", c_double), ("tol", c_double), ("k0", c_double)]
+
+
+class SfftInfo(ctypes.Structure):
+    _fields_ = [("status", c_int32), ("int_rank", c_int32), ("mpo_rank", c_int32),
+                ("out_rank", c_int32), ("tt_bytes", c_int64)]
+
+
+EXPORTS = {
+    "sfft_create": (c_int32, [ctypes.POINTER(c_void_p), c_int32]),
+    "sfft_destroy": (c_int32, [c_void_p]),
+    "sfft_set_stream": (c_int32, [c_void_p, c_void_p]),
+    "sfft_strike_window": (c_int32, [ctypes.POINTER(SfftProblem), c_double, c_double, c_int32,
+                                     ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
+                                     ctypes.POINTER(c_int32)]),
+    "sfft_price_batch": (c_int32, [c_void_p, ctypes.POINTER(SfftProblem), c_int32,
+                                   ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
+                                   ctypes.POINTER(c_int32), c_void_p, c_void_p,
+                                   ctypes.POINTER(c_int32), ctypes.POINTER(SfftInfo)]),
+    "sfft_dense_price_batch": (c_int32, [c_void_p, ctypes.POINTER(SfftProblem), c_int32,
+                                         ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
+                                         ctypes.POINTER(c_int32), c_void_p, c_void_p,
+                                         ctypes.POINTER(c_int32), ctypes.POINTER(SfftInfo)]),
+    "sfft_sample_integrand": (c_int32, [c_void_p, ctypes.POINTER(SfftProblem), c_void_p, c_int64,
+                                        c_void_p]),
+    "sfft_integrand_tt": (c_int32, [c_void_p, ctypes.POINTER(SfftProblem),
+                                    ctypes.POINTER(c_int32), c_void_p, c_int64]),
+    "sfft_mpo": (c_int32, [c_void_p, c_int32, c_double, ctypes.POINTER(c_int32), c_void_p, c_int64]),
+    "sfft_tt_round": (c_int32, [c_void_p, c_int32, c_int32, ctypes.POINTER(c_int32), c_void_p,
+                                c_double, c_int32, ctypes.POINTER(c_int32), c_void_p, c_int64]),
+    "sfft_tt_apply_qft": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_int32), c_void_p, c_double,
+                                    c_int32, ctypes.POINTER(c_int32), c_void_p, c_int64]),
+    "sfft_status_string": (ctypes.c_char_p, [c_int32]),
+    "sfft_last_error": (ctypes.c_char_p, [c_void_p]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libsfft.so and declare every exported symbol. Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run paper_2607_28435_b300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class SfftError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+def to_c_problem(prob) -> SfftProblem:
+    """Marshal a workloads.Problem (or any object with the same attributes)."""
+    c = SfftProblem()
+    c.model = int(prob.model)
+    c.quad = int(prob.quad)
+    c.n = int(prob.n)
+    c.max_rank = int(getattr(prob, "max_rank", 0))
+    p = list(prob.p) + [0.0] * (8 - len(prob.p))
+    for i in range(8):
+        c.p[i] = float(p[i])
+    c.S0, c.r, c.T, c.alpha = float(prob.S0), float(prob.r), float(prob.T), float(prob.alpha)
+    c.eta, c.tol = float(prob.eta), float(prob.tol)
+    c.k0 = float(getattr(prob, "k0", math.nan))
+    return c
+
+
+def strike_window(prob, lo: float = -1.5, hi: float = 1.5, qmax: int = 4096) -> Tuple[int, int, int]:
+    lib = load_library()
+    lb, st, q = c_int64(), c_int64(), c_int32()
+    cp = to_c_problem(prob)
+    s = lib.sfft_strike_window(ctypes.byref(cp), lo, hi, qmax, ctypes.byref(lb), ctypes.byref(st),
+                               ctypes.byref(q))
+    if s != SFFT_OK:
+        raise SfftError(s, lib.sfft_status_string(s).decode())
+    return lb.value, st.value, q.value
+
+
+def _ptr(t) -> int:
+    return t.data_ptr() if t is not None else 0
+
+
+class Pricer:
+    """One library context on one CUDA device. All device work runs on the
+    torch current stream at call time."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the SFFT pricer needs a CUDA device")
+        self.torch = torch
+        self.lib = load_library()
+        self.device = device
+        h = c_void_p()
+        s = self.lib.sfft_create(ctypes.byref(h), device)
+        if s != SFFT_OK:
+            raise SfftError(s, "sfft_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sfft_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers ------------------------------------------------------------
+    def _stream(self):
+        st = self.torch.cuda.current_stream(self.device).cuda_stream
+        self.lib.sfft_set_stream(self.h, c_void_p(st))
+
+    def _check(self, s: int):
+        if s != SFFT_OK:
+            raise SfftError(s, self.lib.sfft_last_error(self.h).decode())
+
+    def last_error(self) -> str:
+        return self.lib.sfft_last_error(self.h).decode()
+
+    # -- pricing ------------------------------------------------------------
+    def _price(self, fn, problems, strikes, prices=None, log_strikes=None, raise_on_error=True):
+        torch = self.torch
+        cnt = len(problems)
+        arr = (SfftProblem * max(cnt, 1))(*[to_c_problem(p) for p in problems])
+        lb = (c_int64 * max(cnt, 1))(*[int(s[0]) for s in strikes])
+        st = (c_int64 * max(cnt, 1))(*[int(s[1]) for s in strikes])
+        q = (c_int32 * max(cnt, 1))(*[int(s[2]) for s in strikes])
+        tot = sum(int(s[2]) for s in strikes)
+        dev = torch.device("cuda", self.device)
+        if prices is None:
+            prices = torch.empty(max(tot, 1), dtype=torch.float64, device=dev)
+        if log_strikes is None:
+            log_strikes = torch.empty(max(tot, 1), dtype=torch.float64, device=dev)
+        status = (c_int32 * max(cnt, 1))()
+        info = (SfftInfo * max(cnt, 1))()
+        self._stream()
+        s = fn(self.h, arr, cnt, lb, st, q, c_void_p(_ptr(prices)), c_void_p(_ptr(log_strikes)),
+               status, info)
+        if raise_on_error and s not in (SFFT_OK,):
+            self._check(s)
+        return prices[:tot], log_strikes[:tot], [status[i] for i in range(cnt)], \
+            [dict(status=info[i].status, int_rank=info[i].int_rank, mpo_rank=info[i].mpo_rank,
+                  out_rank=info[i].out_rank) for i in range(cnt)]
+
+    def price_batch(self, problems, strikes, prices=None, log_strikes=None, raise_on_error=True):
+        """TT-SFFT prices. strikes: list of (l_begin, stride, q) per problem."""
+        return self._price(self.lib.sfft_price_batch, problems, strikes, prices, log_strikes,
+                           raise_on_error)
+
+    def dense_price_batch(self, problems, strikes, prices=None, log_strikes=None,
+                          raise_on_error=True):
+        """Dense-FFT Carr-Madan baseline prices, same contract."""
+        return self._price(self.lib.sfft_dense_price_batch, problems, strikes, prices, log_strikes,
+                           raise_on_error)
+
+    # -- single steps -------------------------------------------------------
+    def sample_integrand(self, prob, j):
+        torch = self.torch
+        j = j.to(device=torch.device("cuda", self.device), dtype=torch.int64).contiguous()
+        x = torch.empty(j.numel(), dtype=torch.complex128, device=j.device)
+        cp = to_c_problem(prob)
+        self._stream()
+        self._check(self.lib.sfft_sample_integrand(self.h, ctypes.byref(cp), c_void_p(_ptr(j)),
+                                                   j.numel(), c_void_p(_ptr(x))))
+        return x
+
+    def _alloc_cores(self, n, d):
+        cap = n * d * MAX_RANK * MAX_RANK
+        return self.torch.empty(cap, dtype=self.torch.complex128,
+                                device=self.torch.device("cuda", self.device)), cap
+
+    def integrand_tt(self, prob):
+        cores, cap = self._alloc_cores(prob.n, 2)
+        ranks = (c_int32 * (MAX_N + 1))()
+        cp = to_c_problem(prob)
+        self._stream()
+        self._check(self.lib.sfft_integrand_tt(self.h, ctypes.byref(cp), ranks, c_void_p(_ptr(cores)), cap))
+        return unpack(cores, [ranks[i] for i in range(prob.n + 1)], 2)
+
+    def mpo(self, n, tol):
+        cores, cap = self._alloc_cores(n, 4)
+        ranks = (c_int32 * (MAX_N + 1))()
+        self._stream()
+        self._check(self.lib.sfft_mpo(self.h, n, tol, ranks, c_void_p(_ptr(cores)), cap))
+        return unpack(cores, [ranks[i] for i in range(n + 1)], 4)
+
+    def tt_round(self, cores: List, tol: float, max_rank: int = 0):
+        n = len(cores)
+        d = cores[0].shape[1]
+        flat, ranks = pack(cores, self.torch, self.device)
+        out, cap = self._alloc_cores(n, d)
+        rin = (c_int32 * (MAX_N + 1))(*ranks)
+        rout = (c_int32 * (MAX_N + 1))()
+        self._stream()
+        self._check(self.lib.sfft_tt_round(self.h, n, d, rin, c_void_p(_ptr(flat)), tol, max_rank, rout,
+                                           c_void_p(_ptr(out)), cap))
+        return unpack(out, [rout[i] for i in range(n + 1)], d)
+
+    def tt_apply_qft(self, cores: List, tol: float, max_rank: int = 0):
+        n = len(cores)
+        flat, ranks = pack(cores, self.torch, self.device)
+        out, cap = self._alloc_cores(n, 2)
+        rin = (c_int32 * (MAX_N + 1))(*ranks)
+        rout = (c_int32 * (MAX_N + 1))()
+        self._stream()
+        self._check(self.lib.sfft_tt_apply_qft(self.h, n, rin, c_void_p(_ptr(flat)), tol, max_rank, rout,
+                                               c_void_p(_ptr(out)), cap))
+        return unpack(out, [rout[i] for i in range(n + 1)], 2)
+
+
+def unpack(flat, ranks: Sequence[int], d: int):
+    """Packed device cores -> list of host numpy arrays (r0, d, r1)."""
+    host = flat.cpu().numpy()
+    out, o = [], 0
+    for s in range(len(ranks) - 1):
+        sz = ranks[s] * d * ranks[s + 1]
+        out.append(host[o:o + sz].reshape(ranks[s], d, ranks[s + 1]).copy())
+        o += sz
+    return out
+
+
+def pack(cores, torch, device):
+    ranks = [1] + [int(G.shape[2]) for G in cores]
+    flat = np.concatenate([np.asarray(G, dtype=np.complex128).reshape(-1) for G in cores])
+    return torch.from_numpy(flat).to(torch.device("cuda", device)), ranks

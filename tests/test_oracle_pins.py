@@ -361,3 +361,12 @@ def test_mpo_full_index_convention():
         cores = tt.tt_svd(T, 1e-14)
         W = [G.reshape(G.shape[0], 2, 2, G.shape[2]) for G in cores]
         assert np.max(np.abs(tt.mpo_full(W) - Q)) < 1e-12
+
+
+def test_tt_entry_matches_full_contraction():
+    rng = np.random.default_rng(11)
+    n = 7
+    A = rng.standard_normal((2,) * n) + 1j * rng.standard_normal((2,) * n)
+    cores = tt.tt_svd(A, 0.0)
+    for idx in rng.integers(0, 2, size=(20, n)):
+        assert abs(tt.tt_entry(cores, idx) - A[tuple(idx)]) < 1e-12
