@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput of the batched TT-SFFT Carr-Madan pricer on one B300.
+
+Metric: priced strikes per second. A step prices one seeded batch of pricing
+instances (default: 4096 instances, one third each Heston / Merton / Variance-
+Gamma, parameters drawn uniformly from the configured boxes, T in [0.1, 3],
+grid exponent n uniform in 16..34, Simpson quadrature, eta = 0.25, alpha = 1.5,
+tolerance 1e-12, FP64) at up to 4096 strikes each in |log(K/S0)| <= 1.5,
+through the C ABI (sfft_price_batch): integrand TT build, zip-up MPO x TT
+contraction with the cached Q_n operator, rounding and readout.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank prices its own seeded batch (weak scaling, no data
+collectives); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "priced strikes/s at <=1e-6*S0 err: batched TT-SFFT vs dense-FFT Carr-Madan, 1 B300"
+UNIT = "strikes/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--count", type=int, default=4096)
+    ap.add_argument("--no-dense", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def _oracle_task(args):
+    """Price one instance with the CPU oracle (direct sum at its strikes)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import numpy as np
+    from oracle import carr_madan as cm
+    from paper_2607_28435_b300 import workloads as wl
+    prob, (lb, st, q) = args
+    t0 = time.perf_counter()
+    u = wl.strike_set(lb, st, q)
+    cm.prices(prob, u, route="sparse")
+    return q, time.perf_counter() - t0
+
+
+def oracle_sample(pool, problems, strikes, seconds, cores):
+    """Run the oracle on consecutive instances of the batch (skipping those
+    whose integrand support exceeds 2^20 points, where a direct sum would take
+    minutes) until about `seconds` of wall time; returns strikes/s."""
+    from oracle import carr_madan as cm
+    tasks = []
+    skipped = 0
+    for p, s in zip(problems, strikes):
+        if cm.support_limit(p) > (1 << 20):
+            skipped += 1
+            continue
+        tasks.append((p, s))
+        if len(tasks) >= 4 * cores:
+            break
+    t0 = time.perf_counter()
+    done_q = 0
+    done_n = 0
+    it = iter(tasks)
+    while time.perf_counter() - t0 < seconds:
+        chunk = [t for _, t in zip(range(cores), it)]
+        if not chunk:
+            break
+        for q, _ in pool.map(_oracle_task, chunk):
+            done_q += q
+            done_n += 1
+    wall = time.perf_counter() - t0
+    return done_q / wall, done_n, skipped, wall
+
+
+# --------------------------------------------------------------------------- clocks
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+# --------------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank, pool, ncores):
+    import numpy as np
+    import torch
+
+    from paper_2607_28435_b300 import sfft, workloads as wl
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    problems = wl.config3_batch(args.count, seed=wl.CONFIG3_SEED + rank)
+    strikes = [sfft.strike_window(p) for p in problems]
+    total_q = sum(s[2] for s in strikes)
+    pricer = sfft.Pricer(local_rank)
+    fp64_peak = pricer.calibrate_fp64()
+    prices = torch.empty(total_q, dtype=torch.float64, device=dev)
+    logk = torch.empty(total_q, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+
+    status = None
+    for _ in range(max(args.warmup, 0)):
+        _, _, status, _ = pricer.price_batch(problems, strikes, prices, logk, raise_on_error=False)
+    torch.cuda.synchronize()
+
+    # timed region: device-resident outputs, per-step CUDA events, L2 flushed between steps
+    pricer.profile(True)
+    pricer.profile_read(reset=True)
+    clocks = Clocks(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, _, status, info = pricer.price_batch(problems, strikes, prices, logk, raise_on_error=False)
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    prof = pricer.profile_read(reset=True)
+    pricer.profile(False)
+
+    ok = [s == 0 for s in status]
+    q_ok = sum(s[2] for s, o in zip(strikes, ok) if o)
+    tot_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([tot_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_s = float(t.item())
+        qq = torch.tensor([float(q_ok)], device=dev)
+        torch.distributed.all_reduce(qq)
+        q_all = float(qq.item())
+    else:
+        q_all = float(q_ok)
+    value = q_all * args.steps / tot_s
+
+    # end to end: same call, outputs copied to pinned host memory inside the timed region
+    hp = torch.empty(total_q, dtype=torch.float64, pin_memory=True)
+    hk = torch.empty(total_q, dtype=torch.float64, pin_memory=True)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pricer.price_batch(problems, strikes, prices, logk, raise_on_error=False)
+        hp.copy_(prices, non_blocking=True)
+        hk.copy_(logk, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_value = q_all / (sum(e2e_ms) / 1e3 / args.steps)
+    h2d = args.count * (ctypes_sizeof_problem() + 20)
+    d2h = 16 * total_q
+
+    # roofline of the dominant TT kernel (FP64 ALU bound)
+    tt_phases = ["build", "zipup", "round", "readout", "probe"]
+    dom = max(tt_phases, key=lambda k: prof[k]["ms"])
+    dms = prof[dom]["ms"]
+    achieved = prof[dom]["flops"] / (dms * 1e-3) / 1e9 if dms > 0 else 0.0
+    launches = sum(v["launches"] for v in prof.values())
+
+    # dense-FFT baseline on the same batch: one instance per n <= 30 timed,
+    # the batch time assembled from the per-n times
+    dense = None
+    if not args.no_dense and rank == 0:
+        dense = dense_baseline(pricer, problems, strikes, torch, dev)
+
+    cpu = None
+    if pool is not None and rank == 0:
+        rate, n_inst, skipped, wall = oracle_sample(pool, problems, strikes, args.cpu_seconds, ncores)
+        cpu = {"value": rate, "unit": UNIT, "cores": ncores, "kind": "oracle",
+               "sample": f"{n_inst} consecutive instances of the batch at all their strikes "
+                         f"(direct sum over the integrand support, {wall:.1f} s wall; "
+                         f"{skipped} instances with support > 2^20 skipped)"}
+
+    phases = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                  "gflop_per_step": v["flops"] / args.steps / 1e9}
+              for k, v in prof.items() if v["launches"]}
+    ranks_out = [i["out_rank"] for i in info if i["status"] == 0]
+    ranks_int = [i["int_rank"] for i in info if i["status"] == 0]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batched TT-SFFT, {args.count} instances (Heston/Merton/VG), n 16..34",
+                   "instances": args.count, "strikes_per_step": total_q, "priced_per_step": q_ok,
+                   "failed_instances": int(len(ok) - sum(ok)), "tol": 1e-12, "eta": 0.25, "alpha": 1.5,
+                   "window": "|log K/S0| <= 1.5, <= 4096 strikes", "l2": "flushed (256 MB write) between steps",
+                   "max_int_rank": max(ranks_int) if ranks_int else None,
+                   "max_out_rank": max(ranks_out) if ranks_out else None},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches // args.steps,
+        "roofline": {"bound": "alu", "kernel": sfft.PHASE_KERNELS[sfft.PHASE_NAMES.index(dom)],
+                     "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s FP64",
+                     "frac": achieved / fp64_peak if fp64_peak else None, "traffic": None,
+                     "peak_source": "measured FP64 FMA calibration (sfft_calibrate_fp64)"},
+        "phases": phases,
+        "cpu_baseline": cpu,
+        "dense_fft": dense,
+    }
+    pricer.close()
+    return line
+
+
+def ctypes_sizeof_problem():
+    import ctypes
+    from paper_2607_28435_b300 import sfft
+    return ctypes.sizeof(sfft.SfftProblem)
+
+
+def dense_baseline(pricer, problems, strikes, torch, dev):
+    by_n = {}
+    for p, s in zip(problems, strikes):
+        by_n.setdefault(p.n, []).append((p, s))
+    t_n = {}
+    for n in sorted(by_n):
+        if n > 30:
+            continue
+        p, s = by_n[n][0]
+        pr = torch.empty(max(s[2], 1), dtype=torch.float64, device=dev)
+        lk = torch.empty_like(pr)
+        pricer.dense_price_batch([p], [s], pr, lk)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pricer.dense_price_batch([p], [s], pr, lk)
+        e1.record()
+        torch.cuda.synchronize()
+        t_n[n] = e0.elapsed_time(e1) / 1e3
+    if not t_n:
+        return None
+    top = max(t_n)
+    est = 0.0
+    extrapolated = []
+    for n, items in by_n.items():
+        if n in t_n:
+            est += len(items) * t_n[n]
+        else:
+            est += len(items) * t_n[top] * 2.0 ** (n - top) * n / top
+            extrapolated.append(n)
+    q = sum(s[2] for s in strikes)
+    return {"value": q / est, "unit": UNIT, "batch_seconds": est, "measured_n": sorted(t_n),
+            "seconds_per_n": {str(k): v for k, v in sorted(t_n.items())},
+            "extrapolated_n": sorted(extrapolated),
+            "how": "one instance per n timed (CUDA events); batch time = sum_n count_n t_n; "
+                   "n > 30 scaled as M log M from n = 30"}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args, pool, ncores):
+    from paper_2607_28435_b300 import workloads as wl
+    from oracle import carr_madan as cm
+    problems = wl.config3_batch(args.count)
+    strikes = [cm.strike_window(p) for p in problems]
+    rates = []
+    for i in range(args.warmup + args.steps):
+        rate, n_inst, skipped, wall = oracle_sample(pool, problems, strikes,
+                                                     max(3.0, args.cpu_seconds / 3), ncores)
+        if i >= args.warmup:
+            rates.append(rate)
+    value = statistics.mean(rates)
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"batched TT-SFFT, {args.count} instances (Heston/Merton/VG), n 16..34"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                         "sample": f"{n_inst} instances per step (direct sum over the support), "
+                                   f"{skipped} with support > 2^20 skipped"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    ncores = len(os.sched_getaffinity(0))
+    pool = None
+    if rank == 0 and (args.impl == "reference" or not args.no_cpu):
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(ncores)
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, pool, ncores)), flush=True)
+        if pool:
+            pool.close()
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group(backend="nccl")
+    line = run_ours(args, rank, world, local_rank, pool, ncores)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pool:
+        pool.close()
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -187,6 +187,30 @@ sfft_status sfft_tt_apply_qft(sfft_ctx *ctx, int32_t n, const int32_t *in_ranks,
                               const double *in_cores, double tol, int32_t max_rank,
                               int32_t *out_ranks, double *out_cores, int64_t cap);
 
+/* ---- tracing ---- */
+
+/* Phases timed by the profiler (index into the arrays of sfft_profile_read):
+ * 0 support probe, 1 integrand TT build, 2 zip-up MPO x TT, 3 rounding,
+ * 4 readout, 5 MPO build, 6 dense sampling, 7 dense FFT passes,
+ * 8 dense gather. */
+#define SFFT_NPHASES 9
+
+/* Turn per-launch CUDA-event timing and in-kernel algorithmic flop counting
+ * on (on != 0) or off. Off by default; costs one event pair per launch. */
+sfft_status sfft_profile_enable(sfft_ctx *ctx, int32_t on);
+
+/* Read the accumulated per-phase totals since the last reset (host arrays of
+ * SFFT_NPHASES entries each, any may be NULL): device milliseconds, launches,
+ * algorithmic FP64 flops (complex multiply-add = 8), integrand evaluations.
+ * Synchronises the context's stream. reset != 0 clears the totals. */
+sfft_status sfft_profile_read(sfft_ctx *ctx, double *ms, double *flops, double *evals,
+                              int64_t *launches, int32_t reset);
+
+/* Measured FP64 fused multiply-add throughput of the context's device in
+ * GFLOP/s (independent FMA chains over 8 blocks per SM, CUDA-event timed);
+ * the denominator of the FP64 roofline of the TT kernels. */
+sfft_status sfft_calibrate_fp64(sfft_ctx *ctx, double *gflops);
+
 /* Static strings; never NULL. */
 const char *sfft_status_string(sfft_status s);
 const char *sfft_last_error(const sfft_ctx *ctx);

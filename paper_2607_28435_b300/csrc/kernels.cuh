@@ -19,6 +19,11 @@
 #define SFFT_READOUT_SCRATCH (2 * 2112 * SFFT_SLOT_RANK_DEV)
 #define SFFT_MPO_NODES 24                     // Chebyshev nodes of the MPO construction
 
+// profiling phases (index into the flop / evaluation accumulators)
+enum { PH_PROBE = 0, PH_BUILD = 1, PH_ZIPUP = 2, PH_ROUND = 3, PH_READOUT = 4, PH_MPO = 5,
+       PH_DENSE_SAMPLE = 6, PH_DENSE_FFT = 7, PH_DENSE_GATHER = 8 };
+#define SFFT_NPHASE_DEV 9
+
 // status codes (same values as sfft_status)
 #define SFFT_EINVAL_DEV 1
 #define SFFT_ERANK_DEV 5
@@ -29,23 +34,25 @@ __global__ void k_support_probe(const InstParams* P, int count, double probe_tol
                                 int* m_out);
 __global__ void k_integrand_ttsvd(const InstParams* P, const int* m_arr, int count, cd* scratch,
                                   long long scratch_stride, cd* tt, const long long* tt_off,
-                                  int core_stride, int* ranks_all, int* status, int hb);
+                                  int core_stride, int* ranks_all, int* status, int hb, double* acc);
 __global__ void k_mpo_interp(int n, int P, cd* W, int core_stride, int* ranks);
 __global__ void k_tt_round(int count, const int* n_arr, int d, int left_orth, const double* tol_arr,
                            const int* maxrank_arr, cd* tt, const long long* tt_off,
                            int core_stride, int* ranks_all, cd* scratch,
-                           long long scratch_stride, int* status, int hb);
+                           long long scratch_stride, int* status, int hb, double* acc, int phase);
 __global__ void k_zipup(int count, const int* n_arr, const double* tol_arr, const int* maxrank_arr,
                         const cd* A, const long long* a_off, const int* a_ranks_all,
                         const cd* Wmpo, const long long* w_off, const int* w_ranks_all, cd* B,
                         const long long* b_off, int* b_ranks_all, int core_stride_a,
                         int core_stride_w, int core_stride_b, cd* scratch,
-                        long long scratch_stride, int* status, int hb);
+                        long long scratch_stride, int* status, int hb, double* acc);
 __global__ void k_readout(int count, const InstParams* P, const cd* B, const long long* b_off,
                           const int* b_ranks_all, int core_stride, const long long* l_begin,
                           const int* tbits, const int* qarr, const long long* out_off,
                           double* prices, double* logk, const int* status, cd* scratch,
                           long long scratch_stride);
+
+__global__ void k_dfma_peak(double* out, int iters);
 
 // dense-FFT baseline
 __global__ void k_dense_sample(InstParams prm, cd* x, long long M);

@@ -162,7 +162,25 @@ __host__ __device__ inline size_t ts_svd_smem_bytes(int p, int hb) {
 struct TsSvd {
   int m;          // number of singular triplets = min(q, p)
   int sweeps;     // Jacobi sweeps (-1: not converged)
+  double flops;   // algorithmic FP64 flops of this factorisation
 };
+
+// Algorithmic FP64 flop counts (complex multiply-add = 8 real flops).
+__host__ __device__ inline double flops_qr(double h, double p) {
+  double f = 0.0;
+  const double k = h < p ? h : p;
+  for (double i = 0; i < k; i += 1.0) f += 16.0 * (h - i) * (p - i - 1.0) + 10.0 * (h - i);
+  return f;
+}
+__host__ __device__ inline double flops_formq(double h, double kq) {
+  double f = 0.0;
+  for (double i = 0; i < kq; i += 1.0) f += 16.0 * (h - i) * (kq - i);
+  return f;
+}
+__host__ __device__ inline double flops_hestenes(double p, double m, double sweeps) {
+  return sweeps * 0.5 * m * (m - 1.0) * 26.0 * p;
+}
+__host__ __device__ inline double flops_gemm(double m, double n, double k) { return 8.0 * m * n * k; }
 
 // Right singular vectors of a tall-skinny Z (q x p, row-major, leading dim
 // ldz, read only; any address space). Streaming Householder QR over row blocks
@@ -207,6 +225,18 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
   TsSvd out;
   out.m = m;
   out.sweeps = hestenes(V, p, p, m, 60, sh_flag);
+  {
+    // QR of the stacked row blocks, Jacobi sweeps, norms and sort
+    double f = 0.0;
+    long long rows = q, carried = 0;
+    while (rows > 0) {
+      const long long b = rows < hb ? rows : hb;
+      f += flops_qr((double)(carried + b), (double)p);
+      carried = carried + b < p ? carried + b : p;
+      rows -= b;
+    }
+    out.flops = f + flops_hestenes(p, m, out.sweeps < 0 ? 60 : out.sweeps) + 4.0 * p * m;
+  }
   // column norms
   double* nrm = reinterpret_cast<double*>(W);  // W is free now
   for (int c = warp_id(); c < m; c += n_warps()) {

@@ -59,7 +59,13 @@ struct sfft_ctx {
   std::deque<MpoEntry> mpos;  // stable addresses across push_back
   // batch workspaces (grow only)
   std::map<std::string, DevBuf> bufs;
-  std::vector<char> pinned_dummy;
+  // profiling: CUDA events around every launch, per phase
+  bool prof = false;
+  double* prof_acc = nullptr;  // device: flops[NPHASE], evals[NPHASE]
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;
+  double prof_ms[SFFT_NPHASE_DEV] = {0};
+  long long prof_launches[SFFT_NPHASE_DEV] = {0};
 };
 
 namespace {
@@ -107,6 +113,39 @@ sfft_status ensure(sfft_ctx* ctx, const char* name, size_t bytes, void** out) {
 }
 
 bool finite(double x) { return isfinite(x) != 0; }
+
+cudaEvent_t take_event(sfft_ctx* ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Records a CUDA event pair around one launch when profiling is on.
+struct PhaseScope {
+  sfft_ctx* ctx;
+  int phase;
+  cudaEvent_t a = nullptr;
+  PhaseScope(sfft_ctx* c, int ph) : ctx(c), phase(ph) {
+    if (ctx->prof) {
+      a = take_event(ctx);
+      cudaEventRecord(a, ctx->stream);
+    }
+  }
+  ~PhaseScope() {
+    if (ctx->prof && a) {
+      cudaEvent_t b = take_event(ctx);
+      cudaEventRecord(b, ctx->stream);
+      ctx->ev_open.push_back({phase, {a, b}});
+    }
+  }
+};
+
+double* acc_ptr(sfft_ctx* ctx) { return ctx->prof ? ctx->prof_acc : nullptr; }
 
 // Andersen-Piterbarg moment-explosion time of E[S_T^p] under Heston.
 double heston_explosion_time(double kappa, double sv, double rho, double p) {
@@ -269,7 +308,10 @@ sfft_status get_mpo(sfft_ctx* ctx, int n, double tol, const MpoEntry** out) {
   e.off = slot * idx;
   cd* W = reinterpret_cast<cd*>(ctx->mpo_pool.p) + e.off;
   int* rk = reinterpret_cast<int*>(ctx->mpo_ranks_dev.p) + (SFFT_MAX_N + 1) * idx;
-  k_mpo_interp<<<n, kThreads, 0, ctx->stream>>>(n, SFFT_MPO_NODES, W, SFFT_CORE_STRIDE_D4, rk);
+  {
+    PhaseScope ps(ctx, PH_MPO);
+    k_mpo_interp<<<n, kThreads, 0, ctx->stream>>>(n, SFFT_MPO_NODES, W, SFFT_CORE_STRIDE_D4, rk);
+  }
   CK(cudaGetLastError());
   // round: one instance, d = 4, with left orthogonalisation
   struct H {
@@ -289,10 +331,13 @@ sfft_status get_mpo(sfft_ctx* ctx, int n, double tol, const MpoEntry** out) {
   void* scr;
   s = ensure(ctx, "mpo_scratch", sizeof(cd) * SFFT_ROUND_SCRATCH, &scr);
   if (s) return s;
-  k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(
-      1, reinterpret_cast<int*>(a), 4, 1, reinterpret_cast<double*>(a + 8),
-      reinterpret_cast<int*>(a + 16), W, reinterpret_cast<long long*>(a + 24), SFFT_CORE_STRIDE_D4,
-      rk, reinterpret_cast<cd*>(scr), SFFT_ROUND_SCRATCH, nullptr, kHb);
+  {
+    PhaseScope ps(ctx, PH_MPO);
+    k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(
+        1, reinterpret_cast<int*>(a), 4, 1, reinterpret_cast<double*>(a + 8),
+        reinterpret_cast<int*>(a + 16), W, reinterpret_cast<long long*>(a + 24), SFFT_CORE_STRIDE_D4,
+        rk, reinterpret_cast<cd*>(scr), SFFT_ROUND_SCRATCH, nullptr, kHb, acc_ptr(ctx), PH_MPO);
+  }
   CK(cudaGetLastError());
   e.ranks.resize(SFFT_MAX_N + 1);
   CK(cudaMemcpyAsync(e.ranks.data(), rk, sizeof(int) * (SFFT_MAX_N + 1), cudaMemcpyDeviceToHost,
@@ -378,7 +423,10 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   int* m_dev;
   if ((s = ensure(ctx, "m_arr", sizeof(int) * cnt, &p))) return s;
   m_dev = reinterpret_cast<int*>(p);
-  k_support_probe<<<cnt, 64, 0, ctx->stream>>>(b.P, cnt, 1e-2, 4, m_dev);
+  {
+    PhaseScope ps(ctx, PH_PROBE);
+    k_support_probe<<<cnt, 64, 0, ctx->stream>>>(b.P, cnt, 1e-2, 4, m_dev);
+  }
   CK(cudaGetLastError());
   std::vector<int> m_host(cnt), st_host(cnt, 0);
   CK(cudaMemcpyAsync(m_host.data(), m_dev, sizeof(int) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
@@ -399,9 +447,12 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   int grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem));
   const long long sstride = 2LL << mmax;
   if ((s = ensure(ctx, "build_scratch", sizeof(cd) * sstride * grid, &p))) return s;
-  k_integrand_ttsvd<<<grid, kThreads, smem, ctx->stream>>>(b.P, m_dev, cnt, reinterpret_cast<cd*>(p),
-                                                           sstride, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
-                                                           b.a_ranks, b.status, kHb);
+  {
+    PhaseScope ps(ctx, PH_BUILD);
+    k_integrand_ttsvd<<<grid, kThreads, smem, ctx->stream>>>(
+        b.P, m_dev, cnt, reinterpret_cast<cd*>(p), sstride, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
+        b.a_ranks, b.status, kHb, acc_ptr(ctx));
+  }
   CK(cudaGetLastError());
   if (!apply) return SFFT_OK;
 
@@ -418,18 +469,24 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
                      ctx->stream));
   grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, smem));
   if ((s = ensure(ctx, "zip_scratch", sizeof(cd) * (size_t)SFFT_ZIP_SCRATCH * grid, &p))) return s;
-  k_zipup<<<grid, kThreads, smem, ctx->stream>>>(
-      cnt, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
-      reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
-      SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
-      SFFT_ZIP_SCRATCH, b.status, kHb);
+  {
+    PhaseScope ps(ctx, PH_ZIPUP);
+    k_zipup<<<grid, kThreads, smem, ctx->stream>>>(
+        cnt, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
+        reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
+        SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
+        SFFT_ZIP_SCRATCH, b.status, kHb, acc_ptr(ctx));
+  }
   CK(cudaGetLastError());
   grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, smem));
   if ((s = ensure(ctx, "round_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * grid, &p))) return s;
-  k_tt_round<<<grid, kThreads, smem, ctx->stream>>>(cnt, b.n_arr, 2, 0, b.tol_arr, b.maxr_arr, b.B,
-                                                    b.a_off, SFFT_CORE_STRIDE_D2, b.b_ranks,
-                                                    reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH,
-                                                    b.status, kHb);
+  {
+    PhaseScope ps(ctx, PH_ROUND);
+    k_tt_round<<<grid, kThreads, smem, ctx->stream>>>(cnt, b.n_arr, 2, 0, b.tol_arr, b.maxr_arr, b.B,
+                                                      b.a_off, SFFT_CORE_STRIDE_D2, b.b_ranks,
+                                                      reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH,
+                                                      b.status, kHb, acc_ptr(ctx), PH_ROUND);
+  }
   CK(cudaGetLastError());
   return SFFT_OK;
 }
@@ -576,6 +633,12 @@ sfft_status sfft_destroy(sfft_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   for (auto& kv : ctx->bufs) kv.second.release();
+  for (auto& e : ctx->ev_open) {
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->prof_acc) cudaFree(ctx->prof_acc);
   ctx->mpo_pool.release();
   ctx->mpo_ranks_dev.release();
   delete ctx;
@@ -695,7 +758,7 @@ sfft_status sfft_tt_round(sfft_ctx* ctx, int32_t n, int32_t d, const int32_t* in
   if ((s = ensure(ctx, "rt_scratch", sizeof(cd) * SFFT_ROUND_SCRATCH, &scr))) return s;
   k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(1, nd, d, 1, td, md, T, od, stride,
                                                       reinterpret_cast<int*>(rd), reinterpret_cast<cd*>(scr),
-                                                      SFFT_ROUND_SCRATCH, sd, kHb);
+                                                      SFFT_ROUND_SCRATCH, sd, kHb, nullptr, PH_ROUND);
   CK(cudaGetLastError());
   int st = 0;
   CK(cudaMemcpyAsync(&st, sd, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -744,11 +807,12 @@ sfft_status sfft_tt_apply_qft(sfft_ctx* ctx, int32_t n, const int32_t* in_ranks,
   k_zipup<<<1, kThreads, svd_smem(), ctx->stream>>>(
       1, nd, td, md, A, od, reinterpret_cast<int*>(ra), reinterpret_cast<const cd*>(ctx->mpo_pool.p), wd,
       reinterpret_cast<int*>(rw), B, od, reinterpret_cast<int*>(rb), SFFT_CORE_STRIDE_D2,
-      SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(scr), SFFT_ZIP_SCRATCH, sd, kHb);
+      SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(scr), SFFT_ZIP_SCRATCH, sd, kHb,
+      nullptr);
   CK(cudaGetLastError());
   k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(1, nd, 2, 0, td, md, B, od, SFFT_CORE_STRIDE_D2,
                                                       reinterpret_cast<int*>(rb), reinterpret_cast<cd*>(scr),
-                                                      SFFT_ROUND_SCRATCH, sd, kHb);
+                                                      SFFT_ROUND_SCRATCH, sd, kHb, nullptr, PH_ROUND);
   CK(cudaGetLastError());
   int st = 0;
   CK(cudaMemcpyAsync(&st, sd, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -825,7 +889,10 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
       const InstParams& P = prm[k];
       const long long M = 1LL << P.n;
       cd* x = reinterpret_cast<cd*>(xb);
-      k_dense_sample<<<ctx->num_sms * 8, kThreads, 0, ctx->stream>>>(P, x, M);
+      {
+        PhaseScope ps(ctx, PH_DENSE_SAMPLE);
+        k_dense_sample<<<ctx->num_sms * 8, kThreads, 0, ctx->stream>>>(P, x, M);
+      }
       CK(cudaGetLastError());
       const int npass = (P.n + 7) / 8;
       std::vector<int> dig(npass);
@@ -842,12 +909,16 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
         const size_t smem = sizeof(cd) * ((size_t)(1 << R) * cols + (1 << R));
         const long long nblk = (M / L) * (Lp / cols);
         const int grid = (int)std::min<long long>(nblk, (long long)ctx->num_sms * 8);
-        k_fft_pass<<<grid, kThreads, smem, ctx->stream>>>(x, M, Lp, R, cols);
+        {
+          PhaseScope ps(ctx, PH_DENSE_FFT);
+          k_fft_pass<<<grid, kThreads, smem, ctx->stream>>>(x, M, Lp, R, cols);
+        }
         CK(cudaGetLastError());
         L = Lp;
       }
       CK(cudaMemcpyAsync(dg, dig.data(), sizeof(int) * npass, cudaMemcpyHostToDevice, ctx->stream));
       if (q_v[k] > 0) {
+        PhaseScope ps(ctx, PH_DENSE_GATHER);
         k_dense_gather<<<(q_v[k] + kThreads - 1) / kThreads, kThreads, 0, ctx->stream>>>(
             P, x, P.n, reinterpret_cast<int*>(dg), npass, lb_v[k], tb_v[k], q_v[k], prices + off_v[k],
             log_strikes + off_v[k]);
@@ -871,11 +942,80 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
   void* p;
   const int grid = std::min(cnt, ctx->num_sms * 4);
   if ((s = ensure(ctx, "readout_scratch", sizeof(cd) * (size_t)SFFT_READOUT_SCRATCH * grid, &p))) return s;
-  k_readout<<<grid, kThreads, 0, ctx->stream>>>(cnt, b.P, b.B, b.a_off, b.b_ranks, SFFT_CORE_STRIDE_D2,
-                                                lb_d, tb_d, q_d, off_d, prices, log_strikes, b.status,
-                                                reinterpret_cast<cd*>(p), SFFT_READOUT_SCRATCH);
+  {
+    PhaseScope ps(ctx, PH_READOUT);
+    k_readout<<<grid, kThreads, 0, ctx->stream>>>(cnt, b.P, b.B, b.a_off, b.b_ranks, SFFT_CORE_STRIDE_D2,
+                                                  lb_d, tb_d, q_d, off_d, prices, log_strikes, b.status,
+                                                  reinterpret_cast<cd*>(p), SFFT_READOUT_SCRATCH);
+  }
   CK(cudaGetLastError());
   return finish_status(ctx, count, valid, host_status, b.status, inst_status, info, &b, &mp);
+}
+
+sfft_status sfft_calibrate_fp64(sfft_ctx* ctx, double* gflops) {
+  if (!ctx || !gflops) return SFFT_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  void* p;
+  sfft_status s = ensure(ctx, "calib", 64, &p);
+  if (s) return s;
+  const int grid = ctx->num_sms * 8, iters = 1 << 14;
+  cudaEvent_t a = take_event(ctx), b = take_event(ctx);
+  k_dfma_peak<<<grid, kThreads, 0, ctx->stream>>>(reinterpret_cast<double*>(p), 256);  // warm-up
+  CK(cudaEventRecord(a, ctx->stream));
+  k_dfma_peak<<<grid, kThreads, 0, ctx->stream>>>(reinterpret_cast<double*>(p), iters);
+  CK(cudaEventRecord(b, ctx->stream));
+  CK(cudaGetLastError());
+  CK(cudaEventSynchronize(b));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, a, b));
+  ctx->ev_pool.push_back(a);
+  ctx->ev_pool.push_back(b);
+  *gflops = 16.0 * iters * (double)grid * kThreads / (ms * 1e-3) / 1e9;
+  return SFFT_OK;
+}
+
+sfft_status sfft_profile_enable(sfft_ctx* ctx, int32_t on) {
+  if (!ctx) return SFFT_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  if (on && !ctx->prof_acc) {
+    CK(cudaMalloc(reinterpret_cast<void**>(&ctx->prof_acc), sizeof(double) * 2 * SFFT_NPHASE_DEV));
+    CK(cudaMemset(ctx->prof_acc, 0, sizeof(double) * 2 * SFFT_NPHASE_DEV));
+  }
+  ctx->prof = on != 0;
+  return SFFT_OK;
+}
+
+sfft_status sfft_profile_read(sfft_ctx* ctx, double* ms, double* flops, double* evals,
+                              int64_t* launches, int32_t reset) {
+  if (!ctx) return SFFT_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (auto& e : ctx->ev_open) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, e.second.first, e.second.second));
+    ctx->prof_ms[e.first] += t;
+    ctx->prof_launches[e.first] += 1;
+    ctx->ev_pool.push_back(e.second.first);
+    ctx->ev_pool.push_back(e.second.second);
+  }
+  ctx->ev_open.clear();
+  double host[2 * SFFT_NPHASE_DEV] = {0};
+  if (ctx->prof_acc)
+    CK(cudaMemcpy(host, ctx->prof_acc, sizeof host, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < SFFT_NPHASE_DEV; ++i) {
+    if (ms) ms[i] = ctx->prof_ms[i];
+    if (launches) launches[i] = ctx->prof_launches[i];
+    if (flops) flops[i] = host[i];
+    if (evals) evals[i] = host[SFFT_NPHASE_DEV + i];
+  }
+  if (reset) {
+    for (int i = 0; i < SFFT_NPHASE_DEV; ++i) {
+      ctx->prof_ms[i] = 0.0;
+      ctx->prof_launches[i] = 0;
+    }
+    if (ctx->prof_acc) CK(cudaMemset(ctx->prof_acc, 0, sizeof(double) * 2 * SFFT_NPHASE_DEV));
+  }
+  return SFFT_OK;
 }
 
 sfft_status sfft_price_batch(sfft_ctx* ctx, const sfft_problem* probs, int32_t count, const int64_t* l_begin,

@@ -152,9 +152,10 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* _
                                   int count, cd* __restrict__ scratch, long long scratch_stride,
                                   cd* __restrict__ tt, const long long* __restrict__ tt_off,
                                   int core_stride, int* __restrict__ ranks_all,
-                                  int* __restrict__ status, int hb) {
+                                  int* __restrict__ status, int hb, double* __restrict__ acc) {
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
+  double fl = 0.0, evals = 0.0;
   for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
     const InstParams prm = P[inst];
     const int n = prm.n;
@@ -168,6 +169,7 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* _
     const long long Mb = 1LL << m;
     for (long long j = threadIdx.x; j < Mb; j += blockDim.x) bufA[j] = integrand(prm, j);
     __syncthreads();
+    evals += (double)Mb;
     int st = 0;
     cd* Z = bufA;
     cd* O = bufB;
@@ -211,6 +213,7 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* _
       }
       gemm_zv(Z, q, p, sm.V, k, O);
       __syncthreads();
+      fl += sv.flops + flops_gemm((double)q, p, k);
       cd* tmp = Z;
       Z = O;
       O = tmp;
@@ -232,6 +235,10 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* _
       status[inst] = st;
     }
     __syncthreads();
+  }
+  if (acc && threadIdx.x == 0) {
+    atomicAdd(acc + PH_BUILD, fl);
+    atomicAdd(acc + SFFT_NPHASE_DEV + PH_BUILD, evals);
   }
 }
 
@@ -313,10 +320,12 @@ __global__ void k_tt_round(int count, const int* __restrict__ n_arr, int d, int 
                            const double* __restrict__ tol_arr, const int* __restrict__ maxrank_arr,
                            cd* __restrict__ tt, const long long* __restrict__ tt_off, int core_stride,
                            int* __restrict__ ranks_all, cd* __restrict__ scratch,
-                           long long scratch_stride, int* __restrict__ status, int hb) {
+                           long long scratch_stride, int* __restrict__ status, int hb,
+                           double* __restrict__ acc, int phase) {
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
   __shared__ double red[32];
+  double fl = 0.0;
   for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
     const int n = n_arr[inst];
     const double tol = tol_arr[inst];
@@ -357,6 +366,7 @@ __global__ void k_tt_round(int count, const int* __restrict__ n_arr, int d, int 
         for (int idx = threadIdx.x; idx < kq * cols; idx += blockDim.x) H[idx] = tmp[idx];
         if (threadIdx.x == 0) r[s + 1] = kq;
         __syncthreads();
+        fl += flops_qr(q, r1) + flops_formq(q, kq) + flops_gemm(kq, cols, r1);
       }
     }
     // norm of the tensor = norm of the last core (cores before it are left-orthonormal)
@@ -422,11 +432,14 @@ __global__ void k_tt_round(int count, const int* __restrict__ n_arr, int d, int 
         for (int idx = threadIdx.x; idx < rows * kk; idx += blockDim.x) Gp[idx] = out[idx];
         if (threadIdx.x == 0) r[s] = kk;
         __syncthreads();
+        fl += sv.flops + flops_gemm(q, r0, k) + flops_qr(q, k) + flops_formq(q, kk) +
+              flops_gemm(r0, kk, k) + flops_gemm(rows, kk, r0);
       }
     }
     if (threadIdx.x == 0 && status) status[inst] = max(status[inst], st);
     __syncthreads();
   }
+  if (acc && threadIdx.x == 0) atomicAdd(acc + phase, fl);
 }
 
 // ---------------------------------------------------------------------------
@@ -447,9 +460,10 @@ __global__ void k_zipup(int count, const int* __restrict__ n_arr, const double* 
                         const long long* __restrict__ b_off, int* __restrict__ b_ranks_all,
                         int core_stride_a, int core_stride_w, int core_stride_b,
                         cd* __restrict__ scratch, long long scratch_stride,
-                        int* __restrict__ status, int hb) {
+                        int* __restrict__ status, int hb, double* __restrict__ acc) {
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
+  double fl = 0.0;
   for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
     const int n = n_arr[inst];
     const double ztol = 0.1 * tol_arr[inst] / sqrt((double)max(n - 1, 1));
@@ -506,6 +520,7 @@ __global__ void k_zipup(int count, const int* __restrict__ n_arr, const double* 
         Z[idx] = acc;
       }
       __syncthreads();
+      fl += flops_gemm(nd, rA0, 1) + flops_gemm((double)q * p, 2.0 * s0, 1);
       cd* Bs = Bb + (size_t)s * core_stride_b;
       if (s == n - 1) {
         // q == 1: B[c][mu][0] = conj(Z[0, (c, mu)])
@@ -531,11 +546,13 @@ __global__ void k_zipup(int count, const int* __restrict__ n_arr, const double* 
       gemm_zv(Z, q, p, sm.V, k, CH);
       if (threadIdx.x == 0) rb[s + 1] = k;
       __syncthreads();
+      fl += sv.flops + flops_gemm(q, p, k);
       rc = k;
     }
     if (threadIdx.x == 0) status[inst] = max(status[inst], st);
     __syncthreads();
   }
+  if (acc && threadIdx.x == 0) atomicAdd(acc + PH_ZIPUP, fl);
 }
 
 // ---------------------------------------------------------------------------

@@ -20,6 +20,11 @@ c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_
 SFFT_OK, SFFT_EINVAL, SFFT_EMOMENT, SFFT_ENOMEM, SFFT_ECUDA, SFFT_ERANK, SFFT_ENOCONV, SFFT_ETIMEOUT = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "EMOMENT", "ENOMEM", "ECUDA", "ERANK", "ENOCONV", "ETIMEOUT"]
 MAX_N = 48
+NPHASES = 9
+PHASE_NAMES = ["probe", "build", "zipup", "round", "readout", "mpo", "dense_sample", "dense_fft",
+               "dense_gather"]
+PHASE_KERNELS = ["k_support_probe", "k_integrand_ttsvd", "k_zipup", "k_tt_round", "k_readout",
+                 "k_mpo_interp+k_tt_round", "k_dense_sample", "k_fft_pass", "k_dense_gather"]
 MAX_RANK = 32
 MAX_STRIKES = 65536
 DENSE_MAX_N = 32
@@ -60,6 +65,10 @@ EXPORTS = {
                                 c_double, c_int32, ctypes.POINTER(c_int32), c_void_p, c_int64]),
     "sfft_tt_apply_qft": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_int32), c_void_p, c_double,
                                     c_int32, ctypes.POINTER(c_int32), c_void_p, c_int64]),
+    "sfft_profile_enable": (c_int32, [c_void_p, c_int32]),
+    "sfft_profile_read": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
+                                    ctypes.POINTER(c_double), ctypes.POINTER(c_int64), c_int32]),
+    "sfft_calibrate_fp64": (c_int32, [c_void_p, ctypes.POINTER(c_double)]),
     "sfft_status_string": (ctypes.c_char_p, [c_int32]),
     "sfft_last_error": (ctypes.c_char_p, [c_void_p]),
 }
@@ -156,6 +165,24 @@ class Pricer:
     def _check(self, s: int):
         if s != SFFT_OK:
             raise SfftError(s, self.lib.sfft_last_error(self.h).decode())
+
+    def profile(self, on: bool = True):
+        self._check(self.lib.sfft_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self, reset: bool = True):
+        ms = (c_double * NPHASES)()
+        fl = (c_double * NPHASES)()
+        ev = (c_double * NPHASES)()
+        ln = (c_int64 * NPHASES)()
+        self._check(self.lib.sfft_profile_read(self.h, ms, fl, ev, ln, 1 if reset else 0))
+        return {PHASE_NAMES[i]: dict(ms=ms[i], flops=fl[i], evals=ev[i], launches=ln[i])
+                for i in range(NPHASES)}
+
+    def calibrate_fp64(self) -> float:
+        g = c_double()
+        self._stream()
+        self._check(self.lib.sfft_calibrate_fp64(self.h, ctypes.byref(g)))
+        return g.value
 
     def last_error(self) -> str:
         return self.lib.sfft_last_error(self.h).decode()
