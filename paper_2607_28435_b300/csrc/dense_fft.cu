@@ -11,7 +11,7 @@
 // (least significant first).
 #include "kernels.cuh"
 
-__global__ void k_dense_sample(InstParams prm, cd* __restrict__ x, long long M) {
+__global__ void k_dense_sample(InstParams prm, cd* x, long long M) {
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < M;
        j += (long long)gridDim.x * blockDim.x)
     x[j] = integrand(prm, j);
@@ -24,7 +24,7 @@ __device__ __forceinline__ cd unit_root(long long t, long long L) {
   return mkc(cs, -sn);
 }
 
-__global__ void k_fft_pass(cd* __restrict__ x, long long M, long long Lp, int R, int cols) {
+__global__ void k_fft_pass(cd* x, long long M, long long Lp, int R, int cols) {
   extern __shared__ double4 smem_raw[];
   cd* sm = reinterpret_cast<cd*>(smem_raw);
   const int Rn = 1 << R;
@@ -67,10 +67,10 @@ __global__ void k_fft_pass(cd* __restrict__ x, long long M, long long Lp, int R,
   }
 }
 
-__global__ void k_dense_gather(InstParams prm, const cd* __restrict__ y, int n,
-                               const int* __restrict__ digits, int ndig, long long l_begin,
-                               int tbits, int q, double* __restrict__ prices,
-                               double* __restrict__ logk) {
+__global__ void k_dense_gather(InstParams prm, const cd* y, int n,
+                               const int* digits, int ndig, long long l_begin,
+                               int tbits, int q, double* prices,
+                               double* logk) {
   const double inv_sqM = 1.0 / (ldexp(1.0, n / 2) * ((n & 1) ? 1.4142135623730951 : 1.0));
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < q; i += gridDim.x * blockDim.x) {
     const long long u = l_begin + ((long long)i << tbits);

@@ -33,8 +33,11 @@ static __device__ void qr_inplace(cd* W, int ld, int h, int p, cd* taus) {
       double s = 0.0;
       for (int i = k + 1 + lane; i < h; i += 32) s += cabs2(col[i]);
       s = warp_sum(s);
-      const cd a0 = col[k];
-      __syncwarp();  // every lane has read the pivot before lane 0 rewrites it
+      // the pivot is read by lane 0 only and broadcast, so lane 0 may
+      // overwrite it below without racing the other lanes
+      cd a0 = (lane == 0) ? col[k] : mkc(0.0, 0.0);
+      a0.x = __shfl_sync(0xffffffffu, a0.x, 0);
+      a0.y = __shfl_sync(0xffffffffu, a0.y, 0);
       cd tau = mkc(0.0, 0.0);
       if (!(s == 0.0 && a0.y == 0.0)) {
         const double beta = -copysign(sqrt(a0.x * a0.x + a0.y * a0.y + s), a0.x);
@@ -83,7 +86,6 @@ static __device__ void form_q(const cd* W, int ld, int h, int kq, const cd* taus
         for (int i = k + 1 + lane; i < h; i += 32) dot = cfmac(v[i], qj[i], dot);
         dot = warp_csum(dot);
         const cd f = cmul(tau, dot);
-        __syncwarp();
         if (lane == 0) qj[k] = csub(qj[k], f);
         for (int i = k + 1 + lane; i < h; i += 32) qj[i] = csub(qj[i], cmul(v[i], f));
       }

@@ -81,8 +81,8 @@ __device__ double cta_norm2(const cd* x, long long len, double* red) {
 // ---------------------------------------------------------------------------
 // K1: integrand samples at listed indices
 // ---------------------------------------------------------------------------
-__global__ void k_sample(const InstParams* __restrict__ P, const long long* __restrict__ j,
-                         long long count, cd* __restrict__ x) {
+__global__ void k_sample(const InstParams* __restrict__ P, const long long* j,
+                         long long count, cd* x) {
   const InstParams prm = *P;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x)
@@ -95,7 +95,7 @@ __global__ void k_sample(const InstParams* __restrict__ P, const long long* __re
 // probe at or beyond 2^m has |x_j| * j <= probe_tol * max |x|.
 // ---------------------------------------------------------------------------
 __global__ void k_support_probe(const InstParams* __restrict__ P, int count, double probe_factor,
-                                int m_min, int* __restrict__ m_out) {
+                                int m_min, int* m_out) {
   const int inst = blockIdx.x;
   if (inst >= count) return;
   const InstParams prm = P[inst];
@@ -148,11 +148,11 @@ __global__ void k_support_probe(const InstParams* __restrict__ P, int count, dou
 // (lambda, rank)) is factorised Z = U S V^H; V^H becomes core n-1-t and Z V
 // the next carry. Sites above the block (Simpson grid, m < n) hold the
 // rank-one core delta_{lambda,0}.
-__global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* __restrict__ m_arr,
-                                  int count, cd* __restrict__ scratch, long long scratch_stride,
-                                  cd* __restrict__ tt, const long long* __restrict__ tt_off,
-                                  int core_stride, int* __restrict__ ranks_all,
-                                  int* __restrict__ status, int hb, double* __restrict__ acc) {
+__global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m_arr,
+                                  int count, cd* scratch, long long scratch_stride,
+                                  cd* tt, const long long* tt_off,
+                                  int core_stride, int* ranks_all,
+                                  int* status, int hb, double* acc) {
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
   double fl = 0.0, evals = 0.0;
@@ -273,8 +273,8 @@ __device__ double lagrange(int p, double x, int P) {
   return num / den;
 }
 
-__global__ void k_mpo_interp(int n, int P, cd* __restrict__ W, int core_stride,
-                             int* __restrict__ ranks) {
+__global__ void k_mpo_interp(int n, int P, cd* W, int core_stride,
+                             int* ranks) {
   const double s2 = 0.70710678118654752;
   for (int s = blockIdx.x; s < n; s += gridDim.x) {
     const int r0 = (s == 0) ? 1 : P;
@@ -316,21 +316,27 @@ __global__ void k_mpo_interp(int n, int P, cd* __restrict__ W, int core_stride,
 // re-orthonormalised by QR, Y = Q_V R_V, so that X ~= (U_k R_V^H) Q_V^H exactly
 // up to the truncation, with Q_V^H right-orthonormal to machine precision
 // (no division by small singular values).
-__global__ void k_tt_round(int count, const int* __restrict__ n_arr, int d, int left_orth,
-                           const double* __restrict__ tol_arr, const int* __restrict__ maxrank_arr,
-                           cd* __restrict__ tt, const long long* __restrict__ tt_off, int core_stride,
-                           int* __restrict__ ranks_all, cd* __restrict__ scratch,
-                           long long scratch_stride, int* __restrict__ status, int hb,
-                           double* __restrict__ acc, int phase) {
+__global__ void k_tt_round(int count, const int* n_arr, int d, int left_orth,
+                           const double* tol_arr, const int* maxrank_arr,
+                           cd* tt, const long long* tt_off, int core_stride,
+                           int* ranks_all, cd* scratch,
+                           long long scratch_stride, int* status, int hb,
+                           double* acc, int phase) {
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
   __shared__ double red[32];
+  // ranks of the instance in flight: thread 0 updates them between barriers,
+  // every thread reads them, so they live in shared memory
+  __shared__ int r[SFFT_MAXN_DEV + 1];
   double fl = 0.0;
   for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
     const int n = n_arr[inst];
     const double tol = tol_arr[inst];
     const int rmax = maxrank_arr[inst];
-    int* r = ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
+    int* rg = ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) r[i] = rg[i];
+    __syncthreads();
     cd* base = tt + tt_off[inst];
     cd* tmp = scratch + (size_t)blockIdx.x * scratch_stride;
     int st = 0;
@@ -436,6 +442,7 @@ __global__ void k_tt_round(int count, const int* __restrict__ n_arr, int d, int 
               flops_gemm(r0, kk, k) + flops_gemm(rows, kk, r0);
       }
     }
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) rg[i] = r[i];
     if (threadIdx.x == 0 && status) status[inst] = max(status[inst], st);
     __syncthreads();
   }
@@ -452,15 +459,15 @@ __global__ void k_tt_round(int count, const int* __restrict__ n_arr, int d, int 
 // vectors V of Z are the left singular vectors of T: V becomes the output core
 // B_s[c][mu][c''] and Z V = T^H V the next carry CH. Singular values below
 // ztol * ||T|| are dropped; the final rounding sweep sets the ranks.
-__global__ void k_zipup(int count, const int* __restrict__ n_arr, const double* __restrict__ tol_arr,
-                        const int* __restrict__ maxrank_arr, const cd* __restrict__ A,
-                        const long long* __restrict__ a_off, const int* __restrict__ a_ranks_all,
-                        const cd* __restrict__ Wmpo, const long long* __restrict__ w_off,
-                        const int* __restrict__ w_ranks_all, cd* __restrict__ B,
-                        const long long* __restrict__ b_off, int* __restrict__ b_ranks_all,
+__global__ void k_zipup(int count, const int* n_arr, const double* tol_arr,
+                        const int* maxrank_arr, const cd* A,
+                        const long long* a_off, const int* a_ranks_all,
+                        const cd* Wmpo, const long long* w_off,
+                        const int* w_ranks_all, cd* B,
+                        const long long* b_off, int* b_ranks_all,
                         int core_stride_a, int core_stride_w, int core_stride_b,
-                        cd* __restrict__ scratch, long long scratch_stride,
-                        int* __restrict__ status, int hb, double* __restrict__ acc) {
+                        cd* scratch, long long scratch_stride,
+                        int* status, int hb, double* acc) {
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
   double fl = 0.0;
@@ -563,13 +570,13 @@ __global__ void k_zipup(int count, const int* __restrict__ n_arr, const double* 
 // 2^h row vectors v B[...]. Sites t+h..n-1: column vectors R_s[prefix] for the
 // contiguous range of prefixes u >> s, built from the top. Then
 // y_u = Lv[(u >> t) mod 2^h] . R_{t+h}[u >> (t+h)].
-__global__ void k_readout(int count, const InstParams* __restrict__ P, const cd* __restrict__ B,
-                          const long long* __restrict__ b_off, const int* __restrict__ b_ranks_all,
-                          int core_stride, const long long* __restrict__ l_begin,
-                          const int* __restrict__ tbits, const int* __restrict__ qarr,
-                          const long long* __restrict__ out_off, double* __restrict__ prices,
-                          double* __restrict__ logk, const int* __restrict__ status,
-                          cd* __restrict__ scratch, long long scratch_stride) {
+__global__ void k_readout(int count, const InstParams* __restrict__ P, const cd* B,
+                          const long long* b_off, const int* b_ranks_all,
+                          int core_stride, const long long* l_begin,
+                          const int* tbits, const int* qarr,
+                          const long long* out_off, double* prices,
+                          double* logk, const int* status,
+                          cd* scratch, long long scratch_stride) {
   __shared__ cd Lv[(1 << READOUT_TREE_BITS) * SFFT_SLOT_RANK_DEV];
   __shared__ cd Lv2[(1 << READOUT_TREE_BITS) * SFFT_SLOT_RANK_DEV];
   for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
