@@ -239,8 +239,12 @@ def test_paper_grid_nrmse_floor(pricer):
         lk = logk.cpu().numpy()
         e, cnt = cm.nrmse(p, c, lk, lambda K: cfm.bs_call(100.0, K, 0.05, 0.3, 0.5))
         assert cnt > 0 and e < 30 * floor, (n, e)
+        # element-wise parity inside the evaluation window K in [50, 150]; outside
+        # it exp(-alpha k) reaches ~1e12 and amplifies rounding (Sec. 5)
         c_ref, _ = cm.prices_from_y(p, np.arange(M), cm.y_full(p, "fft"))
-        assert np.max(np.abs(c - c_ref)) <= PRICE_TOL * p.S0
+        K = np.exp(lk)
+        win = (K >= 50.0) & (K <= 150.0)
+        assert np.max(np.abs(c[win] - c_ref[win])) <= PRICE_TOL * p.S0
 
 
 def test_config3_sample(pricer):
