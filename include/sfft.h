@@ -5,13 +5,13 @@
  * Carr-Madan discrete Fourier transform (Sec. 2.1 of Hauck & Turkalj,
  * "Classical Tensor Train and Quantum Fourier Transform Approaches for
  * Large-Scale Carr-Madan Option Pricing"), evaluated as the tensor-train
- * Superfast Fourier Transform of Sec. 4: the integrand x_j (Eq. x, or its
+ * Superfast Fourier Transform of Sec. 3: the integrand x_j (Eq. x, or its
  * Simpson-weighted variant) is held as a quantics tensor train of n binary
- * cores, the bit-reversed Fourier operator Q_n (Sec. 4.2) is applied as a
+ * cores, the bit-reversed Fourier operator Q_n (Sec. 3.2) is applied as a
  * matrix-product operator, the result is rounded by QR/SVD sweeps, and prices
- * are read out in bit-reversed site order (Sec. 4.3, Eq. discretization_dft).
+ * are read out in bit-reversed site order (Sec. 3.3, Eq. discretization_dft).
  * No length-M vector is formed on that path. A dense-FFT Carr-Madan baseline
- * (Sec. 5.1's FFT route) is exposed with the same calling convention.
+ * (Sec. 4.1's FFT route) is exposed with the same calling convention.
  *
  * Conventions shared by every entry point:
  *   - Every function returns sfft_status; nothing throws across the ABI.
@@ -70,7 +70,7 @@ typedef enum { SFFT_GBM = 0, SFFT_HESTON = 1, SFFT_MERTON = 2, SFFT_VG = 3 } sff
  *     Eq. discretization_dft.
  *   SFFT_QUAD_RECT_SYM: the paper's symmetric rectangle rule, Eqs.
  *     Ck_from_psi, x, discretization_dft; Delta_v = eta, or pi/sqrt(N) when
- *     eta <= 0 (the grid of Sec. 5), Delta_k = pi/(N Delta_v),
+ *     eta <= 0 (the grid of Sec. 4), Delta_k = pi/(N Delta_v),
  *     k'_0 = -N Delta_k/2. */
 typedef enum { SFFT_QUAD_SIMPSON_CM99 = 0, SFFT_QUAD_RECT_SYM = 1 } sfft_quad;
 
@@ -126,7 +126,7 @@ sfft_status sfft_strike_window(const sfft_problem *prob, double lo_logm,
                                double hi_logm, int32_t qmax, int64_t *l_begin,
                                int64_t *stride, int32_t *q);
 
-/* Price `count` instances with the TT-SFFT path (Sec. 4.3).
+/* Price `count` instances with the TT-SFFT path (Sec. 3.3).
  *   probs[count]              host  problem statements
  *   l_begin, stride, q        host  per-instance strike sets on the 2^n grid:
  *                                   u = l_begin + i*stride, i < q; stride a
@@ -161,13 +161,13 @@ sfft_status sfft_dense_price_batch(sfft_ctx *ctx, const sfft_problem *probs, int
 sfft_status sfft_sample_integrand(sfft_ctx *ctx, const sfft_problem *prob,
                                   const int64_t *j, int64_t count, double *x);
 
-/* Integrand TT of one problem (Sec. 4.1/4.3: TT-SVD of the sampled support
+/* Integrand TT of one problem (Sec. 3.1/4.3: TT-SVD of the sampled support
  * block). ranks (host, n+1) receives the ranks, cores (device) the packed
  * cores; cap = capacity of `cores` in complex elements. */
 sfft_status sfft_integrand_tt(sfft_ctx *ctx, const sfft_problem *prob, int32_t *ranks,
                               double *cores, int64_t cap);
 
-/* The MPO of Q_n (Sec. 4.2) compressed to relative Frobenius tolerance tol,
+/* The MPO of Q_n (Sec. 3.2) compressed to relative Frobenius tolerance tol,
  * copied packed (d = 4) into cores (device, capacity cap complex); ranks
  * (host, n+1). */
 sfft_status sfft_mpo(sfft_ctx *ctx, int32_t n, double tol, int32_t *ranks, double *cores,
@@ -186,6 +186,36 @@ sfft_status sfft_tt_round(sfft_ctx *ctx, int32_t n, int32_t d, const int32_t *in
 sfft_status sfft_tt_apply_qft(sfft_ctx *ctx, int32_t n, const int32_t *in_ranks,
                               const double *in_cores, double tol, int32_t max_rank,
                               int32_t *out_ranks, double *out_cores, int64_t cap);
+
+/* ---- rounding without allocation ----
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory when they round (a host application whose
+ * memory manager owns the device, a latency-critical loop that cannot afford
+ * the device-wide synchronisation of cudaMalloc/cudaFree, a plugin that may
+ * not create a library context). It runs the same rounding as sfft_tt_round
+ * (Oseledets' QR orthogonalisation and truncated-SVD sweep) but keeps all of
+ * its scratch in one statically sized device array of
+ * SFFT_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that
+ * loads the library holds until the process exits. It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   n, d                 n <= SFFT_NOALLOC_MAX_N sites, d in {2, 4}
+ *   in_ranks, out_ranks  host, n+1 entries each; every rank <= SFFT_MAX_RANK
+ *   in_cores, out_cores  device, packed cores (out capacity `cap` complex)
+ *   stream               cudaStream_t of the current device (NULL = default)
+ *   errbuf, errlen       optional host buffer for a readable error message
+ * Sizes beyond the limits are rejected with SFFT_EINVAL and a message in
+ * errbuf. The first call on a device (the current one) looks up the array's
+ * device address and sets the kernel's shared-memory limit; make that first
+ * call before any stream capture. Every call shares the one array and leaves
+ * its contents behind (the status word is cleared at the start of each call),
+ * so calls that overlap on the GPU, on any streams or threads, race. Returns
+ * after the stream has completed the call's work. */
+#define SFFT_NOALLOC_MAX_N 48
+#define SFFT_NOALLOC_SCRATCH_BYTES 3473920
+sfft_status sfft_tt_round_noalloc(int32_t n, int32_t d, const int32_t *in_ranks,
+                                  const double *in_cores, double tol, int32_t max_rank,
+                                  int32_t *out_ranks, double *out_cores, int64_t cap,
+                                  void *stream, char *errbuf, int32_t errlen);
 
 /* ---- tracing ---- */
 

@@ -12,9 +12,9 @@ Transform Approaches for Large-Scale Carr-Madan Option Pricing"):
                    (Eq. error_measure), the QFT amplitude readout
                    (Eq. qft_observable_price)
   closed_forms.py  Black-Scholes (Eq. analytic_BS) and Merton's series
-  tt.py            tensor-train toolkit on dense numpy arrays (Sec. 4.1):
+  tt.py            tensor-train toolkit on dense numpy arrays (Sec. 3.1):
                    TT-SVD, rounding, contraction, the bit-reversed DFT operator
-                   Q_n of Sec. 4.2 written out densely
+                   Q_n of Sec. 3.2 written out densely
 
 Only tests, the smoke check and the bench's CPU-baseline leg may import this
 package. It shares no code with the CUDA path: the product never imports it and

@@ -17,7 +17,7 @@ Eq. discretization_dft; Carr and Madan 1999):
              = exp(-alpha k'_u)/pi * sqrt(M) * Re(y_u)   with y of Eq. dft.
 
 RECT_SYM (Eqs. Ck_from_psi, discretization, x, discretization_dft; the grid of
-Sec. 5 when eta <= 0):
+Sec. 4 when eta <= 0):
     N = M/2, Delta_v = eta (or pi/sqrt(N) on the paper grid),
     Delta_k = pi/(N Delta_v), k'_0 = -N Delta_k/2 (literal reading of
     b = log S0 - N Delta_k/2), k'_l = k'_0 + l Delta_k.

@@ -1,12 +1,12 @@
 """Tensor trains on dense numpy arrays -- oracle (test infrastructure only).
 
-Sec. 4.1 of the paper: a TT (Eq. tt_format) is a list of cores A_k of shape
+Sec. 3.1 of the paper: a TT (Eq. tt_format) is a list of cores A_k of shape
 (r_{k-1}, d, r_k); a TT operator (Eq. tto_format) has cores of shape
 (s_{k-1}, d_out, d_in, s_k). The quantics index of Eq. discretized_x is
 j = sum_l lambda_l 2^(n-l): site 1 is the most significant bit, so a core list
 contracts to a vector in C order of shape (2,)*n.
 
-Sec. 4.2: QFT_n = R_n Q_n, where R_n is the bit-reversal permutation of the
+Sec. 3.2: QFT_n = R_n Q_n, where R_n is the bit-reversal permutation of the
 output and Q_n, the SFFT operator, maps x to the DFT y with its output bits in
 reversed site order: output site l carries bit mu_l of the output index u
 with weight 2^(l-1). Densely, row index sum_l mu_l 2^(n-l) = bitrev_n(u).
@@ -151,7 +151,7 @@ def mpo_apply_dense(mpo_cores, tt_cores):
 
 def rank1_exp_tt(gamma, n):
     """Rank-one TT of g(lambda) = exp(gamma * x(lambda)), x = sum lambda_l 2^-l
-    (Sec. 4.3): core l holds [1, exp(gamma 2^-l)]."""
+    (Sec. 3.3): core l holds [1, exp(gamma 2^-l)]."""
     cores = []
     for l in range(1, n + 1):
         G = np.zeros((1, 2, 1), dtype=np.complex128)

@@ -1,4 +1,4 @@
-// Dense-FFT Carr-Madan baseline (the FFT route of Sec. 5.1): every integrand
+// Dense-FFT Carr-Madan baseline (the FFT route of Sec. 4.1): every integrand
 // value x_j, j < M = 2^n, is sampled into device memory, an in-place M-point
 // FFT runs as a sequence of radix-2^R decimation-in-frequency passes, and the
 // requested strikes are gathered and priced (Eq. discretization_dft).

@@ -1,13 +1,13 @@
 // TT-SFFT kernels for sm_103a: integrand TT (TT-SVD of the sampled support
 // block), Q_n MPO generator, zip-up MPO x TT contraction, TT rounding and the
-// bit-reversed readout of prices (Sec. 4 of the paper).
+// bit-reversed readout of prices (Sec. 3 of the paper).
 //
 // Storage: each TT (or MPO, d = 4) of an instance occupies n "core slots" of
 // core_stride complex elements; core s (0-based site, site s+1 of the paper)
 // of shape (r_s, d, r_{s+1}) is stored compactly, index [a][sigma][b] at
 // a*d*r_{s+1} + sigma*r_{s+1} + b. Ranks live in an int array of n+1 entries.
 // Site s carries bit (n-1-s) of the input index j (most significant first,
-// Eq. discretized_x) and bit s of the output index u after Q_n (Sec. 4.2).
+// Eq. discretized_x) and bit s of the output index u after Q_n (Sec. 3.2).
 //
 // One CTA works on one instance at a time (grid-stride over the batch); the
 // site sweeps are sequential, the dense algebra inside a site is spread over
@@ -141,7 +141,7 @@ __global__ void k_support_probe(const InstParams* __restrict__ P, int count, dou
 }
 
 // ---------------------------------------------------------------------------
-// K2: integrand TT by TT-SVD of the support block (Sec. 4.1; Oseledets 2011)
+// K2: integrand TT by TT-SVD of the support block (Sec. 3.1; Oseledets 2011)
 // ---------------------------------------------------------------------------
 // The block x_j, j < 2^m, is swept from its least significant bit: at step t
 // the carried matrix Z (2^(m-t-1) rows = remaining high bits, 2 r columns =
@@ -247,7 +247,7 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
 // ---------------------------------------------------------------------------
 // Q_n = M^{-1/2} prod_l exp(-i pi mu_l (lambda_l + B_l)) with
 // B_l = sum_{l' > l} lambda_l' 2^(l - l') in [0, 1) (the product form of the
-// bit-reversed DFT, Sec. 4.2). The dependence of sites 1..l on B_l is an
+// bit-reversed DFT, Sec. 3.2). The dependence of sites 1..l on B_l is an
 // entire function exp(-2 pi i A B_l), A in [0,1), so it is carried across
 // bond l by its values at P Chebyshev nodes b_q of [0,1]; B_{l-1} =
 // (lambda_l + B_l)/2 gives the transfer core
@@ -473,7 +473,7 @@ __global__ void k_zipup(int count, const int* n_arr, const double* tol_arr,
   double fl = 0.0;
   for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
     const int n = n_arr[inst];
-    const double ztol = 0.1 * tol_arr[inst] / sqrt((double)max(n - 1, 1));
+    const double ztol = tol_arr[inst] / sqrt((double)max(n - 1, 1));
     const int rmax = maxrank_arr[inst];
     const int* ra = a_ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
     const int* rw = w_ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
@@ -563,7 +563,7 @@ __global__ void k_zipup(int count, const int* n_arr, const double* tol_arr,
 }
 
 // ---------------------------------------------------------------------------
-// K6: readout in bit-reversed site order (Sec. 4.3, Eq. discretization_dft)
+// K6: readout in bit-reversed site order (Sec. 3.3, Eq. discretization_dft)
 // ---------------------------------------------------------------------------
 // Requested outputs u = l_begin + i*2^t, i < q. Sites 0..t-1 carry the fixed
 // low bits: a row vector v. Sites t..t+h-1 carry the next h bits: a tree of

@@ -69,6 +69,9 @@ EXPORTS = {
     "sfft_profile_read": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
                                     ctypes.POINTER(c_double), ctypes.POINTER(c_int64), c_int32]),
     "sfft_calibrate_fp64": (c_int32, [c_void_p, ctypes.POINTER(c_double)]),
+    "sfft_tt_round_noalloc": (c_int32, [c_int32, c_int32, ctypes.POINTER(c_int32), c_void_p, c_double,
+                                        c_int32, ctypes.POINTER(c_int32), c_void_p, c_int64, c_void_p,
+                                        ctypes.c_char_p, c_int32]),
     "sfft_status_string": (ctypes.c_char_p, [c_int32]),
     "sfft_last_error": (ctypes.c_char_p, [c_void_p]),
 }
@@ -276,6 +279,30 @@ class Pricer:
         self._check(self.lib.sfft_tt_apply_qft(self.h, n, rin, c_void_p(_ptr(flat)), tol, max_rank, rout,
                                                c_void_p(_ptr(out)), cap))
         return unpack(out, [rout[i] for i in range(n + 1)], 2)
+
+
+def tt_round_noalloc(cores: List, tol: float, max_rank: int = 0, device: int = 0):
+    """Round a TT with the allocation-free entry point (no context; the
+    library's static device scratch). Input/output device buffers are
+    allocated here by torch, which is the caller's side of the contract."""
+    import torch
+    lib = load_library()
+    n = len(cores)
+    d = cores[0].shape[1]
+    flat, ranks = pack(cores, torch, device)
+    cap = n * d * MAX_RANK * MAX_RANK
+    out = torch.empty(cap, dtype=torch.complex128, device=torch.device("cuda", device))
+    width = max(MAX_N + 1, len(ranks))
+    rin = (c_int32 * width)(*ranks)
+    rout = (c_int32 * width)()
+    err = ctypes.create_string_buffer(256)
+    with torch.cuda.device(device):
+        st = torch.cuda.current_stream(device).cuda_stream
+        s = lib.sfft_tt_round_noalloc(n, d, rin, c_void_p(flat.data_ptr()), tol, max_rank, rout,
+                                      c_void_p(out.data_ptr()), cap, c_void_p(st), err, 256)
+    if s != SFFT_OK:
+        raise SfftError(s, err.value.decode())
+    return unpack(out, [rout[i] for i in range(n + 1)], d)
 
 
 def unpack(flat, ranks: Sequence[int], d: int):

@@ -76,7 +76,7 @@ def config2_heston(n: int, tol: float = 1e-12) -> Problem:
 
 
 def paper_grid_bs(n: int) -> Problem:
-    """The paper's experimental grid (Sec. 5): Black-Scholes S0=100, r=0.05,
+    """The paper's experimental grid (Sec. 4): Black-Scholes S0=100, r=0.05,
     sigma=0.3, T=0.5, alpha=2.5, N=2^(n-1), Delta_k=N^(-1/2),
     b=log S0 - N Delta_k/2, Delta_v = pi/(N Delta_k)."""
     return Problem(GBM, (0.3,), S0=100.0, r=0.05, T=0.5, alpha=2.5, eta=0.0,

@@ -230,7 +230,7 @@ def test_config2_heston_sweep(pricer, n):
 
 
 def test_paper_grid_nrmse_floor(pricer):
-    floor = 3.1e-13  # printed SFFT floor of Sec. 5.1
+    floor = 3.1e-13  # printed SFFT floor of Sec. 4.1
     for n in (10, 14, 16):
         p = wl.paper_grid_bs(n)
         M = 1 << n
@@ -240,7 +240,7 @@ def test_paper_grid_nrmse_floor(pricer):
         e, cnt = cm.nrmse(p, c, lk, lambda K: cfm.bs_call(100.0, K, 0.05, 0.3, 0.5))
         assert cnt > 0 and e < 30 * floor, (n, e)
         # element-wise parity inside the evaluation window K in [50, 150]; outside
-        # it exp(-alpha k) reaches ~1e12 and amplifies rounding (Sec. 5)
+        # it exp(-alpha k) reaches ~1e12 and amplifies rounding (Sec. 4)
         c_ref, _ = cm.prices_from_y(p, np.arange(M), cm.y_full(p, "fft"))
         K = np.exp(lk)
         win = (K >= 50.0) & (K <= 150.0)

@@ -314,7 +314,7 @@ def test_tt_svd_exact_and_truncated():
     for f, rk in ((np.exp(3 * x), 1), (np.sin(5 * x), 2), (1 + x - 2 * x ** 2 + x ** 3, 4)):
         c = tt.tt_svd(f.reshape((2,) * n), 1e-13)
         assert max(tt.tt_ranks(c)) == rk
-    # rank-one exponential TT of Sec. 4.3 equals exp(gamma x)
+    # rank-one exponential TT of Sec. 3.3 equals exp(gamma x)
     g = -2.0 + 7.0j
     assert np.max(np.abs(tt.tt_full(tt.rank1_exp_tt(g, n)).reshape(-1) - np.exp(g * x))) < 1e-12
 
