@@ -184,16 +184,7 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
 
     ok = [s == 0 for s in status]
     q_ok = sum(s[2] for s, o in zip(strikes, ok) if o)
-    tot_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([tot_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_s = float(t.item())
-        qq = torch.tensor([float(q_ok)], device=dev)
-        torch.distributed.all_reduce(qq)
-        q_all = float(qq.item())
-    else:
-        q_all = float(q_ok)
+    tot_s, q_all = reduce_over_ranks(sum(step_ms) / 1e3, q_ok, world, dev)
     value = q_all * args.steps / tot_s
 
     # end to end: same call, outputs copied to pinned host memory inside the timed region
@@ -262,6 +253,21 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
     }
     pricer.close()
     return line
+
+
+def reduce_over_ranks(seconds: float, strikes: int, world: int, device):
+    """Whole-job figures across ranks: the slowest rank's time (max) and the
+    strikes all ranks priced (sum). Ranks price independent instance batches,
+    so this is the only cross-rank exchange (weak scaling)."""
+    if world <= 1:
+        return seconds, float(strikes)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    q = torch.tensor([float(strikes)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(q, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(q.item())
 
 
 def ctypes_sizeof_problem():
