@@ -32,21 +32,29 @@ enum { PH_PROBE = 0, PH_BUILD = 1, PH_ZIPUP = 2, PH_ROUND = 3, PH_READOUT = 4, P
 __global__ void k_sample(const InstParams* P, const long long* j, long long count, cd* x);
 __global__ void k_support_probe(const InstParams* P, int count, double probe_tol, int m_min,
                                 int* m_out);
-__global__ void k_integrand_ttsvd(const InstParams* P, const int* m_arr, int count, cd* scratch,
+__global__ void k_integrand_ttsvd(const InstParams* P, const int* m_arr, const int* list, int count,
+                                  int* counter, cd* scratch,
                                   long long scratch_stride, cd* tt, const long long* tt_off,
                                   int core_stride, int* ranks_all, int* status, int hb, double* acc);
+__global__ void k_integrand_cross(const InstParams* P, const int* list, int count, int* counter,
+                                  cd* scratch, long long scratch_stride, cd* tt,
+                                  const long long* tt_off, int core_stride, int* ranks_all,
+                                  int* status, int hb, double* acc, int max_sweeps);
 __global__ void k_mpo_interp(int n, int P, cd* W, int core_stride, int* ranks);
-__global__ void k_tt_round(int count, const int* n_arr, int d, int left_orth, const double* tol_arr,
+__global__ void k_tt_round(const int* list, int count, int* counter, const int* n_arr, int d,
+                           int left_orth, const double* tol_arr,
                            const int* maxrank_arr, cd* tt, const long long* tt_off,
                            int core_stride, int* ranks_all, cd* scratch,
                            long long scratch_stride, int* status, int hb, double* acc, int phase);
-__global__ void k_zipup(int count, const int* n_arr, const double* tol_arr, const int* maxrank_arr,
+__global__ void k_zipup(const int* list, int count, int* counter, const int* n_arr,
+                        const double* tol_arr, const int* maxrank_arr,
                         const cd* A, const long long* a_off, const int* a_ranks_all,
                         const cd* Wmpo, const long long* w_off, const int* w_ranks_all, cd* B,
                         const long long* b_off, int* b_ranks_all, int core_stride_a,
                         int core_stride_w, int core_stride_b, cd* scratch,
                         long long scratch_stride, int* status, int hb, double* acc);
-__global__ void k_readout(int count, const InstParams* P, const cd* B, const long long* b_off,
+__global__ void k_readout(const int* list, int count, int* counter, const InstParams* P,
+                          const cd* B, const long long* b_off,
                           const int* b_ranks_all, int core_stride, const long long* l_begin,
                           const int* tbits, const int* qarr, const long long* out_off,
                           double* prices, double* logk, const int* status, cd* scratch,

@@ -279,4 +279,132 @@ __device__ __forceinline__ int trunc_rank(const double* sig, int m, double delta
   return max(k, 1);
 }
 
+// CTA-wide argmax of |x_i|^2 over i < len with x given by a functor; ties go
+// to the lowest index. red_d / red_i: smem scratch of blockDim/32 entries.
+template <class F>
+__device__ int cta_argmax(int len, F val, double* red_d, int* red_i) {
+  double best = -1.0;
+  int bi = 0x7fffffff;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    const double v = val(i);
+    if (v > best || (v == best && i < bi)) {
+      best = v;
+      bi = i;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) {
+      best = ov;
+      bi = oi;
+    }
+  }
+  if (lane_id() == 0) {
+    red_d[warp_id()] = best;
+    red_i[warp_id()] = bi;
+  }
+  __syncthreads();
+  double b2 = -1.0;
+  int i2 = 0x7fffffff;
+  for (int w = 0; w < n_warps(); ++w)
+    if (red_d[w] > b2 || (red_d[w] == b2 && red_i[w] < i2)) {
+      b2 = red_d[w];
+      i2 = red_i[w];
+    }
+  __syncthreads();
+  return i2;
+}
+
+// Maxvol (Goreinov, Oseledets, Savostyanov, Tyrtyshnikov, Zamarashkin, 2010):
+// r rows of A (N x r, column-major, leading dim lda, N >= r, smem) whose
+// r x r submatrix has locally maximal volume, i.e. every entry of
+// B = A A[piv]^{-1} has modulus <= 1 + 1e-2. Start: rows chosen by Gaussian
+// elimination with partial pivoting. piv[r] (smem) receives the rows.
+// work: smem of 2 N r + 2 r r + N complex; iw: N ints; red_*: reduction scratch.
+static __device__ void maxvol(const cd* A, int lda, int N, int r, int* piv, cd* work, int* iw,
+                              double* red_d, int* red_i) {
+  cd* C = work;                 // N x r elimination copy, then B
+  cd* S = C + (size_t)N * r;    // r x 2r Gauss-Jordan block [A[piv] | I]
+  cd* fac = S + (size_t)2 * r * r;  // N factors
+  for (int idx = threadIdx.x; idx < N * r; idx += blockDim.x) C[idx] = A[(idx / N) * lda + idx % N];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) iw[i] = 0;
+  __syncthreads();
+  // 1. partial-pivoting elimination picks the starting rows
+  for (int c = 0; c < r; ++c) {
+    const int pr = cta_argmax(N, [&](int i) { return iw[i] ? -1.0 : cabs2(C[c * N + i]); }, red_d, red_i);
+    if (threadIdx.x == 0) {
+      piv[c] = pr;
+      iw[pr] = 1;
+    }
+    __syncthreads();
+    const cd pv = C[c * N + pr];
+    const bool nz = cabs2(pv) > 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+      fac[i] = (!iw[i] && nz) ? cdiv(C[c * N + i], pv) : mkc(0.0, 0.0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < N * (r - c - 1); idx += blockDim.x) {
+      const int cc = c + 1 + idx / N, i = idx % N;
+      C[cc * N + i] = csub(C[cc * N + i], cmul(fac[i], C[cc * N + pr]));
+    }
+    __syncthreads();
+  }
+  // 2. S = [A[piv] | I]; Gauss-Jordan with partial pivoting -> A[piv]^{-1}
+  for (int idx = threadIdx.x; idx < r * 2 * r; idx += blockDim.x) {
+    const int i = idx / (2 * r), j = idx % (2 * r);
+    S[idx] = (j < r) ? A[j * lda + piv[i]] : mkc((j - r) == i ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int c = 0; c < r; ++c) {
+    const int pr = c + cta_argmax(r - c, [&](int i) { return cabs2(S[(c + i) * 2 * r + c]); }, red_d, red_i);
+    if (pr != c)
+      for (int j = threadIdx.x; j < 2 * r; j += blockDim.x) {
+        const cd t = S[c * 2 * r + j];
+        S[c * 2 * r + j] = S[pr * 2 * r + j];
+        S[pr * 2 * r + j] = t;
+      }
+    __syncthreads();
+    const cd pv = S[c * 2 * r + c];
+    const cd inv = cabs2(pv) > 0.0 ? cdiv(mkc(1.0, 0.0), pv) : mkc(0.0, 0.0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < 2 * r; j += blockDim.x) S[c * 2 * r + j] = cmul(S[c * 2 * r + j], inv);
+    __syncthreads();
+    for (int i = threadIdx.x; i < r; i += blockDim.x) fac[i] = (i == c) ? mkc(0.0, 0.0) : S[i * 2 * r + c];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < r * 2 * r; idx += blockDim.x) {
+      const int i = idx / (2 * r), j = idx % (2 * r);
+      if (i != c) S[idx] = csub(S[idx], cmul(fac[i], S[c * 2 * r + j]));
+    }
+    __syncthreads();
+  }
+  // 3. B = A A[piv]^{-1} (N x r, column-major) into C
+  for (int idx = threadIdx.x; idx < N * r; idx += blockDim.x) {
+    const int j = idx / N, i = idx % N;
+    cd acc = mkc(0.0, 0.0);
+    for (int a = 0; a < r; ++a) acc = cfma(A[a * lda + i], S[a * 2 * r + r + j], acc);
+    C[idx] = acc;
+  }
+  __syncthreads();
+  // 4. swap in the largest entry until all are <= 1 + 1e-2 (bounded)
+  for (int it = 0; it < 8 * r + 8; ++it) {
+    const int e = cta_argmax(N * r, [&](int idx) { return cabs2(C[idx]); }, red_d, red_i);
+    const int j = e / N, i = e % N;
+    const cd bij = C[e];
+    if (cabs2(bij) <= (1.0 + 1e-2) * (1.0 + 1e-2)) break;
+    // B <- B - B[:, j] (B[i, :] - e_j) / B[i, j]
+    for (int a = threadIdx.x; a < N; a += blockDim.x) fac[a] = cdiv(C[j * N + a], bij);
+    cd* rowi = S;  // reuse: r entries
+    for (int c = threadIdx.x; c < r; c += blockDim.x)
+      rowi[c] = (c == j) ? csub(C[c * N + i], mkc(1.0, 0.0)) : C[c * N + i];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < N * r; idx += blockDim.x) {
+      const int c = idx / N, a = idx % N;
+      C[idx] = csub(C[idx], cmul(fac[a], rowi[c]));
+    }
+    if (threadIdx.x == 0) piv[j] = i;
+    __syncthreads();
+  }
+}
+
 }  // namespace la

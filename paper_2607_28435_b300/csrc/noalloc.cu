@@ -156,7 +156,7 @@ extern "C" sfft_status sfft_tt_round_noalloc(int32_t n, int32_t d, const int32_t
   NA_CK(cudaMemcpyAsync(ranks, rk, sizeof rk, cudaMemcpyHostToDevice, sm), "rank upload failed");
   NA_CK(cudaMemcpyAsync(prm, &hp, sizeof hp, cudaMemcpyHostToDevice, sm), "parameter upload failed");
   const size_t smem = la::ts_svd_smem_bytes(LA_MAXP, kHbNa) + 256;
-  k_tt_round<<<1, kThreadsNa, smem, sm>>>(1, &prm->n, d, 1, &prm->tol, &prm->maxrank, tt, &prm->off,
+  k_tt_round<<<1, kThreadsNa, smem, sm>>>(nullptr, 1, nullptr, &prm->n, d, 1, &prm->tol, &prm->maxrank, tt, &prm->off,
                                          stride, ranks, tmp, SFFT_ROUND_SCRATCH, &prm->status, kHbNa,
                                          nullptr, PH_ROUND);
   NA_CK(cudaGetLastError(), "launch of the rounding kernel failed");

@@ -24,8 +24,9 @@ static_assert(SFFT_MAX_RANK == SFFT_SLOT_RANK_DEV, "slot rank");
 namespace {
 
 const int kThreads = 256;
-const int kHb = 32;  // row-block height reserved next to the 64-column panel
-const int kMaxBlockBits = 22;  // largest support block 2^m sampled for TT-SVD
+const int kHb = 36;  // row-block height reserved next to the 64-column panel
+const int kSvdMaxBits = 14;  // support blocks up to 2^14 points: TT-SVD; wider: cross
+const int kCrossSweeps = 6;
 
 struct DevBuf {
   void* p = nullptr;
@@ -264,6 +265,7 @@ size_t svd_smem() { return la::ts_svd_smem_bytes(LA_MAXP, kHb) + 256; }
 sfft_status set_smem_attrs(sfft_ctx* ctx) {
   const int sm = (int)svd_smem();
   CK(cudaFuncSetAttribute(k_integrand_ttsvd, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_integrand_cross, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   CK(cudaFuncSetAttribute(k_tt_round, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   CK(cudaFuncSetAttribute(k_zipup, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   CK(cudaFuncSetAttribute(k_fft_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
@@ -334,7 +336,7 @@ sfft_status get_mpo(sfft_ctx* ctx, int n, double tol, const MpoEntry** out) {
   {
     PhaseScope ps(ctx, PH_MPO);
     k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(
-        1, reinterpret_cast<int*>(a), 4, 1, reinterpret_cast<double*>(a + 8),
+        nullptr, 1, nullptr, reinterpret_cast<int*>(a), 4, 1, reinterpret_cast<double*>(a + 8),
         reinterpret_cast<int*>(a + 16), W, reinterpret_cast<long long*>(a + 24), SFFT_CORE_STRIDE_D4,
         rk, reinterpret_cast<cd*>(scr), SFFT_ROUND_SCRATCH, nullptr, kHb, acc_ptr(ctx), PH_MPO);
   }
@@ -377,6 +379,8 @@ struct Batch {
   long long* w_off = nullptr;
   int* w_ranks = nullptr;
   std::vector<int> mpo_max;
+  int* all_list = nullptr;  // instances, largest n first
+  int* counters = nullptr;  // work-queue counters of the launches
 };
 
 // Integrand TT -> zip-up -> rounding, for `valid` problems (host vectors of
@@ -419,7 +423,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   CK(cudaMemsetAsync(b.status, 0, sizeof(int) * std::max(cnt, 1), ctx->stream));
   if (cnt == 0) return SFFT_OK;
 
-  // support probe -> block exponent m
+  // support probe -> block exponent m; small blocks by TT-SVD, wide ones by cross
   int* m_dev;
   if ((s = ensure(ctx, "m_arr", sizeof(int) * cnt, &p))) return s;
   m_dev = reinterpret_cast<int*>(p);
@@ -428,30 +432,64 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     k_support_probe<<<cnt, 64, 0, ctx->stream>>>(b.P, cnt, 1e-2, 4, m_dev);
   }
   CK(cudaGetLastError());
-  std::vector<int> m_host(cnt), st_host(cnt, 0);
+  std::vector<int> m_host(cnt);
   CK(cudaMemcpyAsync(m_host.data(), m_dev, sizeof(int) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<int> svd_list, cross_list, all_list(cnt);
   int mmax = 1;
   for (int i = 0; i < cnt; ++i) {
-    if (m_host[i] > kMaxBlockBits) {
-      // support too wide for the TT-SVD block: not built
-      m_host[i] = -1;
-      st_host[i] = SFFT_ENOCONV;
-      continue;
+    all_list[i] = i;
+    if (m_host[i] <= kSvdMaxBits) {
+      svd_list.push_back(i);
+      mmax = std::max(mmax, m_host[i]);
+    } else {
+      cross_list.push_back(i);
     }
-    mmax = std::max(mmax, m_host[i]);
   }
-  CK(cudaMemcpyAsync(m_dev, m_host.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(b.status, st_host.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, ctx->stream));
+  // largest work first
+  std::stable_sort(svd_list.begin(), svd_list.end(), [&](int a, int c) { return m_host[a] > m_host[c]; });
+  std::stable_sort(cross_list.begin(), cross_list.end(), [&](int a, int c) { return prm[a].n > prm[c].n; });
+  std::stable_sort(all_list.begin(), all_list.end(), [&](int a, int c) { return prm[a].n > prm[c].n; });
+  int *svd_dev, *cross_dev, *all_dev, *ctr;
+  if ((s = upload(ctx, "svd_list", svd_list, &svd_dev)) || (s = upload(ctx, "cross_list", cross_list, &cross_dev)) ||
+      (s = upload(ctx, "all_list", all_list, &all_dev)))
+    return s;
+  if ((s = ensure(ctx, "counters", sizeof(int) * 16, &p))) return s;
+  ctr = reinterpret_cast<int*>(p);
+  CK(cudaMemsetAsync(ctr, 0, sizeof(int) * 16, ctx->stream));
+  b.all_list = all_dev;
+  b.counters = ctr;
   const size_t smem = svd_smem();
-  int grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem));
-  const long long sstride = 2LL << mmax;
-  if ((s = ensure(ctx, "build_scratch", sizeof(cd) * sstride * grid, &p))) return s;
-  {
+  if (!svd_list.empty()) {
+    const int nsvd = (int)svd_list.size();
+    const int grid = std::min(nsvd, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem));
+    const long long sstride = 2LL << mmax;
+    if ((s = ensure(ctx, "build_scratch", sizeof(cd) * sstride * grid, &p))) return s;
     PhaseScope ps(ctx, PH_BUILD);
     k_integrand_ttsvd<<<grid, kThreads, smem, ctx->stream>>>(
-        b.P, m_dev, cnt, reinterpret_cast<cd*>(p), sstride, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
-        b.a_ranks, b.status, kHb, acc_ptr(ctx));
+        b.P, m_dev, svd_dev, nsvd, ctr + 0, reinterpret_cast<cd*>(p), sstride, b.A, b.a_off,
+        SFFT_CORE_STRIDE_D2, b.a_ranks, b.status, kHb, acc_ptr(ctx));
+  }
+  CK(cudaGetLastError());
+  if (!cross_list.empty()) {
+    const int ncr = (int)cross_list.size();
+    const int grid = std::min(ncr, ctx->num_sms * blocks_per_sm((const void*)k_integrand_cross, smem));
+    if ((s = ensure(ctx, "cross_scratch", sizeof(cd) * (size_t)4096 * grid, &p))) return s;
+    {
+      PhaseScope ps(ctx, PH_BUILD);
+      k_integrand_cross<<<grid, kThreads, smem, ctx->stream>>>(
+          b.P, cross_dev, ncr, ctr + 1, reinterpret_cast<cd*>(p), 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
+          b.a_ranks, b.status, kHb, acc_ptr(ctx), kCrossSweeps);
+    }
+    CK(cudaGetLastError());
+    // interpolatory cores -> right-orthonormal, truncated to tol
+    const int g2 = std::min(ncr, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, smem));
+    if ((s = ensure(ctx, "xround_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * g2, &p))) return s;
+    PhaseScope ps(ctx, PH_BUILD);
+    k_tt_round<<<g2, kThreads, smem, ctx->stream>>>(cross_dev, ncr, ctr + 2, b.n_arr, 2, 1, b.tol_arr,
+                                                    b.maxr_arr, b.A, b.a_off, SFFT_CORE_STRIDE_D2, b.a_ranks,
+                                                    reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH, b.status,
+                                                    kHb, acc_ptr(ctx), PH_BUILD);
   }
   CK(cudaGetLastError());
   if (!apply) return SFFT_OK;
@@ -467,12 +505,12 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   if ((s = upload(ctx, "w_off", w_off, &b.w_off))) return s;
   CK(cudaMemcpyAsync(b.w_ranks, w_ranks.data(), sizeof(int) * w_ranks.size(), cudaMemcpyHostToDevice,
                      ctx->stream));
-  grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, smem));
+  int grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, smem));
   if ((s = ensure(ctx, "zip_scratch", sizeof(cd) * (size_t)SFFT_ZIP_SCRATCH * grid, &p))) return s;
   {
     PhaseScope ps(ctx, PH_ZIPUP);
     k_zipup<<<grid, kThreads, smem, ctx->stream>>>(
-        cnt, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
+        all_dev, cnt, ctr + 3, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
         reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
         SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
         SFFT_ZIP_SCRATCH, b.status, kHb, acc_ptr(ctx));
@@ -482,7 +520,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   if ((s = ensure(ctx, "round_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * grid, &p))) return s;
   {
     PhaseScope ps(ctx, PH_ROUND);
-    k_tt_round<<<grid, kThreads, smem, ctx->stream>>>(cnt, b.n_arr, 2, 0, b.tol_arr, b.maxr_arr, b.B,
+    k_tt_round<<<grid, kThreads, smem, ctx->stream>>>(all_dev, cnt, ctr + 4, b.n_arr, 2, 0, b.tol_arr, b.maxr_arr, b.B,
                                                       b.a_off, SFFT_CORE_STRIDE_D2, b.b_ranks,
                                                       reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH,
                                                       b.status, kHb, acc_ptr(ctx), PH_ROUND);
@@ -756,7 +794,7 @@ sfft_status sfft_tt_round(sfft_ctx* ctx, int32_t n, int32_t d, const int32_t* in
     return s;
   void* scr;
   if ((s = ensure(ctx, "rt_scratch", sizeof(cd) * SFFT_ROUND_SCRATCH, &scr))) return s;
-  k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(1, nd, d, 1, td, md, T, od, stride,
+  k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(nullptr, 1, nullptr, nd, d, 1, td, md, T, od, stride,
                                                       reinterpret_cast<int*>(rd), reinterpret_cast<cd*>(scr),
                                                       SFFT_ROUND_SCRATCH, sd, kHb, nullptr, PH_ROUND);
   CK(cudaGetLastError());
@@ -805,12 +843,12 @@ sfft_status sfft_tt_apply_qft(sfft_ctx* ctx, int32_t n, const int32_t* in_ranks,
   if ((s = ensure(ctx, "ap_scratch", sizeof(cd) * (size_t)(SFFT_ZIP_SCRATCH + SFFT_ROUND_SCRATCH), &scr)))
     return s;
   k_zipup<<<1, kThreads, svd_smem(), ctx->stream>>>(
-      1, nd, td, md, A, od, reinterpret_cast<int*>(ra), reinterpret_cast<const cd*>(ctx->mpo_pool.p), wd,
+      nullptr, 1, nullptr, nd, td, md, A, od, reinterpret_cast<int*>(ra), reinterpret_cast<const cd*>(ctx->mpo_pool.p), wd,
       reinterpret_cast<int*>(rw), B, od, reinterpret_cast<int*>(rb), SFFT_CORE_STRIDE_D2,
       SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(scr), SFFT_ZIP_SCRATCH, sd, kHb,
       nullptr);
   CK(cudaGetLastError());
-  k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(1, nd, 2, 0, td, md, B, od, SFFT_CORE_STRIDE_D2,
+  k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(nullptr, 1, nullptr, nd, 2, 0, td, md, B, od, SFFT_CORE_STRIDE_D2,
                                                       reinterpret_cast<int*>(rb), reinterpret_cast<cd*>(scr),
                                                       SFFT_ROUND_SCRATCH, sd, kHb, nullptr, PH_ROUND);
   CK(cudaGetLastError());
@@ -944,7 +982,7 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
   if ((s = ensure(ctx, "readout_scratch", sizeof(cd) * (size_t)SFFT_READOUT_SCRATCH * grid, &p))) return s;
   {
     PhaseScope ps(ctx, PH_READOUT);
-    k_readout<<<grid, kThreads, 0, ctx->stream>>>(cnt, b.P, b.B, b.a_off, b.b_ranks, SFFT_CORE_STRIDE_D2,
+    k_readout<<<grid, kThreads, 0, ctx->stream>>>(b.all_list, cnt, b.counters + 5, b.P, b.B, b.a_off, b.b_ranks, SFFT_CORE_STRIDE_D2,
                                                   lb_d, tb_d, q_d, off_d, prices, log_strikes, b.status,
                                                   reinterpret_cast<cd*>(p), SFFT_READOUT_SCRATCH);
   }

@@ -78,6 +78,23 @@ __device__ double cta_norm2(const cd* x, long long len, double* red) {
 
 }  // namespace
 
+// Work distribution shared by the per-instance kernels: slot k of `count`
+// processes instance list[k] (or k). With a counter the CTAs take slots from it
+// in order (the host sorts the list largest-first); without, slots are striped
+// by blockIdx.
+#define WORK_LOOP_BEGIN(list, count, counter)                               \
+  __shared__ int sh_slot_;                                                  \
+  int k_static_ = blockIdx.x;                                               \
+  for (;;) {                                                                \
+    if (threadIdx.x == 0) sh_slot_ = (counter) ? atomicAdd((counter), 1) : k_static_; \
+    __syncthreads();                                                        \
+    const int slot_ = sh_slot_;                                             \
+    __syncthreads();                                                        \
+    k_static_ += gridDim.x;                                                 \
+    if (slot_ >= (count)) break;                                            \
+    const int inst = (list) ? (list)[slot_] : slot_;
+#define WORK_LOOP_END }
+
 // ---------------------------------------------------------------------------
 // K1: integrand samples at listed indices
 // ---------------------------------------------------------------------------
@@ -149,14 +166,15 @@ __global__ void k_support_probe(const InstParams* __restrict__ P, int count, dou
 // the next carry. Sites above the block (Simpson grid, m < n) hold the
 // rank-one core delta_{lambda,0}.
 __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m_arr,
-                                  int count, cd* scratch, long long scratch_stride,
+                                  const int* list, int count, int* counter, cd* scratch,
+                                  long long scratch_stride,
                                   cd* tt, const long long* tt_off,
                                   int core_stride, int* ranks_all,
                                   int* status, int hb, double* acc) {
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
   double fl = 0.0, evals = 0.0;
-  for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
+  WORK_LOOP_BEGIN(list, count, counter)
     const InstParams prm = P[inst];
     const int n = prm.n;
     const int m = m_arr[inst];
@@ -235,7 +253,201 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
       status[inst] = st;
     }
     __syncthreads();
+  WORK_LOOP_END
+  if (acc && threadIdx.x == 0) {
+    atomicAdd(acc + PH_BUILD, fl);
+    atomicAdd(acc + SFFT_NPHASE_DEV + PH_BUILD, evals);
   }
+}
+
+// ---------------------------------------------------------------------------
+// K2b: integrand TT by two-site cross interpolation (Sec. 3.1's TT-cross)
+// ---------------------------------------------------------------------------
+// For integrands whose numerical support is too wide to sample densely. Index
+// sets: I[b] holds r_b prefixes (the b most significant bits of j), J[b] holds
+// r_b suffixes (the n - b least significant bits), for bonds b = 0..n. The
+// two-site supercore at bond b (sites b-1, b) is
+//   Phi[(i, l1), (l2, t)] = x( ((I[b-1][i] 2 + l1) 2 + l2) 2^(n-b-1) + J[b+1][t] ).
+// Left-to-right sweeps pick I[b] by maxvol on the left singular vectors of Phi,
+// right-to-left sweeps pick J[b] from its right singular vectors; the singular
+// values set the rank (relative threshold 0.1 tol, cap max_rank). Sweeps stop
+// when the ranks repeat. Assembly then runs one left-to-right pass: the fibre
+// matrix F_s[(i, l), t] = x((I[s][i] 2 + l) 2^(n-s-1) + J[s+1][t]) is factored
+// F = Q R, maxvol on Q gives I[s+1], and the core is Q Q[piv]^{-1}, which
+// interpolates x on the cross (Oseledets & Tyrtyshnikov 2010; Savostyanov &
+// Oseledets 2011). Rounding afterwards makes the cores right-orthonormal.
+#define CROSS_R SFFT_SLOT_RANK_DEV
+#define CROSS_R0 8
+
+__device__ __forceinline__ long long cross_seed(int t, int L) {
+  // candidate suffixes: 0, 1, all-ones, 2, 3, 5, 8, 13, 21, 34, ...
+  if (L < 4) return t;  // few suffixes: take them all (t < 2^L)
+  const long long top = (L >= 62) ? 0x3fffffffffffffffLL : ((1LL << L) - 1);
+  if (t == 0) return 0;
+  if (t == 1) return 1;
+  if (t == 2) return top;
+  long long a = 2, b = 3;
+  for (int k = 3; k < t; ++k) {
+    const long long c = a + b;
+    a = b;
+    b = c;
+  }
+  return a;
+}
+
+__global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* list, int count,
+                                  int* counter, cd* scratch, long long scratch_stride, cd* tt,
+                                  const long long* tt_off, int core_stride, int* ranks_all,
+                                  int* status, int hb, double* acc, int max_sweeps) {
+  extern __shared__ double4 smem_raw[];
+  SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
+  __shared__ long long Iset[(SFFT_MAXN_DEV + 1) * CROSS_R];
+  __shared__ long long Jset[(SFFT_MAXN_DEV + 1) * CROSS_R];
+  __shared__ int rk[SFFT_MAXN_DEV + 1];
+  __shared__ int rprev[SFFT_MAXN_DEV + 1];
+  __shared__ int piv[2 * CROSS_R];
+  __shared__ int iw[2 * CROSS_R];
+  __shared__ double red_d[32];
+  __shared__ int red_i[32];
+  double fl = 0.0, evals = 0.0;
+  cd* Z = scratch + (size_t)blockIdx.x * scratch_stride;
+  WORK_LOOP_BEGIN(list, count, counter)
+    const InstParams prm = P[inst];
+    const int n = prm.n;
+    const int rmax = min(prm.max_rank, CROSS_R);
+    const double ctol = 0.1 * prm.tol;
+    int st = 0;
+    cd* base = tt + tt_off[inst];
+    int* rg = ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
+    // initial right sets (seeds) and ranks
+    for (int b = threadIdx.x; b <= n; b += blockDim.x) {
+      const int L = n - b;
+      int r0 = (b == 0 || b == n) ? 1 : CROSS_R0;
+      if (L < 30) r0 = min(r0, 1 << L);
+      if (b < 30) r0 = min(r0, 1 << b);
+      r0 = max(r0, 1);
+      rk[b] = r0;
+      rprev[b] = 0;
+      for (int t = 0; t < r0; ++t) Jset[b * CROSS_R + t] = (b == n) ? 0 : cross_seed(t, L);
+      if (b == 0) Iset[0] = 0;
+    }
+    __syncthreads();
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+      // ---- left to right: choose I[b]
+      for (int b = 1; b < n; ++b) {
+        const int rl = rk[b - 1], rr = rk[b + 1];
+        const int p = 2 * rl, q = 2 * rr;
+        const int sh = n - b - 1;
+        for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
+          const int row = e / p, col = e - row * p;  // row (l2, t), col (i, l1)
+          const int l2 = row / rr, t = row - l2 * rr, i = col >> 1, l1 = col & 1;
+          const long long j = ((((Iset[(b - 1) * CROSS_R + i] << 1) | l1) << 1 | l2) << sh) | Jset[(b + 1) * CROSS_R + t];
+          Z[e] = cconj(integrand(prm, j));
+        }
+        __syncthreads();
+        evals += (double)p * q;
+        TsSvd sv = ts_svd(Z, q, p, p, sm.W, SVD_WCAP(hb), sm.V, sm.sig, sm.tau, sm.flag);
+        double s2 = 0.0;
+        for (int i = 0; i < sv.m; ++i) s2 += sm.sig[i] * sm.sig[i];
+        int k = trunc_rank(sm.sig, sv.m, ctol * sqrt(s2));
+        if (k > rmax) {
+          st = SFFT_ERANK_DEV;
+          k = rmax;
+        }
+        maxvol(sm.V, p, p, k, piv, sm.W, iw, red_d, red_i);
+        for (int c = threadIdx.x; c < k; c += blockDim.x)
+          Iset[b * CROSS_R + c] = (Iset[(b - 1) * CROSS_R + (piv[c] >> 1)] << 1) | (piv[c] & 1);
+        if (threadIdx.x == 0) rk[b] = k;
+        __syncthreads();
+        fl += sv.flops;
+      }
+      // ---- right to left: choose J[b]
+      for (int b = n - 1; b >= 1; --b) {
+        const int rl = rk[b - 1], rr = rk[b + 1];
+        const int q = 2 * rl, p = 2 * rr;
+        const int sh = n - b - 1;
+        for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
+          const int row = e / p, col = e - row * p;  // row (i, l1), col (l2, t)
+          const int i = row >> 1, l1 = row & 1, l2 = col / rr, t = col - l2 * rr;
+          const long long j = ((((Iset[(b - 1) * CROSS_R + i] << 1) | l1) << 1 | l2) << sh) | Jset[(b + 1) * CROSS_R + t];
+          Z[e] = integrand(prm, j);
+        }
+        __syncthreads();
+        evals += (double)p * q;
+        TsSvd sv = ts_svd(Z, q, p, p, sm.W, SVD_WCAP(hb), sm.V, sm.sig, sm.tau, sm.flag);
+        double s2 = 0.0;
+        for (int i = 0; i < sv.m; ++i) s2 += sm.sig[i] * sm.sig[i];
+        int k = trunc_rank(sm.sig, sv.m, ctol * sqrt(s2));
+        if (k > rmax) {
+          st = SFFT_ERANK_DEV;
+          k = rmax;
+        }
+        maxvol(sm.V, p, p, k, piv, sm.W, iw, red_d, red_i);
+        for (int c = threadIdx.x; c < k; c += blockDim.x) {
+          const int l2 = piv[c] / rr, t = piv[c] - l2 * rr;
+          Jset[b * CROSS_R + c] = ((long long)l2 << sh) | Jset[(b + 1) * CROSS_R + t];
+        }
+        if (threadIdx.x == 0) rk[b] = k;
+        __syncthreads();
+        fl += sv.flops;
+      }
+      // converged when the ranks repeat
+      int same = 1;
+      for (int b = 0; b <= n; ++b) same &= (rk[b] == rprev[b]);
+      __syncthreads();
+      for (int b = threadIdx.x; b <= n; b += blockDim.x) rprev[b] = rk[b];
+      __syncthreads();
+      if (same && sw >= 1) break;
+    }
+    // ---- assembly: interpolatory cores, left to right
+    if (threadIdx.x == 0) Iset[0] = 0;
+    __syncthreads();
+    for (int s = 0; s < n; ++s) {
+      const int rl = rk[s];
+      cd* G = core_ptr(base, core_stride, s);
+      if (s == n - 1) {
+        for (int e = threadIdx.x; e < 2 * rl; e += blockDim.x) {
+          const int i = e >> 1, l = e & 1;
+          G[e] = integrand(prm, (Iset[s * CROSS_R + i] << 1) | l);
+        }
+        evals += 2.0 * rl;
+        __syncthreads();
+        break;
+      }
+      const int rr = rk[s + 1];
+      const int N = 2 * rl;
+      const int sh = n - s - 1;
+      for (int e = threadIdx.x; e < N * rr; e += blockDim.x) {
+        const int c = e / N, row = e - c * N;  // column-major F
+        const int i = row >> 1, l = row & 1;
+        const long long j = ((((Iset[s * CROSS_R + i] << 1) | l)) << sh) | Jset[(s + 1) * CROSS_R + c];
+        sm.W[e] = integrand(prm, j);
+      }
+      __syncthreads();
+      evals += (double)N * rr;
+      qr_inplace(sm.W, N, N, rr, sm.tau);
+      const int kq = min(N, rr);
+      form_q(sm.W, N, N, kq, sm.tau, sm.V, N);
+      maxvol(sm.V, N, N, kq, piv, sm.W, iw, red_d, red_i);
+      // core (rl, 2, kq): G[i][l][c] = B[c * N + (i, l)] with B = Q Q[piv]^{-1} in W
+      for (int e = threadIdx.x; e < N * kq; e += blockDim.x) {
+        const int row = e / kq, c = e - row * kq;
+        G[e] = sm.W[(size_t)c * N + row];
+      }
+      for (int c = threadIdx.x; c < kq; c += blockDim.x)
+        Iset[(s + 1) * CROSS_R + c] = (Iset[s * CROSS_R + (piv[c] >> 1)] << 1) | (piv[c] & 1);
+      if (threadIdx.x == 0) rk[s + 1] = kq;
+      __syncthreads();
+      fl += flops_qr(N, rr) + flops_formq(N, kq);
+    }
+    for (int b = threadIdx.x; b <= n; b += blockDim.x) rg[b] = rk[b];
+    if (threadIdx.x == 0) {
+      rg[0] = 1;
+      rg[n] = 1;
+      status[inst] = max(status[inst], st);
+    }
+    __syncthreads();
+  WORK_LOOP_END
   if (acc && threadIdx.x == 0) {
     atomicAdd(acc + PH_BUILD, fl);
     atomicAdd(acc + SFFT_NPHASE_DEV + PH_BUILD, evals);
@@ -316,7 +528,8 @@ __global__ void k_mpo_interp(int n, int P, cd* W, int core_stride,
 // re-orthonormalised by QR, Y = Q_V R_V, so that X ~= (U_k R_V^H) Q_V^H exactly
 // up to the truncation, with Q_V^H right-orthonormal to machine precision
 // (no division by small singular values).
-__global__ void k_tt_round(int count, const int* n_arr, int d, int left_orth,
+__global__ void k_tt_round(const int* list, int count, int* counter, const int* n_arr, int d,
+                           int left_orth,
                            const double* tol_arr, const int* maxrank_arr,
                            cd* tt, const long long* tt_off, int core_stride,
                            int* ranks_all, cd* scratch,
@@ -329,7 +542,7 @@ __global__ void k_tt_round(int count, const int* n_arr, int d, int left_orth,
   // every thread reads them, so they live in shared memory
   __shared__ int r[SFFT_MAXN_DEV + 1];
   double fl = 0.0;
-  for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
+  WORK_LOOP_BEGIN(list, count, counter)
     const int n = n_arr[inst];
     const double tol = tol_arr[inst];
     const int rmax = maxrank_arr[inst];
@@ -445,7 +658,7 @@ __global__ void k_tt_round(int count, const int* n_arr, int d, int left_orth,
     for (int i = threadIdx.x; i <= n; i += blockDim.x) rg[i] = r[i];
     if (threadIdx.x == 0 && status) status[inst] = max(status[inst], st);
     __syncthreads();
-  }
+  WORK_LOOP_END
   if (acc && threadIdx.x == 0) atomicAdd(acc + phase, fl);
 }
 
@@ -459,7 +672,7 @@ __global__ void k_tt_round(int count, const int* n_arr, int d, int left_orth,
 // vectors V of Z are the left singular vectors of T: V becomes the output core
 // B_s[c][mu][c''] and Z V = T^H V the next carry CH. Singular values below
 // ztol * ||T|| are dropped; the final rounding sweep sets the ranks.
-__global__ void k_zipup(int count, const int* n_arr, const double* tol_arr,
+__global__ void k_zipup(const int* list, int count, int* counter, const int* n_arr, const double* tol_arr,
                         const int* maxrank_arr, const cd* A,
                         const long long* a_off, const int* a_ranks_all,
                         const cd* Wmpo, const long long* w_off,
@@ -471,7 +684,7 @@ __global__ void k_zipup(int count, const int* n_arr, const double* tol_arr,
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
   double fl = 0.0;
-  for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
+  WORK_LOOP_BEGIN(list, count, counter)
     const int n = n_arr[inst];
     const double ztol = tol_arr[inst] / sqrt((double)max(n - 1, 1));
     const int rmax = maxrank_arr[inst];
@@ -558,7 +771,7 @@ __global__ void k_zipup(int count, const int* n_arr, const double* tol_arr,
     }
     if (threadIdx.x == 0) status[inst] = max(status[inst], st);
     __syncthreads();
-  }
+  WORK_LOOP_END
   if (acc && threadIdx.x == 0) atomicAdd(acc + PH_ZIPUP, fl);
 }
 
@@ -570,7 +783,7 @@ __global__ void k_zipup(int count, const int* n_arr, const double* tol_arr,
 // 2^h row vectors v B[...]. Sites t+h..n-1: column vectors R_s[prefix] for the
 // contiguous range of prefixes u >> s, built from the top. Then
 // y_u = Lv[(u >> t) mod 2^h] . R_{t+h}[u >> (t+h)].
-__global__ void k_readout(int count, const InstParams* __restrict__ P, const cd* B,
+__global__ void k_readout(const int* list, int count, int* counter, const InstParams* __restrict__ P, const cd* B,
                           const long long* b_off, const int* b_ranks_all,
                           int core_stride, const long long* l_begin,
                           const int* tbits, const int* qarr,
@@ -579,7 +792,7 @@ __global__ void k_readout(int count, const InstParams* __restrict__ P, const cd*
                           cd* scratch, long long scratch_stride) {
   __shared__ cd Lv[(1 << READOUT_TREE_BITS) * SFFT_SLOT_RANK_DEV];
   __shared__ cd Lv2[(1 << READOUT_TREE_BITS) * SFFT_SLOT_RANK_DEV];
-  for (int inst = blockIdx.x; inst < count; inst += gridDim.x) {
+  WORK_LOOP_BEGIN(list, count, counter)
     const InstParams prm = P[inst];
     const int n = prm.n;
     const int* rb = b_ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
@@ -678,5 +891,5 @@ __global__ void k_readout(int count, const InstParams* __restrict__ P, const cd*
       lk[i] = log(prm.S0) + prm.k0 + prm.dk * (double)u;
     }
     __syncthreads();
-  }
+  WORK_LOOP_END
 }

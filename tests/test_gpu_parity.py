@@ -175,6 +175,38 @@ def test_integrand_tt_matches_dense(pricer, prob):
     assert max(tt.tt_ranks(cores)) <= 32
 
 
+def _heavy_vg(n):
+    """Variance-Gamma instances of the batch with slowly decaying integrand
+    (small T/nu): their support exceeds the TT-SVD block, so the cross
+    builder takes them."""
+    b = wl.config3_batch()
+    return [q.replace(n=n) for q in b if q.model == wl.VG and q.T / q.p[1] < 0.6][:2]
+
+
+@pytest.mark.parametrize("n", [16, 20, 22])
+def test_cross_builder_matches_dense(pricer, n):
+    for q in _heavy_vg(n):
+        cores = pricer.integrand_tt(q)
+        got = tt.tt_full(cores).reshape(-1)
+        ref = cm.integrand(q, np.arange(1 << n))
+        assert np.linalg.norm(got - ref) <= 5 * q.tol * np.linalg.norm(ref), (q, n)
+        assert max(tt.tt_ranks(cores)) <= 32
+
+
+def test_cross_builder_sampled_entries_large_n(pricer):
+    rng = np.random.default_rng(34)
+    for q in _heavy_vg(34):
+        cores = pricer.integrand_tt(q)
+        nrm = math.sqrt(abs(tt_dot(cores, cores)))
+        M = 1 << q.n
+        js = np.unique(np.concatenate([np.arange(64), rng.integers(0, M, 64),
+                                       (2.0 ** rng.uniform(6, 34, 64)).astype(np.int64)]))
+        js = js[js < M]
+        ref = cm.integrand(q, js)
+        got = np.array([tt.tt_entry(cores, [(int(j) >> (q.n - 1 - s)) & 1 for s in range(q.n)]) for j in js])
+        assert np.max(np.abs(got - ref)) <= 5 * q.tol * nrm
+
+
 # ---------------------------------------------------------- K4+K5 on x ----
 @pytest.mark.parametrize("n", [4, 9, 13])
 def test_apply_matches_dense_dft(pricer, n):
@@ -256,12 +288,29 @@ def test_config3_sample(pricer):
         idx.sort(key=lambda i: batch[i].n)
         picks += [idx[0], idx[len(idx) // 2], idx[-1]]
     probs = [batch[i] for i in picks]
-    ok = []
-    for p in probs:
-        J = cm.support_limit(p)
-        ok.append(J <= (1 << 22))
-    sel = [p for p, o in zip(probs, ok) if o]
+    # every picked instance must price; the oracle checks those whose direct
+    # sum runs over at most 2^22 points
+    strikes = [cm.strike_window(p) for p in probs]
+    _, _, status, _ = pricer.price_batch(probs, strikes, raise_on_error=False)
+    assert status == [0] * len(probs), status
+    sel = [p for p in probs if cm.support_limit(p) <= (1 << 22)]
     check_prices(pricer, sel, sample=6, seed=3)
+
+
+def test_heavy_tail_prices(pricer):
+    # cross-built integrands priced end to end; oracle over the full grid
+    probs = _heavy_vg(20)
+    check_prices(pricer, probs, sample=8, seed=5, J=1 << 20)
+
+
+def test_whole_batch_prices(pricer):
+    # every instance of the 4096-instance batch prices (status OK, finite)
+    batch = wl.config3_batch()
+    strikes = [cm.strike_window(p) for p in batch]
+    prices, _, status, _ = pricer.price_batch(batch, strikes, raise_on_error=False)
+    bad = [(i, s) for i, s in enumerate(status) if s != 0]
+    assert not bad, bad[:10]
+    assert bool(torch.isfinite(prices).all())
 
 
 # -------------------------------------------------------------- dense -----
