@@ -18,6 +18,12 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
 __device__ __forceinline__ int n_warps() { return blockDim.x >> 5; }
 
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 // Householder QR in place. W: h x p, column-major (leading dim ld). On return
 // the upper triangle of the leading min(h,p) rows holds R (W = Q R); the
 // strictly lower part holds the reflectors v (v_0 = 1 implicit) and must not
@@ -30,17 +36,24 @@ static __device__ void qr_inplace(cd* W, int ld, int h, int p, cd* taus) {
   for (int k = 0; k < kmax; ++k) {
     cd* col = W + (size_t)k * ld;
     if (warp == 0) {
-      double s = 0.0;
-      for (int i = k + 1 + lane; i < h; i += 32) s += cabs2(col[i]);
-      s = warp_sum(s);
       // the pivot is read by lane 0 only and broadcast, so lane 0 may
       // overwrite it below without racing the other lanes
       cd a0 = (lane == 0) ? col[k] : mkc(0.0, 0.0);
       a0.x = __shfl_sync(0xffffffffu, a0.x, 0);
       a0.y = __shfl_sync(0xffffffffu, a0.y, 0);
+      // norms are taken on the column scaled by its largest modulus, so that
+      // squares of tiny entries neither underflow nor turn beta into zero
+      double amax = fmax(fabs(a0.x), fabs(a0.y));
+      for (int i = k + 1 + lane; i < h; i += 32) amax = fmax(amax, fmax(fabs(col[i].x), fabs(col[i].y)));
+      amax = warp_max(amax);
+      const double inv = (amax > 1e-290) ? 1.0 / amax : 0.0;
+      double s = 0.0;
+      for (int i = k + 1 + lane; i < h; i += 32) s += cabs2(cscale(col[i], inv));
+      s = warp_sum(s);
       cd tau = mkc(0.0, 0.0);
-      if (!(s == 0.0 && a0.y == 0.0)) {
-        const double beta = -copysign(sqrt(a0.x * a0.x + a0.y * a0.y + s), a0.x);
+      if (inv != 0.0 && !(s == 0.0 && a0.y == 0.0)) {
+        const cd a0s = cscale(a0, inv);
+        const double beta = -copysign(amax * sqrt(cabs2(a0s) + s), a0.x);
         tau = mkc((beta - a0.x) / beta, -a0.y / beta);
         const cd scal = cdiv(mkc(1.0, 0.0), mkc(a0.x - beta, a0.y));
         for (int i = k + 1 + lane; i < h; i += 32) col[i] = cmul(col[i], scal);
@@ -103,7 +116,10 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
   const int lane = lane_id(), warp = warp_id(), nw = n_warps();
   if (m < 2) return 0;
   const int mp = m + (m & 1);
-  const double tol = 2.3e-16 * (double)max(p, 8);
+  // a pair counts as orthogonal once |a^H b| <= tol |a| |b|, the rounding
+  // level of a p-term complex dot product; after max_sweeps the result is
+  // accepted if no pair is worse than 1e-10 (reported as not converged otherwise)
+  const double tol = 1.0e-15 * (double)max(p, 8);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) *sh_flag = 0;
     __syncthreads();
@@ -134,7 +150,9 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
         const double ga = cabsd(g);
         if (ga > tol * sqrt(al) * sqrt(be) && ga > 1e-300) {
           const double zeta = (be - al) / (2.0 * ga);
-          const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          // hypot keeps zeta^2 from overflowing when one column is tiny: then
+          // t ~ 1/(2 zeta), the small-angle rotation
+          const double tt = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
           const double c = 1.0 / sqrt(1.0 + tt * tt);
           const double s = c * tt;
           const cd ph = mkc(g.x / ga, -g.y / ga);  // exp(-i arg g)
@@ -144,7 +162,7 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
             ca[i] = mkc(c * x.x - s * y.x, c * x.y - s * y.y);
             cb[i] = mkc(s * x.x + c * y.x, s * x.y + c * y.y);
           }
-          if (lane == 0) atomicOr(sh_flag, 1);
+          if (lane == 0) atomicOr(sh_flag, (ga > 1e-10 * sqrt(al) * sqrt(be)) ? 3 : 1);
         }
       }
       __syncthreads();
@@ -152,6 +170,7 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
     const int any = *sh_flag;
     __syncthreads();
     if (!any) return sweep + 1;
+    if (sweep == max_sweeps - 1) return (any & 2) ? -1 : max_sweeps;
   }
   return -1;
 }
@@ -258,7 +277,7 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
       rank += (so > sc) || (so == sc && o < c);
     }
     sig[rank] = sc;
-    const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+    const double inv = sc > 1e-290 ? 1.0 / sc : 0.0;
     for (int i = 0; i < p; ++i) Vs[(size_t)rank * p + i] = cscale(V[(size_t)c * p + i], inv);
   }
   __syncthreads();

@@ -76,10 +76,20 @@ __device__ __forceinline__ cd psi1(const InstParams& P, double v) {
   return cscale(cdiv(num, den), P.disc);
 }
 
+// Values below 1e-150 in modulus are returned as zero: they cannot move a
+// price, and their squares would underflow inside the factorisations.
+__device__ __forceinline__ cd flush_tiny(cd x) {
+  return (fmax(fabs(x.x), fabs(x.y)) < 1e-150) ? mkc(0.0, 0.0) : x;
+}
+
 // Integrand x_j at grid index j in [0, 2^n).
 //  SIMPSON_CM99: x_j = (-1)^j w_j eta psi1(eta j), w = 1/3, 4/3, 2/3, ...
 //  RECT_SYM (Eq. x with Delta_v k'_0 = -pi/2): x_j = i^j (-i)^N psi1(Delta_v (j - N)).
+__device__ __forceinline__ cd integrand_raw(const InstParams& P, long long j);
 __device__ __forceinline__ cd integrand(const InstParams& P, long long j) {
+  return flush_tiny(integrand_raw(P, j));
+}
+__device__ __forceinline__ cd integrand_raw(const InstParams& P, long long j) {
   if (P.quad == Q_SIMPSON) {
     const double w = (j == 0) ? (1.0 / 3.0) : ((j & 1) ? (4.0 / 3.0) : (2.0 / 3.0));
     const double sgn = (j & 1) ? -1.0 : 1.0;

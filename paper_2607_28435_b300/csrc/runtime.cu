@@ -148,20 +148,23 @@ struct PhaseScope {
 
 double* acc_ptr(sfft_ctx* ctx) { return ctx->prof ? ctx->prof_acc : nullptr; }
 
-// Andersen-Piterbarg moment-explosion time of E[S_T^p] under Heston.
+// Moment-explosion time of E[S_T^p] under Heston (Andersen & Piterbarg 2007):
+// the Riccati coefficient of v0 in log E[exp(p X_T)] solves
+// B' = a B^2 - b B + c, B(0) = 0, with a = sv^2/2, b = kappa - rho sv p,
+// c = p(p-1)/2, D = b^2 - 4ac; T* is the time B takes to reach infinity.
 double heston_explosion_time(double kappa, double sv, double rho, double p) {
   const double b = kappa - rho * sv * p;
   const double D2 = b * b - sv * sv * p * (p - 1.0);
   if (D2 >= 0.0) {
     const double d = sqrt(D2);
+    // real roots: B settles at the smaller one unless both are negative
     if (p * (p - 1.0) <= 0.0 || b >= 0.0) return INFINITY;
     if (d == 0.0) return -2.0 / b;
-    const double g = (b - d) / (b + d);
-    return log(g) / d;
+    return log((b - d) / (b + d)) / d;
   }
+  // no real roots: T* = integral_0^inf dB / (a B^2 - b B + c)
   const double dl = sqrt(-D2);
-  if (b == 0.0) return M_PI / dl;
-  return 2.0 / dl * ((b < 0.0 ? M_PI : 0.0) + atan(dl / b));
+  return 2.0 / dl * (0.5 * M_PI + atan(b / dl));
 }
 
 // Validation and planning of one problem (host side, before any launch).

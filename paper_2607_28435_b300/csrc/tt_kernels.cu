@@ -270,8 +270,8 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
 //   Phi[(i, l1), (l2, t)] = x( ((I[b-1][i] 2 + l1) 2 + l2) 2^(n-b-1) + J[b+1][t] ).
 // Left-to-right sweeps pick I[b] by maxvol on the left singular vectors of Phi,
 // right-to-left sweeps pick J[b] from its right singular vectors; the singular
-// values set the rank (relative threshold 0.1 tol, cap max_rank). Sweeps stop
-// when the ranks repeat. Assembly then runs one left-to-right pass: the fibre
+// values set the rank (relative threshold 0.01 tol, cap max_rank). Sweeps stop
+// when the ranks repeat, after at least three. Assembly then runs one left-to-right pass: the fibre
 // matrix F_s[(i, l), t] = x((I[s][i] 2 + l) 2^(n-s-1) + J[s+1][t]) is factored
 // F = Q R, maxvol on Q gives I[s+1], and the core is Q Q[piv]^{-1}, which
 // interpolates x on the cross (Oseledets & Tyrtyshnikov 2010; Savostyanov &
@@ -315,7 +315,7 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
     const InstParams prm = P[inst];
     const int n = prm.n;
     const int rmax = min(prm.max_rank, CROSS_R);
-    const double ctol = 0.1 * prm.tol;
+    const double ctol = 0.01 * prm.tol;
     int st = 0;
     cd* base = tt + tt_off[inst];
     int* rg = ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
@@ -397,7 +397,7 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
       __syncthreads();
       for (int b = threadIdx.x; b <= n; b += blockDim.x) rprev[b] = rk[b];
       __syncthreads();
-      if (same && sw >= 1) break;
+      if (same && sw >= 2) break;
     }
     // ---- assembly: interpolatory cores, left to right
     if (threadIdx.x == 0) Iset[0] = 0;

@@ -357,6 +357,31 @@ def test_invalid_inputs_are_rejected(pricer):
     assert np.all(np.isnan(c[:q])) and np.all(np.isfinite(c[q:]))
 
 
+def _heston_explosion_ode(kappa, sv, rho, p, tmax):
+    """Moment-explosion time by integrating the Riccati equation of the v0
+    coefficient, B' = p(p-1)/2 + (rho sv p - kappa) B + sv^2 B^2 / 2, until B
+    passes 1e8 (independent of the closed form the library uses)."""
+    from scipy.integrate import solve_ivp
+    f = lambda t, B: [0.5 * p * (p - 1) + (rho * sv * p - kappa) * B[0] + 0.5 * sv * sv * B[0] ** 2]
+    ev = lambda t, B: B[0] - 1e8
+    ev.terminal = True
+    r = solve_ivp(f, [0, tmax], [0.0], events=ev, rtol=1e-10, atol=1e-12, max_step=0.01)
+    return r.t_events[0][0] if len(r.t_events[0]) else math.inf
+
+
+def test_heston_moment_check_matches_riccati(pricer):
+    from paper_2607_28435_b300 import sfft
+    cases = [(1.1129, 0.0347, 0.6659, -0.021, 0.0653), (0.528, 0.0239, 0.535, -0.1916, 0.0336),
+             (0.5, 0.04, 1.0, 0.0, 0.04), (2.0, 0.04, 0.9, -0.9, 0.04), (0.3, 0.04, 1.2, 0.5, 0.04)]
+    for par in cases:
+        tstar = _heston_explosion_ode(par[0], par[2], par[3], 2.5, 40.0)
+        for T in (0.5 * tstar, 1.2 * tstar) if math.isfinite(tstar) else (3.0,):
+            q = wl.Problem(cf.HESTON, par, r=0.02, T=T, alpha=1.5, n=12)
+            _, _, status, _ = pricer.price_batch([q], [cm.strike_window(q, qmax=8)], raise_on_error=False)
+            want = sfft.SFFT_EMOMENT if T > tstar else 0
+            assert status == [want], (par, T, tstar, status)
+
+
 def test_empty_batch_and_zero_strikes(pricer):
     prices, logk, status, _ = pricer.price_batch([], [])
     assert status == []
