@@ -72,7 +72,8 @@ static __device__ void qr_inplace(cd* W, int ld, int h, int p, cd* taus) {
         dot = warp_csum(dot);
         const cd f = cmul(ctau, dot);
         if (lane == 0) cj[k] = csub(cj[k], f);
-        for (int i = k + 1 + lane; i < h; i += 32) cj[i] = csub(cj[i], cmul(col[i], f));
+        const cd nf = cneg(f);
+        for (int i = k + 1 + lane; i < h; i += 32) cj[i] = cfma(col[i], nf, cj[i]);
       }
     }
     __syncthreads();
@@ -100,7 +101,8 @@ static __device__ void form_q(const cd* W, int ld, int h, int kq, const cd* taus
         dot = warp_csum(dot);
         const cd f = cmul(tau, dot);
         if (lane == 0) qj[k] = csub(qj[k], f);
-        for (int i = k + 1 + lane; i < h; i += 32) qj[i] = csub(qj[i], cmul(v[i], f));
+        const cd nf = cneg(f);
+        for (int i = k + 1 + lane; i < h; i += 32) qj[i] = cfma(v[i], nf, qj[i]);
       }
     }
     __syncthreads();
@@ -110,12 +112,18 @@ static __device__ void form_q(const cd* W, int ld, int h, int kq, const cd* taus
 // One-sided Jacobi (Hestenes): rotates the m columns of L (p rows, column
 // major, leading dim ld) until every pair is orthogonal to working precision,
 // |l_a^H l_b| <= tol * ||l_a|| ||l_b||. Columns are visited in round-robin
-// tournament order, one pair per warp. Returns the number of sweeps used, or
-// -1 if max_sweeps did not reach convergence.
+// tournament order. A pair is handled by a group of 8 lanes (four pairs per
+// warp): the columns are short (p <= 64), so narrower groups spend fewer lanes
+// on the per-pair rotation arithmetic, which every lane of a group repeats.
+// Each warp runs the same number of group iterations, so the group reductions
+// can use full-warp shuffles. Returns the number of sweeps used, or -1 if
+// max_sweeps did not reach convergence.
 static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int* sh_flag) {
   const int lane = lane_id(), warp = warp_id(), nw = n_warps();
+  const int sub = lane & 7, grp = lane >> 3;  // 4 groups of 8 lanes per warp
   if (m < 2) return 0;
   const int mp = m + (m & 1);
+  const int npair = mp / 2;
   // a pair counts as orthogonal once |a^H b| <= tol |a| |b|, the rounding
   // level of a p-term complex dot product; after max_sweeps the result is
   // accepted if no pair is worse than 1e-10 (reported as not converged otherwise)
@@ -124,45 +132,57 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
     if (threadIdx.x == 0) *sh_flag = 0;
     __syncthreads();
     for (int t = 0; t < mp - 1; ++t) {
-      for (int e = warp; e < mp / 2; e += nw) {
-        int a, b;
-        if (e == 0) {
-          a = t;
-          b = mp - 1;
-        } else {
-          a = (t + e) % (mp - 1);
-          b = (t - e + mp - 1) % (mp - 1);
+      for (int e0 = 4 * warp; e0 < npair; e0 += 4 * nw) {
+        const int e = e0 + grp;
+        int a = 0, b = 0;
+        bool live = e < npair;
+        if (live) {
+          if (e == 0) {
+            a = t;
+            b = mp - 1;
+          } else {
+            a = (t + e) % (mp - 1);
+            b = (t - e + mp - 1) % (mp - 1);
+          }
+          live = a < m && b < m;
         }
-        if (a >= m || b >= m) continue;
         cd* ca = L + (size_t)a * ld;
         cd* cb = L + (size_t)b * ld;
-        double al = 0.0, be = 0.0;
-        cd g = mkc(0.0, 0.0);
-        for (int i = lane; i < p; i += 32) {
-          const cd x = ca[i], y = cb[i];
-          al += cabs2(x);
-          be += cabs2(y);
-          g = cfmac(x, y, g);
+        double al = 0.0, be = 0.0, gx = 0.0, gy = 0.0;
+        if (live)
+          for (int i = sub; i < p; i += 8) {
+            const cd x = ca[i], y = cb[i];
+            al = fma(x.x, x.x, fma(x.y, x.y, al));
+            be = fma(y.x, y.x, fma(y.y, y.y, be));
+            gx = fma(x.x, y.x, fma(x.y, y.y, gx));
+            gy = fma(x.x, y.y, fma(-x.y, y.x, gy));
+          }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          gx += __shfl_xor_sync(0xffffffffu, gx, o);
+          gy += __shfl_xor_sync(0xffffffffu, gy, o);
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        g = warp_csum(g);
-        const double ga = cabsd(g);
-        if (ga > tol * sqrt(al) * sqrt(be) && ga > 1e-300) {
+        if (!live) continue;
+        const double ga = sqrt(fma(gx, gx, gy * gy));
+        const double nab = sqrt(al) * sqrt(be);
+        if (ga > tol * nab && ga > 1e-300) {
           const double zeta = (be - al) / (2.0 * ga);
           // hypot keeps zeta^2 from overflowing when one column is tiny: then
           // t ~ 1/(2 zeta), the small-angle rotation
           const double tt = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
-          const double c = 1.0 / sqrt(1.0 + tt * tt);
+          const double c = rsqrt(fma(tt, tt, 1.0));
           const double s = c * tt;
-          const cd ph = mkc(g.x / ga, -g.y / ga);  // exp(-i arg g)
-          for (int i = lane; i < p; i += 32) {
+          const double ig = 1.0 / ga;
+          const cd ph = mkc(gx * ig, -gy * ig);  // exp(-i arg g)
+          for (int i = sub; i < p; i += 8) {
             const cd x = ca[i];
             const cd y = cmul(cb[i], ph);
-            ca[i] = mkc(c * x.x - s * y.x, c * x.y - s * y.y);
-            cb[i] = mkc(s * x.x + c * y.x, s * x.y + c * y.y);
+            ca[i] = mkc(fma(c, x.x, -s * y.x), fma(c, x.y, -s * y.y));
+            cb[i] = mkc(fma(s, x.x, c * y.x), fma(s, x.y, c * y.y));
           }
-          if (lane == 0) atomicOr(sh_flag, (ga > 1e-10 * sqrt(al) * sqrt(be)) ? 3 : 1);
+          if (sub == 0) atomicOr(sh_flag, (ga > 1e-10 * nab) ? 3 : 1);
         }
       }
       __syncthreads();
