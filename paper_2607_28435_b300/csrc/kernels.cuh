@@ -45,7 +45,23 @@ __global__ void k_tt_round(const int* list, int count, int* counter, const int* 
                            int left_orth, const double* tol_arr,
                            const int* maxrank_arr, cd* tt, const long long* tt_off,
                            int core_stride, int* ranks_all, cd* scratch,
-                           long long scratch_stride, int* status, int hb, double* acc, int phase);
+                           long long scratch_stride, int* status, int hb, double* acc, int phase,
+                           int pmax, int vcap);
+
+// Shared memory of k_tt_round for physical dimension d: panels of at most
+// SFFT_SLOT_RANK_DEV columns; W holds a (d r) x r block, V the explicit Q.
+struct RoundSmem {
+  int pmax, hb, vcap;
+  size_t bytes;
+};
+inline RoundSmem round_smem(int d) {
+  RoundSmem r;
+  r.pmax = SFFT_SLOT_RANK_DEV;
+  r.hb = (d - 1) * SFFT_SLOT_RANK_DEV;  // W = (pmax + hb) pmax >= d r x r
+  r.vcap = d * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV;
+  r.bytes = sizeof(cd) * ((size_t)(r.pmax + r.hb) * r.pmax + r.vcap + r.pmax) + sizeof(double) * r.pmax + 320;
+  return r;
+}
 __global__ void k_zipup(const int* list, int count, int* counter, const int* n_arr,
                         const double* tol_arr, const int* maxrank_arr,
                         const cd* A, const long long* a_off, const int* a_ranks_all,

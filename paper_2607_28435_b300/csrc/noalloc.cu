@@ -24,7 +24,6 @@
 namespace {
 
 const int kThreadsNa = 256;
-const int kHbNa = 32;
 
 // layout of the static scratch (byte offsets, each 256-byte aligned)
 constexpr size_t kSlotElems = SFFT_CORE_STRIDE_D4;  // one core slot, any d <= 4
@@ -80,7 +79,7 @@ sfft_status scratch_on_current_device(unsigned char** out, char* errbuf, int32_t
     g_dev_ptr[dev] = p;
   }
   if (!g_attr_set[dev]) {
-    const int smem = (int)la::ts_svd_smem_bytes(LA_MAXP, kHbNa) + 256;
+    const int smem = (int)round_smem(4).bytes;
     if (cudaFuncSetAttribute(k_tt_round, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess) {
       say(errbuf, errlen, "cudaFuncSetAttribute failed");
@@ -155,10 +154,11 @@ extern "C" sfft_status sfft_tt_round_noalloc(int32_t n, int32_t d, const int32_t
   NaParams hp = {n, max_rank ? max_rank : SFFT_DEFAULT_MAX_RANK, tol, 0, 0, 0};
   NA_CK(cudaMemcpyAsync(ranks, rk, sizeof rk, cudaMemcpyHostToDevice, sm), "rank upload failed");
   NA_CK(cudaMemcpyAsync(prm, &hp, sizeof hp, cudaMemcpyHostToDevice, sm), "parameter upload failed");
-  const size_t smem = la::ts_svd_smem_bytes(LA_MAXP, kHbNa) + 256;
-  k_tt_round<<<1, kThreadsNa, smem, sm>>>(nullptr, 1, nullptr, &prm->n, d, 1, &prm->tol, &prm->maxrank, tt, &prm->off,
-                                         stride, ranks, tmp, SFFT_ROUND_SCRATCH, &prm->status, kHbNa,
-                                         nullptr, PH_ROUND);
+  const RoundSmem rsm = round_smem(d);
+  k_tt_round<<<1, kThreadsNa, rsm.bytes, sm>>>(nullptr, 1, nullptr, &prm->n, d, 1, &prm->tol,
+                                              &prm->maxrank, tt, &prm->off, stride, ranks, tmp,
+                                              SFFT_ROUND_SCRATCH, &prm->status, rsm.hb, nullptr, PH_ROUND,
+                                              rsm.pmax, rsm.vcap);
   NA_CK(cudaGetLastError(), "launch of the rounding kernel failed");
   NaParams back;
   NA_CK(cudaMemcpyAsync(rk, ranks, sizeof rk, cudaMemcpyDeviceToHost, sm), "rank download failed");

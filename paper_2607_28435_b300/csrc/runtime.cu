@@ -269,7 +269,8 @@ sfft_status set_smem_attrs(sfft_ctx* ctx) {
   const int sm = (int)svd_smem();
   CK(cudaFuncSetAttribute(k_integrand_ttsvd, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   CK(cudaFuncSetAttribute(k_integrand_cross, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_tt_round, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_tt_round, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)round_smem(4).bytes));
   CK(cudaFuncSetAttribute(k_zipup, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   CK(cudaFuncSetAttribute(k_fft_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
   return SFFT_OK;
@@ -338,10 +339,12 @@ sfft_status get_mpo(sfft_ctx* ctx, int n, double tol, const MpoEntry** out) {
   if (s) return s;
   {
     PhaseScope ps(ctx, PH_MPO);
-    k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(
+    const RoundSmem rs = round_smem(4);
+    k_tt_round<<<1, kThreads, rs.bytes, ctx->stream>>>(
         nullptr, 1, nullptr, reinterpret_cast<int*>(a), 4, 1, reinterpret_cast<double*>(a + 8),
         reinterpret_cast<int*>(a + 16), W, reinterpret_cast<long long*>(a + 24), SFFT_CORE_STRIDE_D4,
-        rk, reinterpret_cast<cd*>(scr), SFFT_ROUND_SCRATCH, nullptr, kHb, acc_ptr(ctx), PH_MPO);
+        rk, reinterpret_cast<cd*>(scr), SFFT_ROUND_SCRATCH, nullptr, rs.hb, acc_ptr(ctx), PH_MPO,
+        rs.pmax, rs.vcap);
   }
   CK(cudaGetLastError());
   e.ranks.resize(SFFT_MAX_N + 1);
@@ -486,13 +489,14 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     }
     CK(cudaGetLastError());
     // interpolatory cores -> right-orthonormal, truncated to tol
-    const int g2 = std::min(ncr, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, smem));
+    const RoundSmem rs = round_smem(2);
+    const int g2 = std::min(ncr, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, rs.bytes));
     if ((s = ensure(ctx, "xround_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * g2, &p))) return s;
     PhaseScope ps(ctx, PH_BUILD);
-    k_tt_round<<<g2, kThreads, smem, ctx->stream>>>(cross_dev, ncr, ctr + 2, b.n_arr, 2, 1, b.tol_arr,
-                                                    b.maxr_arr, b.A, b.a_off, SFFT_CORE_STRIDE_D2, b.a_ranks,
-                                                    reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH, b.status,
-                                                    kHb, acc_ptr(ctx), PH_BUILD);
+    k_tt_round<<<g2, kThreads, rs.bytes, ctx->stream>>>(cross_dev, ncr, ctr + 2, b.n_arr, 2, 1, b.tol_arr,
+                                                        b.maxr_arr, b.A, b.a_off, SFFT_CORE_STRIDE_D2, b.a_ranks,
+                                                        reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH, b.status,
+                                                        rs.hb, acc_ptr(ctx), PH_BUILD, rs.pmax, rs.vcap);
   }
   CK(cudaGetLastError());
   if (!apply) return SFFT_OK;
@@ -519,14 +523,16 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
         SFFT_ZIP_SCRATCH, b.status, kHb, acc_ptr(ctx));
   }
   CK(cudaGetLastError());
-  grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, smem));
+  const RoundSmem rs2 = round_smem(2);
+  grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, rs2.bytes));
   if ((s = ensure(ctx, "round_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * grid, &p))) return s;
   {
     PhaseScope ps(ctx, PH_ROUND);
-    k_tt_round<<<grid, kThreads, smem, ctx->stream>>>(all_dev, cnt, ctr + 4, b.n_arr, 2, 0, b.tol_arr, b.maxr_arr, b.B,
-                                                      b.a_off, SFFT_CORE_STRIDE_D2, b.b_ranks,
-                                                      reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH,
-                                                      b.status, kHb, acc_ptr(ctx), PH_ROUND);
+    k_tt_round<<<grid, kThreads, rs2.bytes, ctx->stream>>>(all_dev, cnt, ctr + 4, b.n_arr, 2, 0, b.tol_arr,
+                                                           b.maxr_arr, b.B, b.a_off, SFFT_CORE_STRIDE_D2,
+                                                           b.b_ranks, reinterpret_cast<cd*>(p),
+                                                           SFFT_ROUND_SCRATCH, b.status, rs2.hb,
+                                                           acc_ptr(ctx), PH_ROUND, rs2.pmax, rs2.vcap);
   }
   CK(cudaGetLastError());
   return SFFT_OK;
@@ -797,9 +803,11 @@ sfft_status sfft_tt_round(sfft_ctx* ctx, int32_t n, int32_t d, const int32_t* in
     return s;
   void* scr;
   if ((s = ensure(ctx, "rt_scratch", sizeof(cd) * SFFT_ROUND_SCRATCH, &scr))) return s;
-  k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(nullptr, 1, nullptr, nd, d, 1, td, md, T, od, stride,
-                                                      reinterpret_cast<int*>(rd), reinterpret_cast<cd*>(scr),
-                                                      SFFT_ROUND_SCRATCH, sd, kHb, nullptr, PH_ROUND);
+  const RoundSmem rs = round_smem(d);
+  k_tt_round<<<1, kThreads, rs.bytes, ctx->stream>>>(nullptr, 1, nullptr, nd, d, 1, td, md, T, od, stride,
+                                                    reinterpret_cast<int*>(rd), reinterpret_cast<cd*>(scr),
+                                                    SFFT_ROUND_SCRATCH, sd, rs.hb, nullptr, PH_ROUND, rs.pmax,
+                                                    rs.vcap);
   CK(cudaGetLastError());
   int st = 0;
   CK(cudaMemcpyAsync(&st, sd, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -851,9 +859,11 @@ sfft_status sfft_tt_apply_qft(sfft_ctx* ctx, int32_t n, const int32_t* in_ranks,
       SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(scr), SFFT_ZIP_SCRATCH, sd, kHb,
       nullptr);
   CK(cudaGetLastError());
-  k_tt_round<<<1, kThreads, svd_smem(), ctx->stream>>>(nullptr, 1, nullptr, nd, 2, 0, td, md, B, od, SFFT_CORE_STRIDE_D2,
-                                                      reinterpret_cast<int*>(rb), reinterpret_cast<cd*>(scr),
-                                                      SFFT_ROUND_SCRATCH, sd, kHb, nullptr, PH_ROUND);
+  const RoundSmem rs = round_smem(2);
+  k_tt_round<<<1, kThreads, rs.bytes, ctx->stream>>>(nullptr, 1, nullptr, nd, 2, 0, td, md, B, od,
+                                                    SFFT_CORE_STRIDE_D2, reinterpret_cast<int*>(rb),
+                                                    reinterpret_cast<cd*>(scr), SFFT_ROUND_SCRATCH, sd, rs.hb,
+                                                    nullptr, PH_ROUND, rs.pmax, rs.vcap);
   CK(cudaGetLastError());
   int st = 0;
   CK(cudaMemcpyAsync(&st, sd, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

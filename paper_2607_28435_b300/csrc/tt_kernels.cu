@@ -34,13 +34,13 @@ struct SvdSmem {
   int* misc;
 };
 
-__device__ SvdSmem carve_svd_smem(void* raw, int p, int hb) {
+__device__ SvdSmem carve_svd_smem(void* raw, int p, int hb, int vcap = 0) {
   SvdSmem s;
   char* c = reinterpret_cast<char*>(raw);
   s.W = reinterpret_cast<cd*>(c);
   c += sizeof(cd) * (size_t)(p + hb) * p;
   s.V = reinterpret_cast<cd*>(c);
-  c += sizeof(cd) * (size_t)p * p;
+  c += sizeof(cd) * (size_t)(vcap > p * p ? vcap : p * p);
   s.sig = reinterpret_cast<double*>(c);
   c += sizeof(double) * p;
   s.tau = reinterpret_cast<cd*>(c);
@@ -534,9 +534,11 @@ __global__ void k_tt_round(const int* list, int count, int* counter, const int* 
                            cd* tt, const long long* tt_off, int core_stride,
                            int* ranks_all, cd* scratch,
                            long long scratch_stride, int* status, int hb,
-                           double* acc, int phase) {
+                           double* acc, int phase, int pmax, int vcap) {
+  // shared memory sized by the launch: panels of at most pmax columns, Q
+  // blocks of vcap elements (see round_smem_bytes on the host)
   extern __shared__ double4 smem_raw[];
-  SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
+  SvdSmem sm = carve_svd_smem(smem_raw, pmax, hb, vcap);
   __shared__ double red[32];
   // ranks of the instance in flight: thread 0 updates them between barriers,
   // every thread reads them, so they live in shared memory
@@ -607,7 +609,7 @@ __global__ void k_tt_round(const int* list, int count, int* counter, const int* 
           Zt[idx] = cconj(Gs[(size_t)a * q + row]);
         }
         __syncthreads();
-        TsSvd sv = ts_svd(Zt, q, r0, r0, sm.W, SVD_WCAP(hb), sm.V, sm.sig, sm.tau, sm.flag);
+        TsSvd sv = ts_svd(Zt, q, r0, r0, sm.W, (pmax + hb) * pmax, sm.V, sm.sig, sm.tau, sm.flag);
         if (sv.sweeps < 0) st = SFFT_ENOCONV_DEV;
         int k = trunc_rank(sm.sig, sv.m, delta);
         if (k > rmax) {
