@@ -232,8 +232,12 @@ __host__ __device__ inline double flops_gemm(double m, double n, double k) { ret
 // descending order, with V[:, i] the vector of sig[i].
 // W: smem work of wcap >= (p + 1) * p + p elements; row blocks are as tall
 // as W allows (hb = wcap / p - p rows below the running R).
-static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, int wcap, cd* V,
-                        double* sig, cd* taus, int* sh_flag) {
+// Streaming Householder QR of a tall Z (q x p, row-major, leading dim ldz,
+// read only): row blocks of hb = wcap/p - p rows are stacked under the running
+// R and factored again. On return R (nR x p, upper triangular, nR = min(q, p))
+// is in the top rows of W, column-major with leading dim p + hb.
+static __device__ int stream_qr(const cd* Z, long long q, int p, int ldz, cd* W, int wcap, cd* taus,
+                                int* ldw_out) {
   const int hb = wcap / p - p;
   const int ldw = p + hb;
   int nR = 0;  // rows of R currently held at the top of W
@@ -256,6 +260,15 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
     __syncthreads();
     if (q == 0) break;
   }
+  *ldw_out = ldw;
+  return nR;
+}
+
+static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, int wcap, cd* V,
+                        double* sig, cd* taus, int* sh_flag) {
+  const int hb = wcap / p - p;
+  int ldw;
+  const int nR = stream_qr(Z, q, p, ldz, W, wcap, taus, &ldw);
   const int m = nR;
   // L = R^H (p x m) into V
   for (int idx = threadIdx.x; idx < p * m; idx += blockDim.x) {
@@ -444,6 +457,141 @@ static __device__ void maxvol(const cd* A, int lda, int N, int r, int* piv, cd* 
     if (threadIdx.x == 0) piv[j] = i;
     __syncthreads();
   }
+}
+
+// Truncated row-space basis of a tall Z (q x p) by rank-revealing QR.
+// Z = Q R by the streaming QR; then R P = Q2 R2 by Householder QR with column
+// pivoting (the column of largest remaining norm first), so that the trailing
+// block R2[k:, k:] has Frobenius norm equal to the error of keeping k rows.
+// k is the smallest rank with that norm <= delta_rel * ||Z||_F (k >= 1,
+// k <= kmax). The kept rows span (R2[:k] P^T); B (p x k, column-major, leading
+// dim p, in W on return) is an orthonormal basis of their conjugate span, so
+// Z ~= Z B B^H with error at most the trailing norm.
+// Smem: W (wcap >= (p + 1) p), V (p x p), taus and cn (p entries each), perm (p ints).
+struct RowBasis {
+  int k;
+  double flops;
+};
+
+static __device__ RowBasis rrqr_basis(const cd* Z, long long q, int p, int ldz, cd* W, int wcap, cd* V,
+                                      double delta_rel, int kmax, cd* taus, double* cn, int* perm,
+                                      double* red_d, int* red_i) {
+  const int lane = lane_id(), warp = warp_id(), nw = n_warps();
+  int ldw;
+  const int m = stream_qr(Z, q, p, ldz, W, wcap, taus, &ldw);
+  RowBasis out;
+  out.flops = 0.0;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) perm[j] = j;
+  __syncthreads();
+  const int kmax_q = min(m, p);
+  double total = 0.0;
+  // pivoted Householder QR of R (m x p) in place
+  for (int k = 0; k < kmax_q; ++k) {
+    for (int j = k + warp; j < p; j += nw) {
+      const cd* cj = W + (size_t)j * ldw;
+      double amax = 0.0;
+      for (int i = k + lane; i < m; i += 32) amax = fmax(amax, fmax(fabs(cj[i].x), fabs(cj[i].y)));
+      amax = warp_max(amax);
+      const double inv = amax > 1e-290 ? 1.0 / amax : 0.0;
+      double ss = 0.0;
+      for (int i = k + lane; i < m; i += 32) ss += cabs2(cscale(cj[i], inv));
+      ss = warp_sum(ss);
+      if (lane == 0) cn[j] = ss * amax * amax;
+    }
+    __syncthreads();
+    if (k == 0) {
+      for (int j = 0; j < p; ++j) total += cn[j];
+    }
+    const int jm = k + cta_argmax(p - k, [&](int t) { return cn[k + t]; }, red_d, red_i);
+    if (jm != k) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const cd t = W[(size_t)k * ldw + i];
+        W[(size_t)k * ldw + i] = W[(size_t)jm * ldw + i];
+        W[(size_t)jm * ldw + i] = t;
+      }
+      if (threadIdx.x == 0) {
+        const int t = perm[k];
+        perm[k] = perm[jm];
+        perm[jm] = t;
+      }
+    }
+    __syncthreads();
+    // one Householder step on column k (rows k..m-1), applied to columns > k
+    cd* col = W + (size_t)k * ldw;
+    if (warp == 0) {
+      cd a0 = (lane == 0) ? col[k] : mkc(0.0, 0.0);
+      a0.x = __shfl_sync(0xffffffffu, a0.x, 0);
+      a0.y = __shfl_sync(0xffffffffu, a0.y, 0);
+      double amax = fmax(fabs(a0.x), fabs(a0.y));
+      for (int i = k + 1 + lane; i < m; i += 32) amax = fmax(amax, fmax(fabs(col[i].x), fabs(col[i].y)));
+      amax = warp_max(amax);
+      const double inv = (amax > 1e-290) ? 1.0 / amax : 0.0;
+      double ss = 0.0;
+      for (int i = k + 1 + lane; i < m; i += 32) ss += cabs2(cscale(col[i], inv));
+      ss = warp_sum(ss);
+      cd tau = mkc(0.0, 0.0);
+      if (inv != 0.0 && !(ss == 0.0 && a0.y == 0.0)) {
+        const cd a0s = cscale(a0, inv);
+        const double beta = -copysign(amax * sqrt(cabs2(a0s) + ss), a0.x);
+        tau = mkc((beta - a0.x) / beta, -a0.y / beta);
+        const cd scal = cdiv(mkc(1.0, 0.0), mkc(a0.x - beta, a0.y));
+        for (int i = k + 1 + lane; i < m; i += 32) col[i] = cmul(col[i], scal);
+        if (lane == 0) col[k] = mkc(beta, 0.0);
+      }
+      if (lane == 0) taus[k] = tau;
+    }
+    __syncthreads();
+    const cd tau = taus[k];
+    if (tau.x != 0.0 || tau.y != 0.0) {
+      const cd ctau = cconj(tau);
+      for (int j = k + 1 + warp; j < p; j += nw) {
+        cd* cj = W + (size_t)j * ldw;
+        cd dot = (lane == 0) ? cj[k] : mkc(0.0, 0.0);
+        for (int i = k + 1 + lane; i < m; i += 32) dot = cfmac(col[i], cj[i], dot);
+        dot = warp_csum(dot);
+        const cd f = cmul(ctau, dot);
+        const cd nf = cneg(f);
+        if (lane == 0) cj[k] = csub(cj[k], f);
+        for (int i = k + 1 + lane; i < m; i += 32) cj[i] = cfma(col[i], nf, cj[i]);
+      }
+    }
+    __syncthreads();
+    out.flops += 20.0 * (m - k) * (p - k);
+  }
+  // rank from the trailing row norms of R2 (upper trapezoidal, row i from column i)
+  for (int i = warp; i < kmax_q; i += nw) {
+    double ss = 0.0;
+    for (int j = i + lane; j < p; j += 32) {
+      const cd v = W[(size_t)j * ldw + i];
+      ss += cabs2(v);
+    }
+    ss = warp_sum(ss);
+    if (lane == 0) cn[i] = ss;
+  }
+  __syncthreads();
+  const double delta = delta_rel * sqrt(total);
+  int k = kmax_q;
+  {
+    double tail = 0.0;
+    for (int i = kmax_q - 1; i >= 0; --i) {
+      tail += cn[i];
+      if (sqrt(tail) <= delta) k = i; else break;
+    }
+  }
+  k = max(k, 1);
+  k = min(k, kmax);
+  out.k = k;
+  // M = (R2[:k] P^T)^H (p x k) into V: M[perm[j], c] = conj(R2[c, j])
+  for (int idx = threadIdx.x; idx < p * k; idx += blockDim.x) {
+    const int c = idx / p, j = idx - c * p;
+    V[(size_t)c * p + perm[j]] = (j >= c) ? cconj(W[(size_t)j * ldw + c]) : mkc(0.0, 0.0);
+  }
+  __syncthreads();
+  // B = orthonormal basis of span(M), written to W (leading dim p)
+  qr_inplace(V, p, p, k, taus);
+  form_q(V, p, p, min(p, k), taus, W, p);
+  out.flops += flops_qr(p, k) + flops_formq(p, min(p, k));
+  return out;
 }
 
 }  // namespace la

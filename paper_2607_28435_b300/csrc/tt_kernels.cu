@@ -685,6 +685,9 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
                         int* status, int hb, double* acc) {
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
+  __shared__ int zperm[LA_MAXP];
+  __shared__ double zred_d[32];
+  __shared__ int zred_i[32];
   double fl = 0.0;
   WORK_LOOP_BEGIN(list, count, counter)
     const int n = n_arr[inst];
@@ -750,25 +753,25 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
         __syncthreads();
         break;
       }
-      TsSvd sv = ts_svd(Z, q, p, p, sm.W, SVD_WCAP(hb), sm.V, sm.sig, sm.tau, sm.flag);
-      if (sv.sweeps < 0) st = SFFT_ENOCONV_DEV;
-      double s2 = 0.0;
-      for (int i = 0; i < sv.m; ++i) s2 += sm.sig[i] * sm.sig[i];
-      int k = trunc_rank(sm.sig, sv.m, ztol * sqrt(s2));
+      // rank-revealing QR gives the kept left subspace of T (truncation error
+      // = trailing norm of the pivoted R); the final rounding makes it optimal
+      const RowBasis rbz = rrqr_basis(Z, q, p, p, sm.W, SVD_WCAP(hb), sm.V, ztol, SFFT_SLOT_RANK_DEV + 1,
+                                      sm.tau, sm.sig, zperm, zred_d, zred_i);
+      int k = rbz.k;
       if (k > SFFT_SLOT_RANK_DEV) {
         st = SFFT_ERANK_DEV;
         k = SFFT_SLOT_RANK_DEV;
       }
       (void)rmax;
-      // B_s[c][mu][c''] = V[(c, mu), c'']
+      // B_s[c][mu][c''] = B[(c, mu), c''] (B in W, column-major, leading dim p)
       for (int idx = threadIdx.x; idx < p * k; idx += blockDim.x) {
         const int row = idx / k, cc = idx - row * k;
-        Bs[idx] = sm.V[(size_t)cc * p + row];
+        Bs[idx] = sm.W[(size_t)cc * p + row];
       }
-      gemm_zv(Z, q, p, sm.V, k, CH);
+      gemm_zv(Z, q, p, sm.W, k, CH);
       if (threadIdx.x == 0) rb[s + 1] = k;
       __syncthreads();
-      fl += sv.flops + flops_gemm(q, p, k);
+      fl += rbz.flops + flops_gemm(q, p, k);
       rc = k;
     }
     if (threadIdx.x == 0) status[inst] = max(status[inst], st);
