@@ -54,6 +54,16 @@ struct RoundSmem {
   int pmax, hb, vcap;
   size_t bytes;
 };
+// Shared memory of k_zipup: 8-row panel blocks at 64 columns and a
+// 64 x (rank cap + 1) basis block, small enough for two CTAs per SM.
+inline RoundSmem zip_smem() {
+  RoundSmem r;
+  r.pmax = LA_MAXP;
+  r.hb = 8;
+  r.vcap = LA_MAXP * (SFFT_SLOT_RANK_DEV + 1);
+  r.bytes = sizeof(cd) * ((size_t)(r.pmax + r.hb) * r.pmax + r.vcap + r.pmax) + sizeof(double) * r.pmax + 320;
+  return r;
+}
 inline RoundSmem round_smem(int d) {
   RoundSmem r;
   r.pmax = SFFT_SLOT_RANK_DEV;

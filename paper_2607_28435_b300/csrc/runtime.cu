@@ -512,15 +512,16 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   if ((s = upload(ctx, "w_off", w_off, &b.w_off))) return s;
   CK(cudaMemcpyAsync(b.w_ranks, w_ranks.data(), sizeof(int) * w_ranks.size(), cudaMemcpyHostToDevice,
                      ctx->stream));
-  int grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, smem));
+  const RoundSmem zs = zip_smem();
+  int grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, zs.bytes));
   if ((s = ensure(ctx, "zip_scratch", sizeof(cd) * (size_t)SFFT_ZIP_SCRATCH * grid, &p))) return s;
   {
     PhaseScope ps(ctx, PH_ZIPUP);
-    k_zipup<<<grid, kThreads, smem, ctx->stream>>>(
+    k_zipup<<<grid, kThreads, zs.bytes, ctx->stream>>>(
         all_dev, cnt, ctr + 3, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
         reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
         SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
-        SFFT_ZIP_SCRATCH, b.status, kHb, acc_ptr(ctx));
+        SFFT_ZIP_SCRATCH, b.status, zs.hb, acc_ptr(ctx));
   }
   CK(cudaGetLastError());
   const RoundSmem rs2 = round_smem(2);
@@ -853,10 +854,11 @@ sfft_status sfft_tt_apply_qft(sfft_ctx* ctx, int32_t n, const int32_t* in_ranks,
   void* scr;
   if ((s = ensure(ctx, "ap_scratch", sizeof(cd) * (size_t)(SFFT_ZIP_SCRATCH + SFFT_ROUND_SCRATCH), &scr)))
     return s;
-  k_zipup<<<1, kThreads, svd_smem(), ctx->stream>>>(
+  const RoundSmem zs = zip_smem();
+  k_zipup<<<1, kThreads, zs.bytes, ctx->stream>>>(
       nullptr, 1, nullptr, nd, td, md, A, od, reinterpret_cast<int*>(ra), reinterpret_cast<const cd*>(ctx->mpo_pool.p), wd,
       reinterpret_cast<int*>(rw), B, od, reinterpret_cast<int*>(rb), SFFT_CORE_STRIDE_D2,
-      SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(scr), SFFT_ZIP_SCRATCH, sd, kHb,
+      SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(scr), SFFT_ZIP_SCRATCH, sd, zs.hb,
       nullptr);
   CK(cudaGetLastError());
   const RoundSmem rs = round_smem(2);

@@ -40,7 +40,7 @@ __device__ SvdSmem carve_svd_smem(void* raw, int p, int hb, int vcap = 0) {
   s.W = reinterpret_cast<cd*>(c);
   c += sizeof(cd) * (size_t)(p + hb) * p;
   s.V = reinterpret_cast<cd*>(c);
-  c += sizeof(cd) * (size_t)(vcap > p * p ? vcap : p * p);
+  c += sizeof(cd) * (size_t)(vcap > 0 ? vcap : p * p);
   s.sig = reinterpret_cast<double*>(c);
   c += sizeof(double) * p;
   s.tau = reinterpret_cast<cd*>(c);
@@ -683,8 +683,10 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
                         int core_stride_a, int core_stride_w, int core_stride_b,
                         cd* scratch, long long scratch_stride,
                         int* status, int hb, double* acc) {
+  // shared memory: W for row blocks of the panel ((LA_MAXP + hb) x LA_MAXP),
+  // V for the p x (rank + 1) block of the basis step (see zip_smem on the host)
   extern __shared__ double4 smem_raw[];
-  SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
+  SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb, LA_MAXP * (SFFT_SLOT_RANK_DEV + 1));
   __shared__ int zperm[LA_MAXP];
   __shared__ double zred_d[32];
   __shared__ int zred_i[32];
