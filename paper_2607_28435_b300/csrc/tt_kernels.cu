@@ -270,12 +270,35 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
 //   Phi[(i, l1), (l2, t)] = x( ((I[b-1][i] 2 + l1) 2 + l2) 2^(n-b-1) + J[b+1][t] ).
 // Left-to-right sweeps pick I[b] by maxvol on the left singular vectors of Phi,
 // right-to-left sweeps pick J[b] from its right singular vectors; the singular
-// values set the rank (relative threshold 0.01 tol, cap max_rank). Sweeps stop
-// when the ranks repeat, after at least three. Assembly then runs one left-to-right pass: the fibre
+// values set the rank (relative threshold 0.01 tol, cap max_rank). The
+// dominant subspaces come from a rank-revealing QR of the supercore (its
+// trailing norm bounds the discarded part), which serves maxvol as well as
+// the singular vectors would at a fraction of the cost. Sweeps stop
+// when the ranks repeat, after at least two. Assembly then runs one left-to-right pass: the fibre
 // matrix F_s[(i, l), t] = x((I[s][i] 2 + l) 2^(n-s-1) + J[s+1][t]) is factored
 // F = Q R, maxvol on Q gives I[s+1], and the core is Q Q[piv]^{-1}, which
 // interpolates x on the cross (Oseledets & Tyrtyshnikov 2010; Savostyanov &
 // Oseledets 2011). Rounding afterwards makes the cores right-orthonormal.
+// Dominant subspace of the rows of Z (q x p): rank-revealing QR basis B
+// (p x k, k from the trailing-norm rule at ctol, capped at rmax), copied to V,
+// then maxvol on it; returns k, the chosen rows in piv.
+__device__ int dominant_basis(const cd* Z, int q, int p, SvdSmem& sm, int hb, double ctol, int rmax,
+                              int* piv, int* iw, double* red_d, int* red_i, int* st, double* fl) {
+  __shared__ int perm_[LA_MAXP];
+  const RowBasis rb = rrqr_basis(Z, q, p, p, sm.W, SVD_WCAP(hb), sm.V, ctol, rmax + 1, sm.tau, sm.sig,
+                                 perm_, red_d, red_i);
+  int k = rb.k;
+  if (k > rmax) {
+    *st = SFFT_ERANK_DEV;
+    k = rmax;
+  }
+  for (int idx = threadIdx.x; idx < p * k; idx += blockDim.x) sm.V[idx] = sm.W[idx];
+  __syncthreads();
+  maxvol(sm.V, p, p, k, piv, sm.W, iw, red_d, red_i);
+  *fl += rb.flops;
+  return k;
+}
+
 #define CROSS_R SFFT_SLOT_RANK_DEV
 #define CROSS_R0 8
 
@@ -346,20 +369,11 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
         }
         __syncthreads();
         evals += (double)p * q;
-        TsSvd sv = ts_svd(Z, q, p, p, sm.W, SVD_WCAP(hb), sm.V, sm.sig, sm.tau, sm.flag);
-        double s2 = 0.0;
-        for (int i = 0; i < sv.m; ++i) s2 += sm.sig[i] * sm.sig[i];
-        int k = trunc_rank(sm.sig, sv.m, ctol * sqrt(s2));
-        if (k > rmax) {
-          st = SFFT_ERANK_DEV;
-          k = rmax;
-        }
-        maxvol(sm.V, p, p, k, piv, sm.W, iw, red_d, red_i);
+        int k = dominant_basis(Z, q, p, sm, hb, ctol, rmax, piv, iw, red_d, red_i, &st, &fl);
         for (int c = threadIdx.x; c < k; c += blockDim.x)
           Iset[b * CROSS_R + c] = (Iset[(b - 1) * CROSS_R + (piv[c] >> 1)] << 1) | (piv[c] & 1);
         if (threadIdx.x == 0) rk[b] = k;
         __syncthreads();
-        fl += sv.flops;
       }
       // ---- right to left: choose J[b]
       for (int b = n - 1; b >= 1; --b) {
@@ -374,22 +388,13 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
         }
         __syncthreads();
         evals += (double)p * q;
-        TsSvd sv = ts_svd(Z, q, p, p, sm.W, SVD_WCAP(hb), sm.V, sm.sig, sm.tau, sm.flag);
-        double s2 = 0.0;
-        for (int i = 0; i < sv.m; ++i) s2 += sm.sig[i] * sm.sig[i];
-        int k = trunc_rank(sm.sig, sv.m, ctol * sqrt(s2));
-        if (k > rmax) {
-          st = SFFT_ERANK_DEV;
-          k = rmax;
-        }
-        maxvol(sm.V, p, p, k, piv, sm.W, iw, red_d, red_i);
+        int k = dominant_basis(Z, q, p, sm, hb, ctol, rmax, piv, iw, red_d, red_i, &st, &fl);
         for (int c = threadIdx.x; c < k; c += blockDim.x) {
           const int l2 = piv[c] / rr, t = piv[c] - l2 * rr;
           Jset[b * CROSS_R + c] = ((long long)l2 << sh) | Jset[(b + 1) * CROSS_R + t];
         }
         if (threadIdx.x == 0) rk[b] = k;
         __syncthreads();
-        fl += sv.flops;
       }
       // converged when the ranks repeat
       int same = 1;
@@ -397,7 +402,7 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
       __syncthreads();
       for (int b = threadIdx.x; b <= n; b += blockDim.x) rprev[b] = rk[b];
       __syncthreads();
-      if (same && sw >= 2) break;
+      if (same && sw >= 1) break;
     }
     // ---- assembly: interpolatory cores, left to right
     if (threadIdx.x == 0) Iset[0] = 0;
