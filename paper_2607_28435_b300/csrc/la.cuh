@@ -24,6 +24,122 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// Cost model behind the Householder and Jacobi routines below. FP64
+// throughput on this part is set by warp instructions, not lanes: an SM
+// retires about one FP64 warp instruction per 19 cycles (one per ~64 cycles
+// on each of its four sub-partitions) whether 1 or 32 lanes are active, and a
+// warp shuffle-add reduction costs one FP64 instruction per step. So every
+// FP64 instruction should carry as many useful lanes as possible, with as few
+// reduction steps as possible. A reflector is applied to a set of columns by
+// groups of S lanes per column (S a power of two dividing 32); the rows below
+// the pivot are strided over the S lanes and each column's dot product needs
+// only log2(S) shuffle steps. S minimises the FP64 instruction count
+//   ceil(ncols S / 32) * (8 ceil(rows / S) + 2 log2 S + 6).
+__device__ __forceinline__ int hh_group_log2(int ncols, int rows) {
+  int best = 0;
+  long long best_cost = 0x7fffffffffffffffLL;
+  for (int lg = 0; lg <= 5; ++lg) {
+    const int S = 1 << lg;
+    const long long w = ((long long)ncols * S + 31) >> 5;
+    const long long cost = w * (8 * ((rows + S - 1) / S) + 2 * lg + 6);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = lg;
+    }
+  }
+  return best;
+}
+
+// c_j <- c_j - t v (v^H c_j) for the columns j in [j0, j1) of A (leading dim
+// lda), with v_k = 1 implicit and v_i = v[i] for k < i < h. t = conj(tau)
+// applies H^H (QR), t = tau applies H (building Q). post(j, c_j[k]) is called
+// by one lane per column with the updated row-k entry. Every thread of the
+// block must call this; each lane touches only its own rows, so the caller
+// needs a barrier before and after.
+struct HhNoPost {
+  __device__ void operator()(int, cd) const {}
+};
+template <class Post>
+static __device__ void hh_apply(const cd* v, int k, int h, cd t, cd* A, int lda, int j0, int j1,
+                                Post post) {
+  const int ncols = j1 - j0;
+  if (ncols <= 0) return;
+  const int lg = hh_group_log2(ncols, h - k - 1);
+  const int S = 1 << lg;
+  const int lane = lane_id();
+  const int sl = lane & (S - 1);
+  const int gpw = 32 >> lg;            // groups per warp
+  const int gpb = n_warps() * gpw;     // groups per block
+  // the bound is uniform over a warp, so every lane reaches the shuffles
+  for (int g0 = warp_id() * gpw; g0 < ncols; g0 += gpb) {
+    const int g = g0 + (lane >> lg);
+    const bool act = g < ncols;
+    cd* c = A + (size_t)(j0 + (act ? g : 0)) * lda;
+    cd dot = (act && sl == 0) ? c[k] : mkc(0.0, 0.0);
+    if (act)
+      for (int i = k + 1 + sl; i < h; i += S) dot = cfmac(v[i], c[i], dot);
+    for (int o = S >> 1; o > 0; o >>= 1) {
+      dot.x += __shfl_xor_sync(0xffffffffu, dot.x, o);
+      dot.y += __shfl_xor_sync(0xffffffffu, dot.y, o);
+    }
+    if (act) {
+      const cd f = cmul(t, dot);
+      if (sl == 0) {
+        const cd ck = csub(c[k], f);
+        c[k] = ck;
+        post(j0 + g, ck);
+      }
+      const cd nf = cneg(f);
+      for (int i = k + 1 + sl; i < h; i += S) c[i] = cfma(v[i], nf, c[i]);
+    }
+  }
+}
+
+// Householder reflector of col[k..h) (LAPACK zlarfg convention), computed by
+// one warp: H^H (a0; x) = (beta; 0) with beta real, H = I - tau v v^H,
+// v = (1; x / (a0 - beta)). On return col[k] = beta, col[k+1..h) = v, and the
+// returned tau is valid in every lane. The sum of squares is taken unscaled;
+// only when it would leave the safe range (entries below ~1e-140 or above
+// ~1e140) is the column rescaled by its largest modulus first.
+static __device__ cd hh_reflector_warp(cd* col, int k, int h) {
+  const int lane = lane_id();
+  // the pivot is read by lane 0 only and broadcast, so lane 0 may overwrite
+  // it below without racing the other lanes
+  cd a0 = (lane == 0) ? col[k] : mkc(0.0, 0.0);
+  a0.x = __shfl_sync(0xffffffffu, a0.x, 0);
+  a0.y = __shfl_sync(0xffffffffu, a0.y, 0);
+  double ss = 0.0;
+  for (int i = k + 1 + lane; i < h; i += 32) ss = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, ss));
+  ss = warp_sum(ss);
+  if (ss == 0.0 && a0.y == 0.0) return mkc(0.0, 0.0);  // H = I
+  const double tot = cabs2(a0) + ss;
+  double beta;
+  cd scal;
+  if (tot > 1e-280 && tot < 1e280) {
+    beta = -copysign(sqrt(tot), a0.x);
+    const cd d = mkc(a0.x - beta, a0.y);  // |d| >= |beta|: no cancellation
+    const double rd = 1.0 / cabs2(d);
+    scal = mkc(d.x * rd, -d.y * rd);
+  } else {
+    double amax = fmax(fabs(a0.x), fabs(a0.y));
+    for (int i = k + 1 + lane; i < h; i += 32) amax = fmax(amax, fmax(fabs(col[i].x), fabs(col[i].y)));
+    amax = warp_max(amax);
+    const double inv = (amax > 1e-290) ? 1.0 / amax : 0.0;
+    double s = 0.0;
+    for (int i = k + 1 + lane; i < h; i += 32) s += cabs2(cscale(col[i], inv));
+    s = warp_sum(s);
+    if (inv == 0.0 || (s == 0.0 && a0.y == 0.0)) return mkc(0.0, 0.0);
+    const cd a0s = cscale(a0, inv);
+    beta = -copysign(amax * sqrt(cabs2(a0s) + s), a0.x);
+    scal = cdiv(mkc(1.0, 0.0), mkc(a0.x - beta, a0.y));
+  }
+  const double rb = 1.0 / beta;
+  const cd tau = mkc((beta - a0.x) * rb, -a0.y * rb);
+  for (int i = k + 1 + lane; i < h; i += 32) col[i] = cmul(col[i], scal);
+  if (lane == 0) col[k] = mkc(beta, 0.0);
+  return tau;
+}
+
 // Householder QR in place. W: h x p, column-major (leading dim ld). On return
 // the upper triangle of the leading min(h,p) rows holds R (W = Q R); the
 // strictly lower part holds the reflectors v (v_0 = 1 implicit) and must not
@@ -31,60 +147,25 @@ __device__ __forceinline__ double warp_max(double v) {
 // H_k^H (a0; x) = (beta; 0), beta real (LAPACK zlarfg); Q = H_0 H_1 ... .
 // taus[k] (smem, min(h,p) entries) receives tau_k.
 static __device__ void qr_inplace(cd* W, int ld, int h, int p, cd* taus) {
-  const int lane = lane_id(), warp = warp_id(), nw = n_warps();
   const int kmax = min(h, p);
   for (int k = 0; k < kmax; ++k) {
     cd* col = W + (size_t)k * ld;
-    if (warp == 0) {
-      // the pivot is read by lane 0 only and broadcast, so lane 0 may
-      // overwrite it below without racing the other lanes
-      cd a0 = (lane == 0) ? col[k] : mkc(0.0, 0.0);
-      a0.x = __shfl_sync(0xffffffffu, a0.x, 0);
-      a0.y = __shfl_sync(0xffffffffu, a0.y, 0);
-      // norms are taken on the column scaled by its largest modulus, so that
-      // squares of tiny entries neither underflow nor turn beta into zero
-      double amax = fmax(fabs(a0.x), fabs(a0.y));
-      for (int i = k + 1 + lane; i < h; i += 32) amax = fmax(amax, fmax(fabs(col[i].x), fabs(col[i].y)));
-      amax = warp_max(amax);
-      const double inv = (amax > 1e-290) ? 1.0 / amax : 0.0;
-      double s = 0.0;
-      for (int i = k + 1 + lane; i < h; i += 32) s += cabs2(cscale(col[i], inv));
-      s = warp_sum(s);
-      cd tau = mkc(0.0, 0.0);
-      if (inv != 0.0 && !(s == 0.0 && a0.y == 0.0)) {
-        const cd a0s = cscale(a0, inv);
-        const double beta = -copysign(amax * sqrt(cabs2(a0s) + s), a0.x);
-        tau = mkc((beta - a0.x) / beta, -a0.y / beta);
-        const cd scal = cdiv(mkc(1.0, 0.0), mkc(a0.x - beta, a0.y));
-        for (int i = k + 1 + lane; i < h; i += 32) col[i] = cmul(col[i], scal);
-        if (lane == 0) col[k] = mkc(beta, 0.0);
-      }
-      if (lane == 0) taus[k] = tau;
+    if (warp_id() == 0) {
+      const cd tau = hh_reflector_warp(col, k, h);
+      if (lane_id() == 0) taus[k] = tau;
     }
     __syncthreads();
     const cd tau = taus[k];
-    if (tau.x != 0.0 || tau.y != 0.0) {
-      const cd ctau = cconj(tau);
-      for (int j = k + 1 + warp; j < p; j += nw) {
-        cd* cj = W + (size_t)j * ld;
-        cd dot = (lane == 0) ? cj[k] : mkc(0.0, 0.0);
-        for (int i = k + 1 + lane; i < h; i += 32) dot = cfmac(col[i], cj[i], dot);
-        dot = warp_csum(dot);
-        const cd f = cmul(ctau, dot);
-        if (lane == 0) cj[k] = csub(cj[k], f);
-        const cd nf = cneg(f);
-        for (int i = k + 1 + lane; i < h; i += 32) cj[i] = cfma(col[i], nf, cj[i]);
-      }
-    }
+    if (tau.x != 0.0 || tau.y != 0.0) hh_apply(col, k, h, cconj(tau), W, ld, k + 1, p, HhNoPost());
     __syncthreads();
   }
 }
 
 // Explicit Q (h x kq, column-major, leading dim ldq; any address space) of a
 // factorisation left by qr_inplace: Q = H_0 ... H_{kq-1} [I; 0], built by
-// applying the reflectors in reverse order to the identity columns.
+// applying the reflectors in reverse order to the identity columns (columns
+// j < k are untouched by H_k).
 static __device__ void form_q(const cd* W, int ld, int h, int kq, const cd* taus, cd* Q, int ldq) {
-  const int lane = lane_id(), warp = warp_id(), nw = n_warps();
   for (int idx = threadIdx.x; idx < h * kq; idx += blockDim.x) {
     const int j = idx / h, i = idx - j * h;
     Q[(size_t)j * ldq + i] = mkc(i == j ? 1.0 : 0.0, 0.0);
@@ -92,19 +173,7 @@ static __device__ void form_q(const cd* W, int ld, int h, int kq, const cd* taus
   __syncthreads();
   for (int k = kq - 1; k >= 0; --k) {
     const cd tau = taus[k];
-    if (tau.x != 0.0 || tau.y != 0.0) {
-      const cd* v = W + (size_t)k * ld;
-      for (int j = k + warp; j < kq; j += nw) {
-        cd* qj = Q + (size_t)j * ldq;
-        cd dot = (lane == 0) ? qj[k] : mkc(0.0, 0.0);
-        for (int i = k + 1 + lane; i < h; i += 32) dot = cfmac(v[i], qj[i], dot);
-        dot = warp_csum(dot);
-        const cd f = cmul(tau, dot);
-        if (lane == 0) qj[k] = csub(qj[k], f);
-        const cd nf = cneg(f);
-        for (int i = k + 1 + lane; i < h; i += 32) qj[i] = cfma(v[i], nf, qj[i]);
-      }
-    }
+    if (tau.x != 0.0 || tau.y != 0.0) hh_apply(W + (size_t)k * ld, k, h, tau, Q, ldq, k, kq, HhNoPost());
     __syncthreads();
   }
 }
@@ -112,28 +181,57 @@ static __device__ void form_q(const cd* W, int ld, int h, int kq, const cd* taus
 // One-sided Jacobi (Hestenes): rotates the m columns of L (p rows, column
 // major, leading dim ld) until every pair is orthogonal to working precision,
 // |l_a^H l_b| <= tol * ||l_a|| ||l_b||. Columns are visited in round-robin
-// tournament order. A pair is handled by a group of 8 lanes (four pairs per
-// warp): the columns are short (p <= 64), so narrower groups spend fewer lanes
-// on the per-pair rotation arithmetic, which every lane of a group repeats.
-// Each warp runs the same number of group iterations, so the group reductions
-// can use full-warp shuffles. Returns the number of sweeps used, or -1 if
-// max_sweeps did not reach convergence.
+// tournament order, the m/2 pairs of a round in parallel. A pair is handled
+// by a group of G lanes (G a power of two): rows are strided over the group
+// and its four sums reduced in log2(G) shuffle steps. G minimises the FP64
+// instruction count of a round (the cost model above hh_group_log2): the
+// rotation parameters cost about as much as 2 rows of dot products and
+// updates, and are shared by all pairs of a warp.
+// Rotation of a pair (a, b) with alpha = |a|^2, beta = |b|^2, g = a^H b,
+// D = beta - alpha: t = sign(D) 2|g| / (|D| + sqrt(D^2 + 4|g|^2)) is the
+// tangent of the annihilating angle, c = 1/sqrt(1 + t^2), and with
+// sp = c t conj(g)/|g| the update is a <- c a - sp b, b <- conj(sp) a + c b.
+// (Rutishauser's rotation with the phase of g moved onto the new b; b is
+// then a singular direction up to a unit factor, which no caller depends on.)
+// Returns the number of sweeps used, or -1 if max_sweeps did not reach
+// convergence.
+__device__ __forceinline__ int jacobi_group_log2(int npair, int p) {
+  int best = 0;
+  long long best_cost = 0x7fffffffffffffffLL;
+  for (int lg = 0; lg <= 5; ++lg) {
+    const int G = 1 << lg;
+    const long long w = ((long long)npair * G + 31) >> 5;
+    const long long cost = w * (20 * ((p + G - 1) / G) + 4 * lg + 40);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = lg;
+    }
+  }
+  return best;
+}
+
 static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int* sh_flag) {
-  const int lane = lane_id(), warp = warp_id(), nw = n_warps();
-  const int sub = lane & 7, grp = lane >> 3;  // 4 groups of 8 lanes per warp
+  const int lane = lane_id(), warp = warp_id();
   if (m < 2) return 0;
   const int mp = m + (m & 1);
   const int npair = mp / 2;
+  const int lg = jacobi_group_log2(npair, p);
+  const int G = 1 << lg;
+  const int sub = lane & (G - 1);
+  const int ppw = 32 >> lg;           // pairs per warp
+  const int ppb = n_warps() * ppw;    // pairs per block pass
   // a pair counts as orthogonal once |a^H b| <= tol |a| |b|, the rounding
   // level of a p-term complex dot product; after max_sweeps the result is
   // accepted if no pair is worse than 1e-10 (reported as not converged otherwise)
   const double tol = 1.0e-15 * (double)max(p, 8);
+  const double tol2 = tol * tol;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) *sh_flag = 0;
     __syncthreads();
     for (int t = 0; t < mp - 1; ++t) {
-      for (int e0 = 4 * warp; e0 < npair; e0 += 4 * nw) {
-        const int e = e0 + grp;
+      // the bound is uniform over a warp, so every lane reaches the shuffles
+      for (int e0 = warp * ppw; e0 < npair; e0 += ppb) {
+        const int e = e0 + (lane >> lg);
         int a = 0, b = 0;
         bool live = e < npair;
         if (live) {
@@ -150,39 +248,45 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
         cd* cb = L + (size_t)b * ld;
         double al = 0.0, be = 0.0, gx = 0.0, gy = 0.0;
         if (live)
-          for (int i = sub; i < p; i += 8) {
+          for (int i = sub; i < p; i += G) {
             const cd x = ca[i], y = cb[i];
             al = fma(x.x, x.x, fma(x.y, x.y, al));
             be = fma(y.x, y.x, fma(y.y, y.y, be));
             gx = fma(x.x, y.x, fma(x.y, y.y, gx));
             gy = fma(x.x, y.y, fma(-x.y, y.x, gy));
           }
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
+        for (int o = G >> 1; o > 0; o >>= 1) {
           al += __shfl_xor_sync(0xffffffffu, al, o);
           be += __shfl_xor_sync(0xffffffffu, be, o);
           gx += __shfl_xor_sync(0xffffffffu, gx, o);
           gy += __shfl_xor_sync(0xffffffffu, gy, o);
         }
         if (!live) continue;
-        const double ga = sqrt(fma(gx, gx, gy * gy));
-        const double nab = sqrt(al) * sqrt(be);
-        if (ga > tol * nab && ga > 1e-300) {
-          const double zeta = (be - al) / (2.0 * ga);
-          // hypot keeps zeta^2 from overflowing when one column is tiny: then
-          // t ~ 1/(2 zeta), the small-angle rotation
-          const double tt = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
-          const double c = rsqrt(fma(tt, tt, 1.0));
-          const double s = c * tt;
-          const double ig = 1.0 / ga;
-          const cd ph = mkc(gx * ig, -gy * ig);  // exp(-i arg g)
-          for (int i = sub; i < p; i += 8) {
-            const cd x = ca[i];
-            const cd y = cmul(cb[i], ph);
-            ca[i] = mkc(fma(c, x.x, -s * y.x), fma(c, x.y, -s * y.y));
-            cb[i] = mkc(fma(s, x.x, c * y.x), fma(s, x.y, c * y.y));
+        const double g2 = fma(gx, gx, gy * gy);
+        const double ab = al * be;
+        if (g2 > tol2 * ab && g2 > 1e-290) {
+          // t, c and sp are invariant under a common scaling of al, be, g;
+          // rescale only when the squares below could overflow
+          double D = be - al, G2 = g2, sx = gx, sy = gy;
+          const double big = fmax(al, be);
+          if (big > 1e140) {
+            const double inv = 1.0 / big;
+            D *= inv;
+            sx *= inv;
+            sy *= inv;
+            G2 = fma(sx, sx, sy * sy);
           }
-          if (sub == 0) atomicOr(sh_flag, (ga > 1e-10 * nab) ? 3 : 1);
+          const double r = sqrt(fma(D, D, 4.0 * G2));
+          const double w = copysign(2.0, D) / (fabs(D) + r);  // t = w |g|
+          const double c = rsqrt(fma(w * w, G2, 1.0));
+          const double cw = c * w;
+          const double spx = cw * sx, spy = -cw * sy;           // sp = c w conj(g)
+          for (int i = sub; i < p; i += G) {
+            const cd x = ca[i], y = cb[i];
+            ca[i] = mkc(fma(c, x.x, -fma(spx, y.x, -spy * y.y)), fma(c, x.y, -fma(spx, y.y, spy * y.x)));
+            cb[i] = mkc(fma(c, y.x, fma(spx, x.x, spy * x.y)), fma(c, y.y, fma(spx, x.y, -spy * x.x)));
+          }
+          if (sub == 0) atomicOr(sh_flag, (g2 > 1e-20 * ab) ? 3 : 1);
         }
       }
       __syncthreads();
@@ -464,9 +568,13 @@ static __device__ void maxvol(const cd* A, int lda, int N, int r, int* piv, cd* 
 // pivoting (the column of largest remaining norm first), so that the trailing
 // block R2[k:, k:] has Frobenius norm equal to the error of keeping k rows.
 // k is the smallest rank with that norm <= delta_rel * ||Z||_F (k >= 1,
-// k <= kmax). The kept rows span (R2[:k] P^T); B (p x k, column-major, leading
-// dim p, in W on return) is an orthonormal basis of their conjugate span, so
-// Z ~= Z B B^H with error at most the trailing norm.
+// k <= kmax); the pivoted factorisation stops there. The kept rows span
+// (R2[:k] P^T); B (p x k, column-major, leading dim p, in W on return) is an
+// orthonormal basis of their conjugate span, so Z ~= Z B B^H with error at
+// most the trailing norm.
+// Column norms are downdated after each step (|R2[k, j]|^2 subtracted) and
+// recomputed from the rows once a norm has fallen below 1e-8 of its value at
+// the last recomputation, the safeguard of LAPACK's xGEQP3.
 // Smem: W (wcap >= (p + 1) p), V (p x p), taus and cn (p entries each), perm (p ints).
 struct RowBasis {
   int k;
@@ -476,111 +584,131 @@ struct RowBasis {
 static __device__ RowBasis rrqr_basis(const cd* Z, long long q, int p, int ldz, cd* W, int wcap, cd* V,
                                       double delta_rel, int kmax, cd* taus, double* cn, int* perm,
                                       double* red_d, int* red_i) {
-  const int lane = lane_id(), warp = warp_id(), nw = n_warps();
+  __shared__ double ref[LA_MAXP];
+  __shared__ int flag[LA_MAXP];
+  __shared__ int ctl;  // 1 once the rank is found
+  (void)red_d;
+  (void)red_i;
+  const int lane = lane_id(), warp = warp_id();
   int ldw;
   const int m = stream_qr(Z, q, p, ldz, W, wcap, taus, &ldw);
   RowBasis out;
+  out.k = 1;
   out.flops = 0.0;
-  for (int j = threadIdx.x; j < p; j += blockDim.x) perm[j] = j;
-  __syncthreads();
-  const int kmax_q = min(m, p);
-  double total = 0.0;
-  // pivoted Householder QR of R (m x p) in place
-  for (int k = 0; k < kmax_q; ++k) {
-    for (int j = k + warp; j < p; j += nw) {
-      const cd* cj = W + (size_t)j * ldw;
-      double amax = 0.0;
-      for (int i = k + lane; i < m; i += 32) amax = fmax(amax, fmax(fabs(cj[i].x), fabs(cj[i].y)));
-      amax = warp_max(amax);
-      const double inv = amax > 1e-290 ? 1.0 / amax : 0.0;
-      double ss = 0.0;
-      for (int i = k + lane; i < m; i += 32) ss += cabs2(cscale(cj[i], inv));
-      ss = warp_sum(ss);
-      if (lane == 0) cn[j] = ss * amax * amax;
-    }
-    __syncthreads();
-    if (k == 0) {
-      for (int j = 0; j < p; ++j) total += cn[j];
-    }
-    const int jm = k + cta_argmax(p - k, [&](int t) { return cn[k + t]; }, red_d, red_i);
-    if (jm != k) {
-      for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const cd t = W[(size_t)k * ldw + i];
-        W[(size_t)k * ldw + i] = W[(size_t)jm * ldw + i];
-        W[(size_t)jm * ldw + i] = t;
-      }
-      if (threadIdx.x == 0) {
-        const int t = perm[k];
-        perm[k] = perm[jm];
-        perm[jm] = t;
-      }
-    }
-    __syncthreads();
-    // one Householder step on column k (rows k..m-1), applied to columns > k
-    cd* col = W + (size_t)k * ldw;
-    if (warp == 0) {
-      cd a0 = (lane == 0) ? col[k] : mkc(0.0, 0.0);
-      a0.x = __shfl_sync(0xffffffffu, a0.x, 0);
-      a0.y = __shfl_sync(0xffffffffu, a0.y, 0);
-      double amax = fmax(fabs(a0.x), fabs(a0.y));
-      for (int i = k + 1 + lane; i < m; i += 32) amax = fmax(amax, fmax(fabs(col[i].x), fabs(col[i].y)));
-      amax = warp_max(amax);
-      const double inv = (amax > 1e-290) ? 1.0 / amax : 0.0;
-      double ss = 0.0;
-      for (int i = k + 1 + lane; i < m; i += 32) ss += cabs2(cscale(col[i], inv));
-      ss = warp_sum(ss);
-      cd tau = mkc(0.0, 0.0);
-      if (inv != 0.0 && !(ss == 0.0 && a0.y == 0.0)) {
-        const cd a0s = cscale(a0, inv);
-        const double beta = -copysign(amax * sqrt(cabs2(a0s) + ss), a0.x);
-        tau = mkc((beta - a0.x) / beta, -a0.y / beta);
-        const cd scal = cdiv(mkc(1.0, 0.0), mkc(a0.x - beta, a0.y));
-        for (int i = k + 1 + lane; i < m; i += 32) col[i] = cmul(col[i], scal);
-        if (lane == 0) col[k] = mkc(beta, 0.0);
-      }
-      if (lane == 0) taus[k] = tau;
-    }
-    __syncthreads();
-    const cd tau = taus[k];
-    if (tau.x != 0.0 || tau.y != 0.0) {
-      const cd ctau = cconj(tau);
-      for (int j = k + 1 + warp; j < p; j += nw) {
-        cd* cj = W + (size_t)j * ldw;
-        cd dot = (lane == 0) ? cj[k] : mkc(0.0, 0.0);
-        for (int i = k + 1 + lane; i < m; i += 32) dot = cfmac(col[i], cj[i], dot);
-        dot = warp_csum(dot);
-        const cd f = cmul(ctau, dot);
-        const cd nf = cneg(f);
-        if (lane == 0) cj[k] = csub(cj[k], f);
-        for (int i = k + 1 + lane; i < m; i += 32) cj[i] = cfma(col[i], nf, cj[i]);
-      }
-    }
-    __syncthreads();
-    out.flops += 20.0 * (m - k) * (p - k);
-  }
-  // rank from the trailing row norms of R2 (upper trapezoidal, row i from column i)
-  for (int i = warp; i < kmax_q; i += nw) {
-    double ss = 0.0;
-    for (int j = i + lane; j < p; j += 32) {
-      const cd v = W[(size_t)j * ldw + i];
-      ss += cabs2(v);
-    }
-    ss = warp_sum(ss);
-    if (lane == 0) cn[i] = ss;
-  }
-  __syncthreads();
-  const double delta = delta_rel * sqrt(total);
-  int k = kmax_q;
   {
-    double tail = 0.0;
-    for (int i = kmax_q - 1; i >= 0; --i) {
-      tail += cn[i];
-      if (sqrt(tail) <= delta) k = i; else break;
+    long long rows = q, carried = 0;
+    const int hb = wcap / p - p;
+    while (rows > 0) {
+      const long long b = rows < hb ? rows : hb;
+      out.flops += flops_qr((double)(carried + b), (double)p);
+      carried = carried + b < p ? carried + b : p;
+      rows -= b;
     }
   }
-  k = max(k, 1);
-  k = min(k, kmax);
-  out.k = k;
+  // exact column norms of R (m x p, upper trapezoidal)
+  for (int j = warp; j < p; j += n_warps()) {
+    const cd* cj = W + (size_t)j * ldw;
+    double ss = 0.0;
+    for (int i = lane; i < m && i <= j; i += 32) ss = fma(cj[i].x, cj[i].x, fma(cj[i].y, cj[i].y, ss));
+    ss = warp_sum(ss);
+    if (lane == 0) {
+      cn[j] = ss;
+      ref[j] = ss;
+      flag[j] = 0;
+      perm[j] = j;
+    }
+  }
+  __syncthreads();
+  double total = 0.0;
+  for (int j = 0; j < p; ++j) total += cn[j];
+  const double delta2 = delta_rel * delta_rel * total;
+  const int kstop = min(min(m, p), kmax);
+  for (int k = 0;; ++k) {
+    if (warp == 0) {
+      // norms that lost too many digits to downdating: recompute rows k..m-1
+      for (int jj = k; jj < p; ++jj) {
+        if (!flag[jj]) continue;
+        const cd* cj = W + (size_t)jj * ldw;
+        double ss = 0.0;
+        for (int i = k + lane; i < m; i += 32) ss = fma(cj[i].x, cj[i].x, fma(cj[i].y, cj[i].y, ss));
+        ss = warp_sum(ss);
+        __syncwarp();
+        if (lane == 0) {
+          cn[jj] = ss;
+          ref[jj] = ss;
+          flag[jj] = 0;
+        }
+        __syncwarp();
+      }
+      // trailing norm ||R[k:, k:]||^2 and the pivot column
+      double tr = 0.0, best = -1.0;
+      int bi = 0x7fffffff;
+      for (int j = k + lane; j < p; j += 32) {
+        const double v = cn[j];
+        tr += v;
+        if (v > best) {
+          best = v;
+          bi = j;
+        }
+      }
+      tr = warp_sum(tr);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      const bool stop = (k >= 1 && tr <= delta2) || k >= kstop;
+      if (!stop) {
+        if (bi != k) {
+          cd* ck = W + (size_t)k * ldw;
+          cd* cb = W + (size_t)bi * ldw;
+          for (int i = lane; i < m; i += 32) {
+            const cd tmp = ck[i];
+            ck[i] = cb[i];
+            cb[i] = tmp;
+          }
+          if (lane == 0) {
+            const double t1 = cn[k], t2 = ref[k];
+            cn[k] = cn[bi];
+            ref[k] = ref[bi];
+            cn[bi] = t1;
+            ref[bi] = t2;
+            const int t3 = perm[k];
+            perm[k] = perm[bi];
+            perm[bi] = t3;
+          }
+        }
+        __syncwarp();
+        const cd tau = hh_reflector_warp(W + (size_t)k * ldw, k, m);
+        if (lane == 0) taus[k] = tau;
+      }
+      if (lane == 0) ctl = stop ? 1 : 0;
+    }
+    __syncthreads();
+    if (ctl) {
+      out.k = max(k, 1);
+      break;
+    }
+    const cd tau = taus[k];
+    auto downdate = [&](int j, cd rkj) {
+      const double c = cn[j] - cabs2(rkj);
+      cn[j] = c;
+      if (c <= 1e-8 * ref[j]) flag[j] = 1;
+    };
+    if (tau.x != 0.0 || tau.y != 0.0) {
+      hh_apply(W + (size_t)k * ldw, k, m, cconj(tau), W, ldw, k + 1, p, downdate);
+    } else {
+      // H = I: row k is already final, its entries still leave the norms
+      for (int j = k + 1 + threadIdx.x; j < p; j += blockDim.x) downdate(j, W[(size_t)j * ldw + k]);
+    }
+    __syncthreads();
+    out.flops += flops_qr((double)(m - k), (double)(p - k)) - flops_qr((double)(m - k - 1), (double)(p - k - 1));
+  }
+  const int k = out.k;
   // M = (R2[:k] P^T)^H (p x k) into V: M[perm[j], c] = conj(R2[c, j])
   for (int idx = threadIdx.x; idx < p * k; idx += blockDim.x) {
     const int c = idx / p, j = idx - c * p;
