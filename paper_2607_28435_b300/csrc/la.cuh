@@ -310,22 +310,32 @@ struct TsSvd {
   double flops;   // algorithmic FP64 flops of this factorisation
 };
 
-// Algorithmic FP64 flop counts (complex multiply-add = 8 real flops).
-__host__ __device__ inline double flops_qr(double h, double p) {
-  double f = 0.0;
-  const double k = h < p ? h : p;
-  for (double i = 0; i < k; i += 1.0) f += 16.0 * (h - i) * (p - i - 1.0) + 10.0 * (h - i);
-  return f;
+// Algorithmic FP64 flop counts (complex multiply-add = 8 real flops), in
+// closed form and integer arithmetic: every thread evaluates them, and on
+// this part FP64 instructions are the scarce resource, so the bookkeeping
+// must not spend any.
+// Householder QR of h x p: sum_{i<k} 16 (h-i)(p-1-i) + 10 (h-i), k = min(h, p).
+__host__ __device__ inline double flops_qr(long long h, long long p) {
+  const long long k = h < p ? h : p;
+  if (k <= 0) return 0.0;
+  const long long s1 = k * h * (p - 1) - (h + p - 1) * (k * (k - 1) / 2) + (k - 1) * k * (2 * k - 1) / 6;
+  const long long s2 = k * h - k * (k - 1) / 2;
+  return (double)(16 * s1 + 10 * s2);
 }
-__host__ __device__ inline double flops_formq(double h, double kq) {
-  double f = 0.0;
-  for (double i = 0; i < kq; i += 1.0) f += 16.0 * (h - i) * (kq - i);
-  return f;
+// One Householder step (column i of an h x p factorisation): the i-th term above.
+__host__ __device__ inline double flops_qr_step(long long h, long long p, long long i) {
+  return (double)(16 * (h - i) * (p - 1 - i) + 10 * (h - i));
 }
-__host__ __device__ inline double flops_hestenes(double p, double m, double sweeps) {
-  return sweeps * 0.5 * m * (m - 1.0) * 26.0 * p;
+// Explicit Q: sum_{i<kq} 16 (h-i)(kq-i).
+__host__ __device__ inline double flops_formq(long long h, long long kq) {
+  if (kq <= 0) return 0.0;
+  const long long s = kq * h * kq - (h + kq) * (kq * (kq - 1) / 2) + (kq - 1) * kq * (2 * kq - 1) / 6;
+  return (double)(16 * s);
 }
-__host__ __device__ inline double flops_gemm(double m, double n, double k) { return 8.0 * m * n * k; }
+__host__ __device__ inline double flops_hestenes(long long p, long long m, long long sweeps) {
+  return (double)(sweeps * m * (m - 1) / 2 * 26 * p);
+}
+__host__ __device__ inline double flops_gemm(long long m, long long n, long long k) { return (double)(8 * m * n * k); }
 
 // Right singular vectors of a tall-skinny Z (q x p, row-major, leading dim
 // ldz, read only; any address space). Streaming Householder QR over row blocks
@@ -389,11 +399,11 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
     long long rows = q, carried = 0;
     while (rows > 0) {
       const long long b = rows < hb ? rows : hb;
-      f += flops_qr((double)(carried + b), (double)p);
+      f += flops_qr(carried + b, p);
       carried = carried + b < p ? carried + b : p;
       rows -= b;
     }
-    out.flops = f + flops_hestenes(p, m, out.sweeps < 0 ? 60 : out.sweeps) + 4.0 * p * m;
+    out.flops = f + flops_hestenes(p, m, out.sweeps < 0 ? 60 : out.sweeps) + (double)(4 * p * m);
   }
   // column norms
   double* nrm = reinterpret_cast<double*>(W);  // W is free now
@@ -427,10 +437,11 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
 // evaluated redundantly by every thread.
 __device__ __forceinline__ int trunc_rank(const double* sig, int m, double delta) {
   double tail = 0.0;
+  const double d2 = delta * delta;
   int k = m;
   for (int i = m - 1; i >= 0; --i) {
-    tail += sig[i] * sig[i];
-    if (sqrt(tail) <= delta) k = i; else break;
+    tail = fma(sig[i], sig[i], tail);
+    if (tail <= d2) k = i; else break;
   }
   return max(k, 1);
 }
@@ -600,7 +611,7 @@ static __device__ RowBasis rrqr_basis(const cd* Z, long long q, int p, int ldz, 
     const int hb = wcap / p - p;
     while (rows > 0) {
       const long long b = rows < hb ? rows : hb;
-      out.flops += flops_qr((double)(carried + b), (double)p);
+      out.flops += flops_qr(carried + b, p);
       carried = carried + b < p ? carried + b : p;
       rows -= b;
     }
@@ -706,7 +717,7 @@ static __device__ RowBasis rrqr_basis(const cd* Z, long long q, int p, int ldz, 
       for (int j = k + 1 + threadIdx.x; j < p; j += blockDim.x) downdate(j, W[(size_t)j * ldw + k]);
     }
     __syncthreads();
-    out.flops += flops_qr((double)(m - k), (double)(p - k)) - flops_qr((double)(m - k - 1), (double)(p - k - 1));
+    out.flops += flops_qr_step(m, p, k);
   }
   const int k = out.k;
   // M = (R2[:k] P^T)^H (p x k) into V: M[perm[j], c] = conj(R2[c, j])

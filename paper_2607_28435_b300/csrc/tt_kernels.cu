@@ -231,7 +231,7 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
       }
       gemm_zv(Z, q, p, sm.V, k, O);
       __syncthreads();
-      fl += sv.flops + flops_gemm((double)q, p, k);
+      fl += sv.flops + flops_gemm(q, p, k);
       cd* tmp = Z;
       Z = O;
       O = tmp;
@@ -752,7 +752,7 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
         Z[idx] = acc;
       }
       __syncthreads();
-      fl += flops_gemm(nd, rA0, 1) + flops_gemm((double)q * p, 2.0 * s0, 1);
+      fl += flops_gemm(nd, rA0, 1) + flops_gemm((long long)q * p, 2 * s0, 1);
       cd* Bs = Bb + (size_t)s * core_stride_b;
       if (s == n - 1) {
         // q == 1: B[c][mu][0] = conj(Z[0, (c, mu)])
