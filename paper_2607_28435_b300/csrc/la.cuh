@@ -574,53 +574,37 @@ static __device__ void maxvol(const cd* A, int lda, int N, int r, int* piv, cd* 
   }
 }
 
-// Truncated row-space basis of a tall Z (q x p) by rank-revealing QR.
-// Z = Q R by the streaming QR; then R P = Q2 R2 by Householder QR with column
-// pivoting (the column of largest remaining norm first), so that the trailing
-// block R2[k:, k:] has Frobenius norm equal to the error of keeping k rows.
-// k is the smallest rank with that norm <= delta_rel * ||Z||_F (k >= 1,
-// k <= kmax); the pivoted factorisation stops there. The kept rows span
-// (R2[:k] P^T); B (p x k, column-major, leading dim p, in W on return) is an
-// orthonormal basis of their conjugate span, so Z ~= Z B B^H with error at
-// most the trailing norm.
-// Column norms are downdated after each step (|R2[k, j]|^2 subtracted) and
+// Truncated Householder QR with column pivoting of A (m x ncol, column-major,
+// leading dim lda, smem): A P = Q R with the column of largest remaining norm
+// first, stopped at the smallest k >= 1 with ||R[k:, k:]||_F <= delta_rel
+// ||A||_F (or at k = min(m, ncol, kmax)). On return rows 0..k-1 of R are final
+// in the upper part of A (pivoted column order), the reflectors of steps
+// 0..k-1 lie below the diagonal with taus[0..k), and perm[i] is the original
+// index of pivoted column i. ||R[k:, k:]||_F is the error of keeping k rows.
+// Column norms are downdated after each step (|R[k, j]|^2 subtracted) and
 // recomputed from the rows once a norm has fallen below 1e-8 of its value at
 // the last recomputation, the safeguard of LAPACK's xGEQP3.
-// Smem: W (wcap >= (p + 1) p), V (p x p), taus and cn (p entries each), perm (p ints).
+// Smem: taus (min(m, ncol) entries), cn and perm (ncol entries, ncol <= LA_MAXQ).
+#define LA_MAXQ 128
 struct RowBasis {
   int k;
   double flops;
 };
 
-static __device__ RowBasis rrqr_basis(const cd* Z, long long q, int p, int ldz, cd* W, int wcap, cd* V,
-                                      double delta_rel, int kmax, cd* taus, double* cn, int* perm,
-                                      double* red_d, int* red_i) {
-  __shared__ double ref[LA_MAXP];
-  __shared__ int flag[LA_MAXP];
+static __device__ RowBasis pivqr_trunc(cd* A, int lda, int m, int ncol, double delta_rel, int kmax, cd* taus,
+                                       double* cn, int* perm) {
+  __shared__ double ref[LA_MAXQ];
+  __shared__ int flag[LA_MAXQ];
   __shared__ int ctl;  // 1 once the rank is found
-  (void)red_d;
-  (void)red_i;
   const int lane = lane_id(), warp = warp_id();
-  int ldw;
-  const int m = stream_qr(Z, q, p, ldz, W, wcap, taus, &ldw);
   RowBasis out;
   out.k = 1;
   out.flops = 0.0;
-  {
-    long long rows = q, carried = 0;
-    const int hb = wcap / p - p;
-    while (rows > 0) {
-      const long long b = rows < hb ? rows : hb;
-      out.flops += flops_qr(carried + b, p);
-      carried = carried + b < p ? carried + b : p;
-      rows -= b;
-    }
-  }
-  // exact column norms of R (m x p, upper trapezoidal)
-  for (int j = warp; j < p; j += n_warps()) {
-    const cd* cj = W + (size_t)j * ldw;
+  // exact column norms
+  for (int j = warp; j < ncol; j += n_warps()) {
+    const cd* cj = A + (size_t)j * lda;
     double ss = 0.0;
-    for (int i = lane; i < m && i <= j; i += 32) ss = fma(cj[i].x, cj[i].x, fma(cj[i].y, cj[i].y, ss));
+    for (int i = lane; i < m; i += 32) ss = fma(cj[i].x, cj[i].x, fma(cj[i].y, cj[i].y, ss));
     ss = warp_sum(ss);
     if (lane == 0) {
       cn[j] = ss;
@@ -631,15 +615,16 @@ static __device__ RowBasis rrqr_basis(const cd* Z, long long q, int p, int ldz, 
   }
   __syncthreads();
   double total = 0.0;
-  for (int j = 0; j < p; ++j) total += cn[j];
+  for (int j = lane; j < ncol; j += 32) total += cn[j];
+  total = warp_sum(total);
   const double delta2 = delta_rel * delta_rel * total;
-  const int kstop = min(min(m, p), kmax);
+  const int kstop = min(min(m, ncol), kmax);
   for (int k = 0;; ++k) {
     if (warp == 0) {
       // norms that lost too many digits to downdating: recompute rows k..m-1
-      for (int jj = k; jj < p; ++jj) {
+      for (int jj = k; jj < ncol; ++jj) {
         if (!flag[jj]) continue;
-        const cd* cj = W + (size_t)jj * ldw;
+        const cd* cj = A + (size_t)jj * lda;
         double ss = 0.0;
         for (int i = k + lane; i < m; i += 32) ss = fma(cj[i].x, cj[i].x, fma(cj[i].y, cj[i].y, ss));
         ss = warp_sum(ss);
@@ -654,7 +639,7 @@ static __device__ RowBasis rrqr_basis(const cd* Z, long long q, int p, int ldz, 
       // trailing norm ||R[k:, k:]||^2 and the pivot column
       double tr = 0.0, best = -1.0;
       int bi = 0x7fffffff;
-      for (int j = k + lane; j < p; j += 32) {
+      for (int j = k + lane; j < ncol; j += 32) {
         const double v = cn[j];
         tr += v;
         if (v > best) {
@@ -675,8 +660,8 @@ static __device__ RowBasis rrqr_basis(const cd* Z, long long q, int p, int ldz, 
       const bool stop = (k >= 1 && tr <= delta2) || k >= kstop;
       if (!stop) {
         if (bi != k) {
-          cd* ck = W + (size_t)k * ldw;
-          cd* cb = W + (size_t)bi * ldw;
+          cd* ck = A + (size_t)k * lda;
+          cd* cb = A + (size_t)bi * lda;
           for (int i = lane; i < m; i += 32) {
             const cd tmp = ck[i];
             ck[i] = cb[i];
@@ -694,7 +679,7 @@ static __device__ RowBasis rrqr_basis(const cd* Z, long long q, int p, int ldz, 
           }
         }
         __syncwarp();
-        const cd tau = hh_reflector_warp(W + (size_t)k * ldw, k, m);
+        const cd tau = hh_reflector_warp(A + (size_t)k * lda, k, m);
         if (lane == 0) taus[k] = tau;
       }
       if (lane == 0) ctl = stop ? 1 : 0;
@@ -711,14 +696,42 @@ static __device__ RowBasis rrqr_basis(const cd* Z, long long q, int p, int ldz, 
       if (c <= 1e-8 * ref[j]) flag[j] = 1;
     };
     if (tau.x != 0.0 || tau.y != 0.0) {
-      hh_apply(W + (size_t)k * ldw, k, m, cconj(tau), W, ldw, k + 1, p, downdate);
+      hh_apply(A + (size_t)k * lda, k, m, cconj(tau), A, lda, k + 1, ncol, downdate);
     } else {
       // H = I: row k is already final, its entries still leave the norms
-      for (int j = k + 1 + threadIdx.x; j < p; j += blockDim.x) downdate(j, W[(size_t)j * ldw + k]);
+      for (int j = k + 1 + threadIdx.x; j < ncol; j += blockDim.x) downdate(j, A[(size_t)j * lda + k]);
     }
     __syncthreads();
-    out.flops += flops_qr_step(m, p, k);
+    out.flops += flops_qr_step(m, ncol, k);
   }
+  return out;
+}
+
+// Truncated row-space basis of a tall Z (q x p) by rank-revealing QR.
+// Z = Q R by the streaming QR; then R P = Q2 R2 by pivqr_trunc, so that the
+// trailing block R2[k:, k:] has Frobenius norm equal to the error of keeping
+// k rows; k is the smallest rank with that norm <= delta_rel * ||Z||_F
+// (k >= 1, k <= kmax). The kept rows span (R2[:k] P^T); B (p x k,
+// column-major, leading dim p, in W on return) is an orthonormal basis of
+// their conjugate span, so Z ~= Z B B^H with error at most the trailing norm.
+// Smem: W (wcap >= (p + 1) p), V (p x p), taus and cn (p entries each), perm (p ints).
+static __device__ RowBasis rrqr_basis(const cd* Z, long long q, int p, int ldz, cd* W, int wcap, cd* V,
+                                      double delta_rel, int kmax, cd* taus, double* cn, int* perm) {
+  int ldw;
+  const int m = stream_qr(Z, q, p, ldz, W, wcap, taus, &ldw);
+  double fl = 0.0;
+  {
+    long long rows = q, carried = 0;
+    const int hb = wcap / p - p;
+    while (rows > 0) {
+      const long long b = rows < hb ? rows : hb;
+      fl += flops_qr(carried + b, p);
+      carried = carried + b < p ? carried + b : p;
+      rows -= b;
+    }
+  }
+  RowBasis out = pivqr_trunc(W, ldw, m, p, delta_rel, kmax, taus, cn, perm);
+  out.flops += fl;
   const int k = out.k;
   // M = (R2[:k] P^T)^H (p x k) into V: M[perm[j], c] = conj(R2[c, j])
   for (int idx = threadIdx.x; idx < p * k; idx += blockDim.x) {
@@ -730,6 +743,20 @@ static __device__ RowBasis rrqr_basis(const cd* Z, long long q, int p, int ldz, 
   qr_inplace(V, p, p, k, taus);
   form_q(V, p, p, min(p, k), taus, W, p);
   out.flops += flops_qr(p, k) + flops_formq(p, min(p, k));
+  return out;
+}
+
+// Dominant column space of T (p x q, column-major with leading dim p, placed
+// in W by the caller; q <= LA_MAXQ): T P = Q R by pivqr_trunc, and
+// B = Q[:, :k] (p x k, column-major, leading dim p) into V. Then
+// ||T - B B^H T||_F = ||R[k:, k:]||_F <= delta_rel ||T||_F, and
+// B^H T = R[:k, :] P^T exactly, which the caller reads from W: pivoted column
+// i of R (original column perm[i]) has rows 0..min(i, k-1) in W[i * p + ...].
+static __device__ RowBasis colpiv_basis(cd* W, int p, int q, cd* V, double delta_rel, int kmax, cd* taus,
+                                        double* cn, int* perm) {
+  RowBasis out = pivqr_trunc(W, p, p, q, delta_rel, kmax, taus, cn, perm);
+  form_q(W, p, p, out.k, taus, V, p);
+  out.flops += flops_formq(p, out.k);
   return out;
 }
 

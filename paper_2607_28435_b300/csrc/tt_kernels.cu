@@ -286,7 +286,7 @@ __device__ int dominant_basis(const cd* Z, int q, int p, SvdSmem& sm, int hb, do
                               int* piv, int* iw, double* red_d, int* red_i, int* st, double* fl) {
   __shared__ int perm_[LA_MAXP];
   const RowBasis rb = rrqr_basis(Z, q, p, p, sm.W, SVD_WCAP(hb), sm.V, ctol, rmax + 1, sm.tau, sm.sig,
-                                 perm_, red_d, red_i);
+                                 perm_);
   int k = rb.k;
   if (k > rmax) {
     *st = SFFT_ERANK_DEV;
@@ -692,9 +692,8 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
   // V for the p x (rank + 1) block of the basis step (see zip_smem on the host)
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb, LA_MAXP * (SFFT_SLOT_RANK_DEV + 1));
-  __shared__ int zperm[LA_MAXP];
-  __shared__ double zred_d[32];
-  __shared__ int zred_i[32];
+  __shared__ int zperm[LA_MAXQ];
+  __shared__ double zcn[LA_MAXQ];
   double fl = 0.0;
   WORK_LOOP_BEGIN(list, count, counter)
     const int n = n_arr[inst];
@@ -736,6 +735,9 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
       }
       __syncthreads();
       const int q = s1 * rA1, p = 2 * rc;
+      // T = Z^H (p x q, column-major) goes straight to shared memory when it
+      // fits: Z's row-major buffer and T's column-major one share the index
+      const bool direct = q <= LA_MAXQ && p * q <= SVD_WCAP(hb);
       for (int idx = threadIdx.x; idx < q * p; idx += blockDim.x) {
         const int row = idx / p, col = idx - row * p;
         const int ap = row / rA1, bp = row - ap * rA1;
@@ -749,21 +751,47 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
             acc = cfma(d, cconj(w), acc);
           }
         }
-        Z[idx] = acc;
+        if (direct)
+          sm.W[idx] = cconj(acc);
+        else
+          Z[idx] = acc;
       }
       __syncthreads();
       fl += flops_gemm(nd, rA0, 1) + flops_gemm((long long)q * p, 2 * s0, 1);
       cd* Bs = Bb + (size_t)s * core_stride_b;
       if (s == n - 1) {
         // q == 1: B[c][mu][0] = conj(Z[0, (c, mu)])
-        for (int idx = threadIdx.x; idx < p; idx += blockDim.x) Bs[idx] = cconj(Z[idx]);
+        for (int idx = threadIdx.x; idx < p; idx += blockDim.x) Bs[idx] = direct ? sm.W[idx] : cconj(Z[idx]);
         __syncthreads();
         break;
       }
-      // rank-revealing QR gives the kept left subspace of T (truncation error
-      // = trailing norm of the pivoted R); the final rounding makes it optimal
+      if (direct) {
+        // column-pivoted QR of T: B = Q[:, :k] is the output core and the
+        // next carry is CH = Z B = (R[:k] P^T)^H, read from R
+        const RowBasis rbz = colpiv_basis(sm.W, p, q, sm.V, ztol, SFFT_SLOT_RANK_DEV + 1, sm.tau, zcn, zperm);
+        int k = rbz.k;
+        if (k > SFFT_SLOT_RANK_DEV) {
+          st = SFFT_ERANK_DEV;
+          k = SFFT_SLOT_RANK_DEV;
+        }
+        for (int idx = threadIdx.x; idx < p * k; idx += blockDim.x) {
+          const int row = idx / k, cc = idx - row * k;
+          Bs[idx] = sm.V[(size_t)cc * p + row];
+        }
+        for (int idx = threadIdx.x; idx < q * k; idx += blockDim.x) {
+          const int i = idx / k, c = idx - i * k;
+          CH[(size_t)zperm[i] * k + c] = (c <= i) ? cconj(sm.W[(size_t)i * p + c]) : mkc(0.0, 0.0);
+        }
+        if (threadIdx.x == 0) rb[s + 1] = k;
+        __syncthreads();
+        fl += rbz.flops;
+        rc = k;
+        continue;
+      }
+      // otherwise: rank-revealing QR of the panel in global memory gives the
+      // kept left subspace of T, and the carry is the product Z B
       const RowBasis rbz = rrqr_basis(Z, q, p, p, sm.W, SVD_WCAP(hb), sm.V, ztol, SFFT_SLOT_RANK_DEV + 1,
-                                      sm.tau, sm.sig, zperm, zred_d, zred_i);
+                                      sm.tau, zcn, zperm);
       int k = rbz.k;
       if (k > SFFT_SLOT_RANK_DEV) {
         st = SFFT_ERANK_DEV;
