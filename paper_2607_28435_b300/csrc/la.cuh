@@ -95,6 +95,51 @@ static __device__ void hh_apply(const cd* v, int k, int h, cd t, cd* A, int lda,
   }
 }
 
+// As hh_apply with t = conj(tau), and also returns through post(j, c_j[k],
+// ||c_j[k+1..h)||^2) the exact squared norm of the updated rows below the
+// pivot, summed over the group's lanes (the column norms a pivoted QR needs).
+template <class Post>
+static __device__ void hh_apply_norms(const cd* v, int k, int h, cd t, cd* A, int lda, int j0, int j1,
+                                      Post post) {
+  const int ncols = j1 - j0;
+  if (ncols <= 0) return;
+  const int lg = hh_group_log2(ncols, h - k - 1);
+  const int S = 1 << lg;
+  const int lane = lane_id();
+  const int sl = lane & (S - 1);
+  const int gpw = 32 >> lg;
+  const int gpb = n_warps() * gpw;
+  for (int g0 = warp_id() * gpw; g0 < ncols; g0 += gpb) {
+    const int g = g0 + (lane >> lg);
+    const bool act = g < ncols;
+    cd* c = A + (size_t)(j0 + (act ? g : 0)) * lda;
+    cd dot = (act && sl == 0) ? c[k] : mkc(0.0, 0.0);
+    if (act)
+      for (int i = k + 1 + sl; i < h; i += S) dot = cfmac(v[i], c[i], dot);
+    for (int o = S >> 1; o > 0; o >>= 1) {
+      dot.x += __shfl_xor_sync(0xffffffffu, dot.x, o);
+      dot.y += __shfl_xor_sync(0xffffffffu, dot.y, o);
+    }
+    double nn = 0.0;
+    cd ck = mkc(0.0, 0.0);
+    if (act) {
+      const cd f = cmul(t, dot);
+      if (sl == 0) {
+        ck = csub(c[k], f);
+        c[k] = ck;
+      }
+      const cd nf = cneg(f);
+      for (int i = k + 1 + sl; i < h; i += S) {
+        const cd u = cfma(v[i], nf, c[i]);
+        c[i] = u;
+        nn = fma(u.x, u.x, fma(u.y, u.y, nn));
+      }
+    }
+    for (int o = S >> 1; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    if (act && sl == 0) post(j0 + g, ck, nn);
+  }
+}
+
 // Householder reflector of col[k..h) (LAPACK zlarfg convention), computed by
 // one warp: H^H (a0; x) = (beta; 0) with beta real, H = I - tau v v^H,
 // v = (1; x / (a0 - beta)). On return col[k] = beta, col[k+1..h) = v, and the
@@ -337,10 +382,123 @@ __host__ __device__ inline double flops_hestenes(long long p, long long m, long 
 }
 __host__ __device__ inline double flops_gemm(long long m, long long n, long long k) { return (double)(8 * m * n * k); }
 
+// Truncated Householder QR with column pivoting of A (m x ncol, column-major,
+// leading dim lda, smem): A P = Q R with the column of largest remaining norm
+// first, stopped at the smallest k >= 1 with ||R[k:, k:]||_F <= delta_rel
+// ||A||_F (or at k = min(m, ncol, kmax); delta_rel < 0 never stops early). On
+// return rows 0..k-1 of R are final in the upper part of A (pivoted column
+// order), the reflectors of steps 0..k-1 lie below the diagonal with
+// taus[0..k), and perm[i] is the original index of pivoted column i.
+// ||R[k:, k:]||_F is the error of keeping k rows. The remaining column norms
+// are summed exactly from the updated rows at every step (by the lanes that
+// update them), so no downdating error builds up near the truncation level.
+// Smem: taus (min(m, ncol) entries), cn and perm (ncol entries).
+#define LA_MAXQ 128
+struct RowBasis {
+  int k;
+  double flops;
+};
+
+static __device__ RowBasis pivqr_trunc(cd* A, int lda, int m, int ncol, double delta_rel, int kmax, cd* taus,
+                                       double* cn, int* perm) {
+  __shared__ int ctl;  // 1 once the rank is found
+  const int lane = lane_id(), warp = warp_id();
+  RowBasis out;
+  out.k = 1;
+  out.flops = 0.0;
+  // exact column norms
+  for (int j = warp; j < ncol; j += n_warps()) {
+    const cd* cj = A + (size_t)j * lda;
+    double ss = 0.0;
+    for (int i = lane; i < m; i += 32) ss = fma(cj[i].x, cj[i].x, fma(cj[i].y, cj[i].y, ss));
+    ss = warp_sum(ss);
+    if (lane == 0) {
+      cn[j] = ss;
+      perm[j] = j;
+    }
+  }
+  __syncthreads();
+  double total = 0.0;
+  for (int j = lane; j < ncol; j += 32) total += cn[j];
+  total = warp_sum(total);
+  const double delta2 = delta_rel < 0.0 ? -1.0 : delta_rel * delta_rel * total;
+  const int kstop = min(min(m, ncol), kmax);
+  for (int k = 0;; ++k) {
+    if (warp == 0) {
+      // trailing norm ||R[k:, k:]||^2 and the pivot column
+      double tr = 0.0, best = -1.0;
+      int bi = 0x7fffffff;
+      for (int j = k + lane; j < ncol; j += 32) {
+        const double v = cn[j];
+        tr += v;
+        if (v > best) {
+          best = v;
+          bi = j;
+        }
+      }
+      tr = warp_sum(tr);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      const bool stop = (k >= 1 && tr <= delta2) || k >= kstop;
+      if (!stop) {
+        if (bi != k) {
+          cd* ck = A + (size_t)k * lda;
+          cd* cb = A + (size_t)bi * lda;
+          for (int i = lane; i < m; i += 32) {
+            const cd tmp = ck[i];
+            ck[i] = cb[i];
+            cb[i] = tmp;
+          }
+          if (lane == 0) {
+            const double t1 = cn[k];
+            cn[k] = cn[bi];
+            cn[bi] = t1;
+            const int t3 = perm[k];
+            perm[k] = perm[bi];
+            perm[bi] = t3;
+          }
+        }
+        __syncwarp();
+        const cd tau = hh_reflector_warp(A + (size_t)k * lda, k, m);
+        if (lane == 0) taus[k] = tau;
+      }
+      if (lane == 0) ctl = stop ? 1 : 0;
+    }
+    __syncthreads();
+    if (ctl) {
+      out.k = max(k, 1);
+      break;
+    }
+    const cd tau = taus[k];
+    if (tau.x != 0.0 || tau.y != 0.0) {
+      hh_apply_norms(A + (size_t)k * lda, k, m, cconj(tau), A, lda, k + 1, ncol,
+                     [&](int j, cd, double nn) { cn[j] = nn; });
+    } else {
+      // H = I: rows below k are unchanged; drop row k from the norms
+      for (int j = k + 1 + threadIdx.x; j < ncol; j += blockDim.x) {
+        const cd* cj = A + (size_t)j * lda;
+        double ss = 0.0;
+        for (int i = k + 1; i < m; ++i) ss = fma(cj[i].x, cj[i].x, fma(cj[i].y, cj[i].y, ss));
+        cn[j] = ss;
+      }
+    }
+    __syncthreads();
+    out.flops += flops_qr_step(m, ncol, k);
+  }
+  return out;
+}
+
 // Right singular vectors of a tall-skinny Z (q x p, row-major, leading dim
 // ldz, read only; any address space). Streaming Householder QR over row blocks
-// of hb rows gives R (Z = Q R); the columns of L = R^H are then orthogonalised
-// by Hestenes' method, so L W = Y with Y/||Y|| the left singular vectors of
+// of hb rows gives R (Z = Q R), and a column-pivoted QR of R gives R2; the
+// columns of L = R2^H are then orthogonalised by Hestenes' method, so L W = Y with Y/||Y|| the left singular vectors of
 // R^H, i.e. the right singular vectors of Z.
 // Output: V (p x m, column-major, leading dim p) in smem, sig[m] in
 // descending order, with V[:, i] the vector of sig[i].
@@ -384,7 +542,12 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
   int ldw;
   const int nR = stream_qr(Z, q, p, ldz, W, wcap, taus, &ldw);
   const int m = nR;
-  // L = R^H (p x m) into V
+  // R P = Q2 R2 with column pivoting: the rows of R2 come out graded, which
+  // makes the Jacobi sweeps on R2^H converge in fewer sweeps (Drmac and
+  // Veselic 2008); sig serves as the norm scratch until the sort below
+  __shared__ int pperm[LA_MAXP];
+  const RowBasis pre = pivqr_trunc(W, ldw, m, p, -1.0, m, taus, sig, pperm);
+  // L = R2^H (p x m) into V, rows in pivoted order
   for (int idx = threadIdx.x; idx < p * m; idx += blockDim.x) {
     const int c = idx / p, i = idx - c * p;
     V[(size_t)c * p + i] = (i >= c) ? cconj(W[(size_t)i * ldw + c]) : mkc(0.0, 0.0);
@@ -403,7 +566,7 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
       carried = carried + b < p ? carried + b : p;
       rows -= b;
     }
-    out.flops = f + flops_hestenes(p, m, out.sweeps < 0 ? 60 : out.sweeps) + (double)(4 * p * m);
+    out.flops = f + pre.flops + flops_hestenes(p, m, out.sweeps < 0 ? 60 : out.sweeps) + (double)(4 * p * m);
   }
   // column norms
   double* nrm = reinterpret_cast<double*>(W);  // W is free now
@@ -425,7 +588,7 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
     }
     sig[rank] = sc;
     const double inv = sc > 1e-290 ? 1.0 / sc : 0.0;
-    for (int i = 0; i < p; ++i) Vs[(size_t)rank * p + i] = cscale(V[(size_t)c * p + i], inv);
+    for (int i = 0; i < p; ++i) Vs[(size_t)rank * p + pperm[i]] = cscale(V[(size_t)c * p + i], inv);
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < p * m; idx += blockDim.x) V[idx] = Vs[idx];
@@ -572,139 +735,6 @@ static __device__ void maxvol(const cd* A, int lda, int N, int r, int* piv, cd* 
     if (threadIdx.x == 0) piv[j] = i;
     __syncthreads();
   }
-}
-
-// Truncated Householder QR with column pivoting of A (m x ncol, column-major,
-// leading dim lda, smem): A P = Q R with the column of largest remaining norm
-// first, stopped at the smallest k >= 1 with ||R[k:, k:]||_F <= delta_rel
-// ||A||_F (or at k = min(m, ncol, kmax)). On return rows 0..k-1 of R are final
-// in the upper part of A (pivoted column order), the reflectors of steps
-// 0..k-1 lie below the diagonal with taus[0..k), and perm[i] is the original
-// index of pivoted column i. ||R[k:, k:]||_F is the error of keeping k rows.
-// Column norms are downdated after each step (|R[k, j]|^2 subtracted) and
-// recomputed from the rows once a norm has fallen below 1e-8 of its value at
-// the last recomputation, the safeguard of LAPACK's xGEQP3.
-// Smem: taus (min(m, ncol) entries), cn and perm (ncol entries, ncol <= LA_MAXQ).
-#define LA_MAXQ 128
-struct RowBasis {
-  int k;
-  double flops;
-};
-
-static __device__ RowBasis pivqr_trunc(cd* A, int lda, int m, int ncol, double delta_rel, int kmax, cd* taus,
-                                       double* cn, int* perm) {
-  __shared__ double ref[LA_MAXQ];
-  __shared__ int flag[LA_MAXQ];
-  __shared__ int ctl;  // 1 once the rank is found
-  const int lane = lane_id(), warp = warp_id();
-  RowBasis out;
-  out.k = 1;
-  out.flops = 0.0;
-  // exact column norms
-  for (int j = warp; j < ncol; j += n_warps()) {
-    const cd* cj = A + (size_t)j * lda;
-    double ss = 0.0;
-    for (int i = lane; i < m; i += 32) ss = fma(cj[i].x, cj[i].x, fma(cj[i].y, cj[i].y, ss));
-    ss = warp_sum(ss);
-    if (lane == 0) {
-      cn[j] = ss;
-      ref[j] = ss;
-      flag[j] = 0;
-      perm[j] = j;
-    }
-  }
-  __syncthreads();
-  double total = 0.0;
-  for (int j = lane; j < ncol; j += 32) total += cn[j];
-  total = warp_sum(total);
-  const double delta2 = delta_rel * delta_rel * total;
-  const int kstop = min(min(m, ncol), kmax);
-  for (int k = 0;; ++k) {
-    if (warp == 0) {
-      // norms that lost too many digits to downdating: recompute rows k..m-1
-      for (int jj = k; jj < ncol; ++jj) {
-        if (!flag[jj]) continue;
-        const cd* cj = A + (size_t)jj * lda;
-        double ss = 0.0;
-        for (int i = k + lane; i < m; i += 32) ss = fma(cj[i].x, cj[i].x, fma(cj[i].y, cj[i].y, ss));
-        ss = warp_sum(ss);
-        __syncwarp();
-        if (lane == 0) {
-          cn[jj] = ss;
-          ref[jj] = ss;
-          flag[jj] = 0;
-        }
-        __syncwarp();
-      }
-      // trailing norm ||R[k:, k:]||^2 and the pivot column
-      double tr = 0.0, best = -1.0;
-      int bi = 0x7fffffff;
-      for (int j = k + lane; j < ncol; j += 32) {
-        const double v = cn[j];
-        tr += v;
-        if (v > best) {
-          best = v;
-          bi = j;
-        }
-      }
-      tr = warp_sum(tr);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) {
-          best = ov;
-          bi = oi;
-        }
-      }
-      const bool stop = (k >= 1 && tr <= delta2) || k >= kstop;
-      if (!stop) {
-        if (bi != k) {
-          cd* ck = A + (size_t)k * lda;
-          cd* cb = A + (size_t)bi * lda;
-          for (int i = lane; i < m; i += 32) {
-            const cd tmp = ck[i];
-            ck[i] = cb[i];
-            cb[i] = tmp;
-          }
-          if (lane == 0) {
-            const double t1 = cn[k], t2 = ref[k];
-            cn[k] = cn[bi];
-            ref[k] = ref[bi];
-            cn[bi] = t1;
-            ref[bi] = t2;
-            const int t3 = perm[k];
-            perm[k] = perm[bi];
-            perm[bi] = t3;
-          }
-        }
-        __syncwarp();
-        const cd tau = hh_reflector_warp(A + (size_t)k * lda, k, m);
-        if (lane == 0) taus[k] = tau;
-      }
-      if (lane == 0) ctl = stop ? 1 : 0;
-    }
-    __syncthreads();
-    if (ctl) {
-      out.k = max(k, 1);
-      break;
-    }
-    const cd tau = taus[k];
-    auto downdate = [&](int j, cd rkj) {
-      const double c = cn[j] - cabs2(rkj);
-      cn[j] = c;
-      if (c <= 1e-8 * ref[j]) flag[j] = 1;
-    };
-    if (tau.x != 0.0 || tau.y != 0.0) {
-      hh_apply(A + (size_t)k * lda, k, m, cconj(tau), A, lda, k + 1, ncol, downdate);
-    } else {
-      // H = I: row k is already final, its entries still leave the norms
-      for (int j = k + 1 + threadIdx.x; j < ncol; j += blockDim.x) downdate(j, A[(size_t)j * lda + k]);
-    }
-    __syncthreads();
-    out.flops += flops_qr_step(m, ncol, k);
-  }
-  return out;
 }
 
 // Truncated row-space basis of a tall Z (q x p) by rank-revealing QR.

@@ -268,33 +268,42 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
 // r_b suffixes (the n - b least significant bits), for bonds b = 0..n. The
 // two-site supercore at bond b (sites b-1, b) is
 //   Phi[(i, l1), (l2, t)] = x( ((I[b-1][i] 2 + l1) 2 + l2) 2^(n-b-1) + J[b+1][t] ).
-// Left-to-right sweeps pick I[b] by maxvol on the left singular vectors of Phi,
-// right-to-left sweeps pick J[b] from its right singular vectors; the singular
-// values set the rank (relative threshold 0.01 tol, cap max_rank). The
-// dominant subspaces come from a rank-revealing QR of the supercore (its
-// trailing norm bounds the discarded part), which serves maxvol as well as
-// the singular vectors would at a fraction of the cost. Sweeps stop
+// Left-to-right sweeps pick I[b] from the columns (i, l1) of Phi^T,
+// right-to-left sweeps pick J[b] from the columns (l2, t) of Phi: in both a
+// column-pivoted QR, stopped once the trailing norm is below 0.01 tol of the
+// supercore's norm (rank cap max_rank), keeps the pivot columns, i.e. the
+// greedy maximum-volume subset that maxvol would refine. Sweeps stop
 // when the ranks repeat, after at least two. Assembly then runs one left-to-right pass: the fibre
 // matrix F_s[(i, l), t] = x((I[s][i] 2 + l) 2^(n-s-1) + J[s+1][t]) is factored
 // F = Q R, maxvol on Q gives I[s+1], and the core is Q Q[piv]^{-1}, which
 // interpolates x on the cross (Oseledets & Tyrtyshnikov 2010; Savostyanov &
 // Oseledets 2011). Rounding afterwards makes the cores right-orthonormal.
-// Dominant subspace of the rows of Z (q x p): rank-revealing QR basis B
-// (p x k, k from the trailing-norm rule at ctol, capped at rmax), copied to V,
-// then maxvol on it; returns k, the chosen rows in piv.
+// Index choice of a cross step: the k columns of Z (q x p) picked by a
+// column-pivoted QR truncated at ctol (the greedy maximum-volume column
+// subset, as in Q-DEIM), k capped at rmax; returns k, the columns in piv.
+// Pivoting Z and pivoting R of Z = Q R choose the same columns, so the rank
+// is the one a rank-revealing QR of the supercore gives.
 __device__ int dominant_basis(const cd* Z, int q, int p, SvdSmem& sm, int hb, double ctol, int rmax,
                               int* piv, int* iw, double* red_d, int* red_i, int* st, double* fl) {
   __shared__ int perm_[LA_MAXP];
-  const RowBasis rb = rrqr_basis(Z, q, p, p, sm.W, SVD_WCAP(hb), sm.V, ctol, rmax + 1, sm.tau, sm.sig,
-                                 perm_);
+  (void)hb;
+  (void)iw;
+  (void)red_d;
+  (void)red_i;
+  // Z (row-major) -> W (column-major, leading dim q)
+  for (int idx = threadIdx.x; idx < q * p; idx += blockDim.x) {
+    const int row = idx / p, col = idx - row * p;
+    sm.W[(size_t)col * q + row] = Z[idx];
+  }
+  __syncthreads();
+  const RowBasis rb = pivqr_trunc(sm.W, q, q, p, ctol, rmax + 1, sm.tau, sm.sig, perm_);
   int k = rb.k;
   if (k > rmax) {
     *st = SFFT_ERANK_DEV;
     k = rmax;
   }
-  for (int idx = threadIdx.x; idx < p * k; idx += blockDim.x) sm.V[idx] = sm.W[idx];
+  for (int c = threadIdx.x; c < k; c += blockDim.x) piv[c] = perm_[c];
   __syncthreads();
-  maxvol(sm.V, p, p, k, piv, sm.W, iw, red_d, red_i);
   *fl += rb.flops;
   return k;
 }
