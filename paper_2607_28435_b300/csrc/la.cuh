@@ -497,8 +497,8 @@ static __device__ RowBasis pivqr_trunc(cd* A, int lda, int m, int ncol, double d
 
 // Right singular vectors of a tall-skinny Z (q x p, row-major, leading dim
 // ldz, read only; any address space). Streaming Householder QR over row blocks
-// of hb rows gives R (Z = Q R), and a column-pivoted QR of R gives R2; the
-// columns of L = R2^H are then orthogonalised by Hestenes' method, so L W = Y with Y/||Y|| the left singular vectors of
+// of hb rows gives R (Z = Q R); the columns of L = R^H are then orthogonalised
+// by Hestenes' method, so L W = Y with Y/||Y|| the left singular vectors of
 // R^H, i.e. the right singular vectors of Z.
 // Output: V (p x m, column-major, leading dim p) in smem, sig[m] in
 // descending order, with V[:, i] the vector of sig[i].
@@ -542,12 +542,7 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
   int ldw;
   const int nR = stream_qr(Z, q, p, ldz, W, wcap, taus, &ldw);
   const int m = nR;
-  // R P = Q2 R2 with column pivoting: the rows of R2 come out graded, which
-  // makes the Jacobi sweeps on R2^H converge in fewer sweeps (Drmac and
-  // Veselic 2008); sig serves as the norm scratch until the sort below
-  __shared__ int pperm[LA_MAXP];
-  const RowBasis pre = pivqr_trunc(W, ldw, m, p, -1.0, m, taus, sig, pperm);
-  // L = R2^H (p x m) into V, rows in pivoted order
+  // L = R^H (p x m) into V
   for (int idx = threadIdx.x; idx < p * m; idx += blockDim.x) {
     const int c = idx / p, i = idx - c * p;
     V[(size_t)c * p + i] = (i >= c) ? cconj(W[(size_t)i * ldw + c]) : mkc(0.0, 0.0);
@@ -566,7 +561,7 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
       carried = carried + b < p ? carried + b : p;
       rows -= b;
     }
-    out.flops = f + pre.flops + flops_hestenes(p, m, out.sweeps < 0 ? 60 : out.sweeps) + (double)(4 * p * m);
+    out.flops = f + flops_hestenes(p, m, out.sweeps < 0 ? 60 : out.sweeps) + (double)(4 * p * m);
   }
   // column norms
   double* nrm = reinterpret_cast<double*>(W);  // W is free now
@@ -588,7 +583,7 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
     }
     sig[rank] = sc;
     const double inv = sc > 1e-290 ? 1.0 / sc : 0.0;
-    for (int i = 0; i < p; ++i) Vs[(size_t)rank * p + pperm[i]] = cscale(V[(size_t)c * p + i], inv);
+    for (int i = 0; i < p; ++i) Vs[(size_t)rank * p + i] = cscale(V[(size_t)c * p + i], inv);
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < p * m; idx += blockDim.x) V[idx] = Vs[idx];
