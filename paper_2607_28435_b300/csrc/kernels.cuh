@@ -64,11 +64,15 @@ inline RoundSmem zip_smem() {
   r.bytes = sizeof(cd) * ((size_t)(r.pmax + r.hb) * r.pmax + r.vcap + r.pmax) + sizeof(double) * r.pmax + 320;
   return r;
 }
-inline RoundSmem round_smem(int d) {
+// Shared memory of k_tt_round. The left-orthogonalisation pass writes an
+// explicit Q of d r x r into V; without it (left_orth = 0) V holds only the
+// r x r right singular vectors, and the smaller carve lets 4 CTAs share an SM
+// for d = 2. A launch with left_orth = 1 must use the full carve.
+inline RoundSmem round_smem(int d, bool left_orth = true) {
   RoundSmem r;
   r.pmax = SFFT_SLOT_RANK_DEV;
   r.hb = (d - 1) * SFFT_SLOT_RANK_DEV;  // W = (pmax + hb) pmax >= d r x r
-  r.vcap = d * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV;
+  r.vcap = (left_orth ? d : 1) * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV;
   r.bytes = sizeof(cd) * ((size_t)(r.pmax + r.hb) * r.pmax + r.vcap + r.pmax) + sizeof(double) * r.pmax + 320;
   return r;
 }

@@ -524,7 +524,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
         SFFT_ZIP_SCRATCH, b.status, zs.hb, acc_ptr(ctx));
   }
   CK(cudaGetLastError());
-  const RoundSmem rs2 = round_smem(2);
+  const RoundSmem rs2 = round_smem(2, false);
   grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, rs2.bytes));
   if ((s = ensure(ctx, "round_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * grid, &p))) return s;
   {
@@ -861,7 +861,7 @@ sfft_status sfft_tt_apply_qft(sfft_ctx* ctx, int32_t n, const int32_t* in_ranks,
       SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(scr), SFFT_ZIP_SCRATCH, sd, zs.hb,
       nullptr);
   CK(cudaGetLastError());
-  const RoundSmem rs = round_smem(2);
+  const RoundSmem rs = round_smem(2, false);
   k_tt_round<<<1, kThreads, rs.bytes, ctx->stream>>>(nullptr, 1, nullptr, nd, 2, 0, td, md, B, od,
                                                     SFFT_CORE_STRIDE_D2, reinterpret_cast<int*>(rb),
                                                     reinterpret_cast<cd*>(scr), SFFT_ROUND_SCRATCH, sd, rs.hb,

@@ -542,7 +542,7 @@ __global__ void k_mpo_interp(int n, int P, cd* W, int core_stride,
 // re-orthonormalised by QR, Y = Q_V R_V, so that X ~= (U_k R_V^H) Q_V^H exactly
 // up to the truncation, with Q_V^H right-orthonormal to machine precision
 // (no division by small singular values).
-__global__ void k_tt_round(const int* list, int count, int* counter, const int* n_arr, int d,
+__global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count, int* counter, const int* n_arr, int d,
                            int left_orth,
                            const double* tol_arr, const int* maxrank_arr,
                            cd* tt, const long long* tt_off, int core_stride,
