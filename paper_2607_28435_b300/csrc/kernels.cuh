@@ -21,8 +21,8 @@
 
 // profiling phases (index into the flop / evaluation accumulators)
 enum { PH_PROBE = 0, PH_BUILD = 1, PH_ZIPUP = 2, PH_ROUND = 3, PH_READOUT = 4, PH_MPO = 5,
-       PH_DENSE_SAMPLE = 6, PH_DENSE_FFT = 7, PH_DENSE_GATHER = 8 };
-#define SFFT_NPHASE_DEV 9
+       PH_DENSE_SAMPLE = 6, PH_DENSE_FFT = 7, PH_DENSE_GATHER = 8, PH_CROSS = 9 };
+#define SFFT_NPHASE_DEV 10
 
 // status codes (same values as sfft_status)
 #define SFFT_EINVAL_DEV 1

@@ -482,7 +482,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     const int grid = std::min(ncr, ctx->num_sms * blocks_per_sm((const void*)k_integrand_cross, smem));
     if ((s = ensure(ctx, "cross_scratch", sizeof(cd) * (size_t)4096 * grid, &p))) return s;
     {
-      PhaseScope ps(ctx, PH_BUILD);
+      PhaseScope ps(ctx, PH_CROSS);
       k_integrand_cross<<<grid, kThreads, smem, ctx->stream>>>(
           b.P, cross_dev, ncr, ctr + 1, reinterpret_cast<cd*>(p), 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
           b.a_ranks, b.status, kHb, acc_ptr(ctx), kCrossSweeps);
@@ -492,11 +492,11 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     const RoundSmem rs = round_smem(2);
     const int g2 = std::min(ncr, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, rs.bytes));
     if ((s = ensure(ctx, "xround_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * g2, &p))) return s;
-    PhaseScope ps(ctx, PH_BUILD);
+    PhaseScope ps(ctx, PH_CROSS);
     k_tt_round<<<g2, kThreads, rs.bytes, ctx->stream>>>(cross_dev, ncr, ctr + 2, b.n_arr, 2, 1, b.tol_arr,
                                                         b.maxr_arr, b.A, b.a_off, SFFT_CORE_STRIDE_D2, b.a_ranks,
                                                         reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH, b.status,
-                                                        rs.hb, acc_ptr(ctx), PH_BUILD, rs.pmax, rs.vcap);
+                                                        rs.hb, acc_ptr(ctx), PH_CROSS, rs.pmax, rs.vcap);
   }
   CK(cudaGetLastError());
   if (!apply) return SFFT_OK;

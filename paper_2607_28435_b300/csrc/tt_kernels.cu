@@ -463,8 +463,8 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
     __syncthreads();
   WORK_LOOP_END
   if (acc && threadIdx.x == 0) {
-    atomicAdd(acc + PH_BUILD, fl);
-    atomicAdd(acc + SFFT_NPHASE_DEV + PH_BUILD, evals);
+    atomicAdd(acc + PH_CROSS, fl);
+    atomicAdd(acc + SFFT_NPHASE_DEV + PH_CROSS, evals);
   }
 }
 

@@ -20,11 +20,12 @@ c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_
 SFFT_OK, SFFT_EINVAL, SFFT_EMOMENT, SFFT_ENOMEM, SFFT_ECUDA, SFFT_ERANK, SFFT_ENOCONV, SFFT_ETIMEOUT = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "EMOMENT", "ENOMEM", "ECUDA", "ERANK", "ENOCONV", "ETIMEOUT"]
 MAX_N = 48
-NPHASES = 9
+NPHASES = 10
 PHASE_NAMES = ["probe", "build", "zipup", "round", "readout", "mpo", "dense_sample", "dense_fft",
-               "dense_gather"]
+               "dense_gather", "cross"]
 PHASE_KERNELS = ["k_support_probe", "k_integrand_ttsvd", "k_zipup", "k_tt_round", "k_readout",
-                 "k_mpo_interp+k_tt_round", "k_dense_sample", "k_fft_pass", "k_dense_gather"]
+                 "k_mpo_interp+k_tt_round", "k_dense_sample", "k_fft_pass", "k_dense_gather",
+                 "k_integrand_cross+k_tt_round"]
 MAX_RANK = 32
 MAX_STRIKES = 65536
 DENSE_MAX_N = 32
