@@ -5,6 +5,7 @@ is present, the calls raise.
 """
 from __future__ import annotations
 
+import collections.abc
 import ctypes
 import math
 import os
@@ -94,6 +95,61 @@ def load_library(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+class Batch:
+    """Problems and strike sets marshalled into the C arrays of sfft_price_batch,
+    with the per-instance status and info arrays the call fills. Building one
+    costs Python time proportional to the batch (tens of ms for 4096 problems);
+    a caller that prices the same batch repeatedly builds it once. Lazy
+    statuses()/infos() convert the filled arrays back to Python."""
+
+    def __init__(self, problems, strikes):
+        cnt = len(problems)
+        n1 = max(cnt, 1)
+        self.count = cnt
+        self.problems = (SfftProblem * n1)(*[to_c_problem(p) for p in problems])
+        self.l_begin = (c_int64 * n1)(*[int(s[0]) for s in strikes])
+        self.stride = (c_int64 * n1)(*[int(s[1]) for s in strikes])
+        self.q = (c_int32 * n1)(*[int(s[2]) for s in strikes])
+        self.total = sum(int(s[2]) for s in strikes)
+        self.status = (c_int32 * n1)()
+        self.info = (SfftInfo * n1)()
+
+    def statuses(self):
+        return [self.status[i] for i in range(self.count)]
+
+    def _info(self, i):
+        return dict(status=self.info[i].status, int_rank=self.info[i].int_rank,
+                    mpo_rank=self.info[i].mpo_rank, out_rank=self.info[i].out_rank)
+
+    def infos(self):
+        return [self._info(i) for i in range(self.count)]
+
+    def status_view(self):
+        return _View(self.count, lambda i: self.status[i])
+
+    def info_view(self):
+        return _View(self.count, self._info)
+
+
+class _View(collections.abc.Sequence):
+    """Read-only sequence over a filled C array, converting one entry per access."""
+
+    def __init__(self, n, get):
+        self._n, self._get = n, get
+
+    def __len__(self):
+        return self._n
+
+    def __getitem__(self, i):
+        if isinstance(i, slice):
+            return [self._get(k) for k in range(*i.indices(self._n))]
+        if i < 0:
+            i += self._n
+        if not 0 <= i < self._n:
+            raise IndexError(i)
+        return self._get(i)
 
 
 class SfftError(RuntimeError):
@@ -194,30 +250,25 @@ class Pricer:
     # -- pricing ------------------------------------------------------------
     def _price(self, fn, problems, strikes, prices=None, log_strikes=None, raise_on_error=True):
         torch = self.torch
-        cnt = len(problems)
-        arr = (SfftProblem * max(cnt, 1))(*[to_c_problem(p) for p in problems])
-        lb = (c_int64 * max(cnt, 1))(*[int(s[0]) for s in strikes])
-        st = (c_int64 * max(cnt, 1))(*[int(s[1]) for s in strikes])
-        q = (c_int32 * max(cnt, 1))(*[int(s[2]) for s in strikes])
-        tot = sum(int(s[2]) for s in strikes)
+        b = problems if isinstance(problems, Batch) else Batch(problems, strikes)
+        cnt, tot = b.count, b.total
         dev = torch.device("cuda", self.device)
         if prices is None:
             prices = torch.empty(max(tot, 1), dtype=torch.float64, device=dev)
         if log_strikes is None:
             log_strikes = torch.empty(max(tot, 1), dtype=torch.float64, device=dev)
-        status = (c_int32 * max(cnt, 1))()
-        info = (SfftInfo * max(cnt, 1))()
         self._stream()
-        s = fn(self.h, arr, cnt, lb, st, q, c_void_p(_ptr(prices)), c_void_p(_ptr(log_strikes)),
-               status, info)
+        s = fn(self.h, b.problems, cnt, b.l_begin, b.stride, b.q, c_void_p(_ptr(prices)),
+               c_void_p(_ptr(log_strikes)), b.status, b.info)
         if raise_on_error and s not in (SFFT_OK,):
             self._check(s)
-        return prices[:tot], log_strikes[:tot], [status[i] for i in range(cnt)], \
-            [dict(status=info[i].status, int_rank=info[i].int_rank, mpo_rank=info[i].mpo_rank,
-                  out_rank=info[i].out_rank) for i in range(cnt)]
+        if b is problems:  # a reused Batch: hand back its arrays, converted on access
+            return prices[:tot], log_strikes[:tot], b.status_view(), b.info_view()
+        return prices[:tot], log_strikes[:tot], b.statuses(), b.infos()
 
-    def price_batch(self, problems, strikes, prices=None, log_strikes=None, raise_on_error=True):
-        """TT-SFFT prices. strikes: list of (l_begin, stride, q) per problem."""
+    def price_batch(self, problems, strikes=None, prices=None, log_strikes=None, raise_on_error=True):
+        """TT-SFFT prices. strikes: list of (l_begin, stride, q) per problem; or pass a
+        Batch as `problems` (strikes=None) to reuse its marshalled arrays."""
         return self._price(self.lib.sfft_price_batch, problems, strikes, prices, log_strikes,
                            raise_on_error)
 

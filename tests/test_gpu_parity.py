@@ -297,6 +297,22 @@ def test_config3_sample(pricer):
     check_prices(pricer, sel, sample=6, seed=3)
 
 
+def test_reused_batch_matches_lists(pricer):
+    # a Batch marshalled once gives the same prices, statuses and ranks as the
+    # list form, on two calls in a row
+    from paper_2607_28435_b300 import sfft
+    probs = wl.config3_batch(24)
+    strikes = [cm.strike_window(p) for p in probs]
+    p0, k0, s0, i0 = pricer.price_batch(probs, strikes, raise_on_error=False)
+    b = sfft.Batch(probs, strikes)
+    for _ in range(2):
+        p1, k1, s1, i1 = pricer.price_batch(b, None, raise_on_error=False)
+        assert list(s1) == s0
+        assert list(i1) == i0
+        assert np.array_equal(p1.cpu().numpy(), p0.cpu().numpy())
+        assert np.array_equal(k1.cpu().numpy(), k0.cpu().numpy())
+
+
 def test_heavy_tail_prices(pricer):
     # cross-built integrands priced end to end; oracle over the full grid
     probs = _heavy_vg(20)
