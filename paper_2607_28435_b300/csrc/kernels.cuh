@@ -35,7 +35,8 @@ __global__ void k_support_probe(const InstParams* P, int count, double probe_tol
 __global__ void k_integrand_ttsvd(const InstParams* P, const int* m_arr, const int* list, int count,
                                   int* counter, cd* scratch,
                                   long long scratch_stride, cd* tt, const long long* tt_off,
-                                  int core_stride, int* ranks_all, int* status, int hb, double* acc);
+                                  int core_stride, int* ranks_all, int* status, int hb, double* acc,
+                                  int pmax, int* defer, const int* dcount);
 __global__ void k_integrand_cross(const InstParams* P, const int* list, int count, int* counter,
                                   cd* scratch, long long scratch_stride, cd* tt,
                                   const long long* tt_off, int core_stride, int* ranks_all,
@@ -46,7 +47,7 @@ __global__ void k_tt_round(const int* list, int count, int* counter, const int* 
                            const int* maxrank_arr, cd* tt, const long long* tt_off,
                            int core_stride, int* ranks_all, cd* scratch,
                            long long scratch_stride, int* status, int hb, double* acc, int phase,
-                           int pmax, int vcap);
+                           int pmax, int vcap, int* defer, const int* dcount);
 
 // Shared memory of k_tt_round for physical dimension d: panels of at most
 // SFFT_SLOT_RANK_DEV columns; W holds a (d r) x r block, V the explicit Q.
@@ -68,11 +69,11 @@ inline RoundSmem zip_smem() {
 // explicit Q of d r x r into V; without it (left_orth = 0) V holds only the
 // r x r right singular vectors, and the smaller carve lets 4 CTAs share an SM
 // for d = 2. A launch with left_orth = 1 must use the full carve.
-inline RoundSmem round_smem(int d, bool left_orth = true) {
+inline RoundSmem round_smem(int d, bool left_orth = true, int pmax = SFFT_SLOT_RANK_DEV) {
   RoundSmem r;
-  r.pmax = SFFT_SLOT_RANK_DEV;
-  r.hb = (d - 1) * SFFT_SLOT_RANK_DEV;  // W = (pmax + hb) pmax >= d r x r
-  r.vcap = (left_orth ? d : 1) * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV;
+  r.pmax = pmax;
+  r.hb = (d - 1) * pmax;  // W = (pmax + hb) pmax >= d r x r
+  r.vcap = (left_orth ? d : 1) * pmax * pmax;
   r.bytes = sizeof(cd) * ((size_t)(r.pmax + r.hb) * r.pmax + r.vcap + r.pmax) + sizeof(double) * r.pmax + 320;
   return r;
 }

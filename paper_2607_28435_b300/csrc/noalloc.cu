@@ -158,7 +158,7 @@ extern "C" sfft_status sfft_tt_round_noalloc(int32_t n, int32_t d, const int32_t
   k_tt_round<<<1, kThreadsNa, rsm.bytes, sm>>>(nullptr, 1, nullptr, &prm->n, d, 1, &prm->tol,
                                               &prm->maxrank, tt, &prm->off, stride, ranks, tmp,
                                               SFFT_ROUND_SCRATCH, &prm->status, rsm.hb, nullptr, PH_ROUND,
-                                              rsm.pmax, rsm.vcap);
+                                              rsm.pmax, rsm.vcap, nullptr, nullptr);
   NA_CK(cudaGetLastError(), "launch of the rounding kernel failed");
   NaParams back;
   NA_CK(cudaMemcpyAsync(rk, ranks, sizeof rk, cudaMemcpyDeviceToHost, sm), "rank download failed");

@@ -24,6 +24,13 @@ static_assert(SFFT_MAX_RANK == SFFT_SLOT_RANK_DEV, "slot rank");
 namespace {
 
 const int kThreads = 256;
+// First-tier launches of the two-tier kernels: 128-thread CTAs with carves
+// for panels of up to kSmallP columns (builder) or ranks up to kSmallRoundR
+// (rounding); the batch's integrand ranks stay below 10 and its output ranks
+// below 25, so the full-size second tier rarely has work.
+const int kThreadsSmall = 128;
+const int kSmallP = 32;
+const int kSmallRoundR = 24;
 const int kHb = 36;  // row-block height reserved next to the 64-column panel
 const int kSvdMaxBits = 14;  // support blocks up to 2^14 points: TT-SVD; wider: cross
 const int kCrossSweeps = 6;
@@ -257,9 +264,9 @@ sfft_status check_strikes(sfft_ctx* ctx, int n, long long lb, long long stride, 
   return SFFT_OK;
 }
 
-int blocks_per_sm(const void* fn, size_t smem) {
+int blocks_per_sm(const void* fn, size_t smem, int threads = kThreads) {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kThreads, smem) != cudaSuccess) b = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, smem) != cudaSuccess) b = 1;
   return std::max(b, 1);
 }
 
@@ -344,7 +351,7 @@ sfft_status get_mpo(sfft_ctx* ctx, int n, double tol, const MpoEntry** out) {
         nullptr, 1, nullptr, reinterpret_cast<int*>(a), 4, 1, reinterpret_cast<double*>(a + 8),
         reinterpret_cast<int*>(a + 16), W, reinterpret_cast<long long*>(a + 24), SFFT_CORE_STRIDE_D4,
         rk, reinterpret_cast<cd*>(scr), SFFT_ROUND_SCRATCH, nullptr, rs.hb, acc_ptr(ctx), PH_MPO,
-        rs.pmax, rs.vcap);
+        rs.pmax, rs.vcap, nullptr, nullptr);
   }
   CK(cudaGetLastError());
   e.ranks.resize(SFFT_MAX_N + 1);
@@ -466,15 +473,35 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   b.all_list = all_dev;
   b.counters = ctr;
   const size_t smem = svd_smem();
+  // hand-off lists of the two-tier launches: [count, instances...]
+  int *defer_build, *defer_round;
+  if ((s = ensure(ctx, "defer_build", sizeof(int) * (cnt + 1), &p))) return s;
+  defer_build = reinterpret_cast<int*>(p);
+  if ((s = ensure(ctx, "defer_round", sizeof(int) * (cnt + 1), &p))) return s;
+  defer_round = reinterpret_cast<int*>(p);
+  CK(cudaMemsetAsync(defer_build, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(defer_round, 0, sizeof(int), ctx->stream));
   if (!svd_list.empty()) {
+    // tier 1: panels up to kSmallP columns, 128-thread CTAs, several per SM;
+    // tier 2: the full carve for the instances tier 1 handed on
     const int nsvd = (int)svd_list.size();
-    const int grid = std::min(nsvd, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem));
+    const size_t smem1 = la::ts_svd_smem_bytes(kSmallP, kSmallP) + 256;
+    const int grid1 = std::min(nsvd, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem1,
+                                                                  kThreadsSmall));
+    const int grid2 = std::min(nsvd, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem));
     const long long sstride = 2LL << mmax;
-    if ((s = ensure(ctx, "build_scratch", sizeof(cd) * sstride * grid, &p))) return s;
+    if ((s = ensure(ctx, "build_scratch", sizeof(cd) * sstride * std::max(grid1, grid2), &p))) return s;
+    {
+      PhaseScope ps(ctx, PH_BUILD);
+      k_integrand_ttsvd<<<grid1, kThreadsSmall, smem1, ctx->stream>>>(
+          b.P, m_dev, svd_dev, nsvd, ctr + 0, reinterpret_cast<cd*>(p), sstride, b.A, b.a_off,
+          SFFT_CORE_STRIDE_D2, b.a_ranks, b.status, kSmallP, acc_ptr(ctx), kSmallP, defer_build, nullptr);
+    }
+    CK(cudaGetLastError());
     PhaseScope ps(ctx, PH_BUILD);
-    k_integrand_ttsvd<<<grid, kThreads, smem, ctx->stream>>>(
-        b.P, m_dev, svd_dev, nsvd, ctr + 0, reinterpret_cast<cd*>(p), sstride, b.A, b.a_off,
-        SFFT_CORE_STRIDE_D2, b.a_ranks, b.status, kHb, acc_ptr(ctx));
+    k_integrand_ttsvd<<<grid2, kThreads, smem, ctx->stream>>>(
+        b.P, m_dev, defer_build + 1, 0, ctr + 5, reinterpret_cast<cd*>(p), sstride, b.A, b.a_off,
+        SFFT_CORE_STRIDE_D2, b.a_ranks, b.status, kHb, acc_ptr(ctx), LA_MAXP, nullptr, defer_build);
   }
   CK(cudaGetLastError());
   if (!cross_list.empty()) {
@@ -496,7 +523,8 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     k_tt_round<<<g2, kThreads, rs.bytes, ctx->stream>>>(cross_dev, ncr, ctr + 2, b.n_arr, 2, 1, b.tol_arr,
                                                         b.maxr_arr, b.A, b.a_off, SFFT_CORE_STRIDE_D2, b.a_ranks,
                                                         reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH, b.status,
-                                                        rs.hb, acc_ptr(ctx), PH_CROSS, rs.pmax, rs.vcap);
+                                                        rs.hb, acc_ptr(ctx), PH_CROSS, rs.pmax, rs.vcap, nullptr,
+                                                        nullptr);
   }
   CK(cudaGetLastError());
   if (!apply) return SFFT_OK;
@@ -524,16 +552,27 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
         SFFT_ZIP_SCRATCH, b.status, zs.hb, acc_ptr(ctx));
   }
   CK(cudaGetLastError());
+  // tier 1: ranks up to kSmallRoundR in 128-thread CTAs; tier 2: the rest
+  const RoundSmem rs1 = round_smem(2, false, kSmallRoundR);
   const RoundSmem rs2 = round_smem(2, false);
-  grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, rs2.bytes));
-  if ((s = ensure(ctx, "round_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * grid, &p))) return s;
+  const int grid1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, rs1.bytes, kThreadsSmall));
+  const int grid2 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, rs2.bytes));
+  if ((s = ensure(ctx, "round_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * std::max(grid1, grid2), &p)))
+    return s;
   {
     PhaseScope ps(ctx, PH_ROUND);
-    k_tt_round<<<grid, kThreads, rs2.bytes, ctx->stream>>>(all_dev, cnt, ctr + 4, b.n_arr, 2, 0, b.tol_arr,
-                                                           b.maxr_arr, b.B, b.a_off, SFFT_CORE_STRIDE_D2,
-                                                           b.b_ranks, reinterpret_cast<cd*>(p),
-                                                           SFFT_ROUND_SCRATCH, b.status, rs2.hb,
-                                                           acc_ptr(ctx), PH_ROUND, rs2.pmax, rs2.vcap);
+    k_tt_round<<<grid1, kThreadsSmall, rs1.bytes, ctx->stream>>>(
+        all_dev, cnt, ctr + 4, b.n_arr, 2, 0, b.tol_arr, b.maxr_arr, b.B, b.a_off, SFFT_CORE_STRIDE_D2,
+        b.b_ranks, reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH, b.status, rs1.hb, acc_ptr(ctx), PH_ROUND,
+        rs1.pmax, rs1.vcap, defer_round, nullptr);
+  }
+  CK(cudaGetLastError());
+  {
+    PhaseScope ps(ctx, PH_ROUND);
+    k_tt_round<<<grid2, kThreads, rs2.bytes, ctx->stream>>>(
+        defer_round + 1, 0, ctr + 6, b.n_arr, 2, 0, b.tol_arr, b.maxr_arr, b.B, b.a_off, SFFT_CORE_STRIDE_D2,
+        b.b_ranks, reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH, b.status, rs2.hb, acc_ptr(ctx), PH_ROUND,
+        rs2.pmax, rs2.vcap, nullptr, defer_round);
   }
   CK(cudaGetLastError());
   return SFFT_OK;
@@ -808,7 +847,7 @@ sfft_status sfft_tt_round(sfft_ctx* ctx, int32_t n, int32_t d, const int32_t* in
   k_tt_round<<<1, kThreads, rs.bytes, ctx->stream>>>(nullptr, 1, nullptr, nd, d, 1, td, md, T, od, stride,
                                                     reinterpret_cast<int*>(rd), reinterpret_cast<cd*>(scr),
                                                     SFFT_ROUND_SCRATCH, sd, rs.hb, nullptr, PH_ROUND, rs.pmax,
-                                                    rs.vcap);
+                                                    rs.vcap, nullptr, nullptr);
   CK(cudaGetLastError());
   int st = 0;
   CK(cudaMemcpyAsync(&st, sd, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -865,7 +904,7 @@ sfft_status sfft_tt_apply_qft(sfft_ctx* ctx, int32_t n, const int32_t* in_ranks,
   k_tt_round<<<1, kThreads, rs.bytes, ctx->stream>>>(nullptr, 1, nullptr, nd, 2, 0, td, md, B, od,
                                                     SFFT_CORE_STRIDE_D2, reinterpret_cast<int*>(rb),
                                                     reinterpret_cast<cd*>(scr), SFFT_ROUND_SCRATCH, sd, rs.hb,
-                                                    nullptr, PH_ROUND, rs.pmax, rs.vcap);
+                                                    nullptr, PH_ROUND, rs.pmax, rs.vcap, nullptr, nullptr);
   CK(cudaGetLastError());
   int st = 0;
   CK(cudaMemcpyAsync(&st, sd, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

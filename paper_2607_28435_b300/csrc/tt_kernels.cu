@@ -95,6 +95,19 @@ __device__ double cta_norm2(const cd* x, long long len, double* red) {
     const int inst = (list) ? (list)[slot_] : slot_;
 #define WORK_LOOP_END }
 
+// Two-tier launches: a first launch with a small shared-memory carve (more
+// CTAs per SM) hands every instance that does not fit it to a second launch
+// with the full carve. The hand-off appends the instance to defer[1..]
+// (defer[0] counts them) before anything of it has been written that the
+// second launch would not rewrite; the second launch reads its count from
+// defer[0] (dcount), so the host never waits for the first.
+__device__ __forceinline__ void defer_instance(int* defer, int inst) {
+  if (threadIdx.x == 0) {
+    const int i = atomicAdd(defer, 1);
+    defer[1 + i] = inst;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K1: integrand samples at listed indices
 // ---------------------------------------------------------------------------
@@ -170,11 +183,16 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
                                   long long scratch_stride,
                                   cd* tt, const long long* tt_off,
                                   int core_stride, int* ranks_all,
-                                  int* status, int hb, double* acc) {
+                                  int* status, int hb, double* acc, int pmax, int* defer,
+                                  const int* dcount) {
+  // panels of at most pmax columns (carve sized by the launch); with defer
+  // set, instances that need wider panels go to the full-size launch
   extern __shared__ double4 smem_raw[];
-  SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
+  SvdSmem sm = carve_svd_smem(smem_raw, pmax, hb);
+  const int wcap = (pmax + hb) * pmax;
+  const int count_ = dcount ? *dcount : count;
   double fl = 0.0, evals = 0.0;
-  WORK_LOOP_BEGIN(list, count, counter)
+  WORK_LOOP_BEGIN(list, count_, counter)
     const InstParams prm = P[inst];
     const int n = prm.n;
     const int m = m_arr[inst];
@@ -195,8 +213,14 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
     int rprev = 1;
     double delta = 0.0;
     int site = n - 1;
+    bool deferred = false;
     for (int t = 0; t < m; ++t, --site) {
       const int p = 2 * rprev;
+      if (defer && p > pmax) {
+        defer_instance(defer, inst);
+        deferred = true;
+        break;
+      }
       cd* G = core_ptr(base, core_stride, site);
       if (q == 1) {
         // top of the block: the carry itself is the core (1, 2, rprev)
@@ -208,7 +232,7 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
         __syncthreads();
         break;
       }
-      TsSvd sv = ts_svd(Z, q, p, p, sm.W, SVD_WCAP(hb), sm.V, sm.sig, sm.tau, sm.flag);
+      TsSvd sv = ts_svd(Z, q, p, p, sm.W, wcap, sm.V, sm.sig, sm.tau, sm.flag);
       if (sv.sweeps < 0) st = SFFT_ENOCONV_DEV;
       if (t == 0) {
         double s2 = 0.0;
@@ -238,6 +262,7 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
       q >>= 1;
       rprev = k;
     }
+    if (deferred) continue;
     // sites above the block
     for (int s = 0; s < n - m; ++s) {
       cd* G = core_ptr(base, core_stride, s);
@@ -548,7 +573,8 @@ __global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count,
                            cd* tt, const long long* tt_off, int core_stride,
                            int* ranks_all, cd* scratch,
                            long long scratch_stride, int* status, int hb,
-                           double* acc, int phase, int pmax, int vcap) {
+                           double* acc, int phase, int pmax, int vcap, int* defer,
+                           const int* dcount) {
   // shared memory sized by the launch: panels of at most pmax columns, Q
   // blocks of vcap elements (see round_smem_bytes on the host)
   extern __shared__ double4 smem_raw[];
@@ -557,8 +583,9 @@ __global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count,
   // ranks of the instance in flight: thread 0 updates them between barriers,
   // every thread reads them, so they live in shared memory
   __shared__ int r[SFFT_MAXN_DEV + 1];
+  const int count_ = dcount ? *dcount : count;
   double fl = 0.0;
-  WORK_LOOP_BEGIN(list, count, counter)
+  WORK_LOOP_BEGIN(list, count_, counter)
     const int n = n_arr[inst];
     const double tol = tol_arr[inst];
     const int rmax = maxrank_arr[inst];
@@ -570,6 +597,15 @@ __global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count,
     cd* tmp = scratch + (size_t)blockIdx.x * scratch_stride;
     int st = 0;
     if (status && status[inst] != 0) continue;
+    if (defer) {
+      // ranks never grow here, so the input ranks decide whether the carve fits
+      int mr = 0;
+      for (int i = 0; i <= n; ++i) mr = max(mr, r[i]);
+      if (mr > pmax) {
+        defer_instance(defer, inst);
+        continue;
+      }
+    }
     if (left_orth) {
       for (int s = 0; s + 1 < n; ++s) {
         const int r0 = r[s], r1 = r[s + 1], r2 = r[s + 2];
