@@ -471,6 +471,9 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   ctr = reinterpret_cast<int*>(p);
   CK(cudaMemsetAsync(ctr, 0, sizeof(int) * 16, ctx->stream));
   b.all_list = all_dev;
+  // work-queue counters, one per launch of a step: 0 TT-SVD builder (tier 1),
+  // 1 cross builder, 2 rounding of the cross output, 3 zip-up, 4 output
+  // rounding (tier 1), 5 readout, 7 builder tier 2, 8 rounding tier 2
   b.counters = ctr;
   const size_t smem = svd_smem();
   // hand-off lists of the two-tier launches: [count, instances...]
@@ -500,7 +503,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     CK(cudaGetLastError());
     PhaseScope ps(ctx, PH_BUILD);
     k_integrand_ttsvd<<<grid2, kThreads, smem, ctx->stream>>>(
-        b.P, m_dev, defer_build + 1, 0, ctr + 5, reinterpret_cast<cd*>(p), sstride, b.A, b.a_off,
+        b.P, m_dev, defer_build + 1, 0, ctr + 7, reinterpret_cast<cd*>(p), sstride, b.A, b.a_off,
         SFFT_CORE_STRIDE_D2, b.a_ranks, b.status, kHb, acc_ptr(ctx), LA_MAXP, nullptr, defer_build);
   }
   CK(cudaGetLastError());
@@ -570,7 +573,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   {
     PhaseScope ps(ctx, PH_ROUND);
     k_tt_round<<<grid2, kThreads, rs2.bytes, ctx->stream>>>(
-        defer_round + 1, 0, ctr + 6, b.n_arr, 2, 0, b.tol_arr, b.maxr_arr, b.B, b.a_off, SFFT_CORE_STRIDE_D2,
+        defer_round + 1, 0, ctr + 8, b.n_arr, 2, 0, b.tol_arr, b.maxr_arr, b.B, b.a_off, SFFT_CORE_STRIDE_D2,
         b.b_ranks, reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH, b.status, rs2.hb, acc_ptr(ctx), PH_ROUND,
         rs2.pmax, rs2.vcap, nullptr, defer_round);
   }
