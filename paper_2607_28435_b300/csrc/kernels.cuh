@@ -57,11 +57,12 @@ struct RoundSmem {
 };
 // Shared memory of k_zipup: 8-row panel blocks at 64 columns and a
 // 64 x (rank cap + 1) basis block, small enough for two CTAs per SM.
-inline RoundSmem zip_smem() {
+inline RoundSmem zip_smem(bool small = false) {
+  // small: W only (70 x 64, Q behind T), three CTAs per SM at 128 threads
   RoundSmem r;
   r.pmax = LA_MAXP;
-  r.hb = 8;
-  r.vcap = LA_MAXP * (SFFT_SLOT_RANK_DEV + 1);
+  r.hb = small ? 6 : 8;
+  r.vcap = small ? 1 : LA_MAXP * (SFFT_SLOT_RANK_DEV + 1);
   r.bytes = sizeof(cd) * ((size_t)(r.pmax + r.hb) * r.pmax + r.vcap + r.pmax) + sizeof(double) * r.pmax + 320;
   return r;
 }
@@ -83,7 +84,8 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
                         const cd* Wmpo, const long long* w_off, const int* w_ranks_all, cd* B,
                         const long long* b_off, int* b_ranks_all, int core_stride_a,
                         int core_stride_w, int core_stride_b, cd* scratch,
-                        long long scratch_stride, int* status, int hb, double* acc);
+                        long long scratch_stride, int* status, int hb, double* acc, int vcap, int* defer,
+                        const int* dcount);
 __global__ void k_readout(const int* list, int count, int* counter, const InstParams* P,
                           const cd* B, const long long* b_off,
                           const int* b_ranks_all, int core_stride, const long long* l_begin,

@@ -473,7 +473,8 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   b.all_list = all_dev;
   // work-queue counters, one per launch of a step: 0 TT-SVD builder (tier 1),
   // 1 cross builder, 2 rounding of the cross output, 3 zip-up, 4 output
-  // rounding (tier 1), 5 readout, 7 builder tier 2, 8 rounding tier 2
+  // rounding (tier 1), 5 readout, 7 builder tier 2, 8 rounding tier 2,
+  // 9 zip-up tier 2
   b.counters = ctr;
   const size_t smem = svd_smem();
   // hand-off lists of the two-tier launches: [count, instances...]
@@ -543,16 +544,34 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   if ((s = upload(ctx, "w_off", w_off, &b.w_off))) return s;
   CK(cudaMemcpyAsync(b.w_ranks, w_ranks.data(), sizeof(int) * w_ranks.size(), cudaMemcpyHostToDevice,
                      ctx->stream));
+  // tier 1: W-only carve, 128-thread CTAs; tier 2: the full carve for the
+  // instances whose panels (with their explicit Q) outgrow it
+  int* defer_zip;
+  if ((s = ensure(ctx, "defer_zip", sizeof(int) * (cnt + 1), &p))) return s;
+  defer_zip = reinterpret_cast<int*>(p);
+  CK(cudaMemsetAsync(defer_zip, 0, sizeof(int), ctx->stream));
+  const RoundSmem zs1 = zip_smem(true);
   const RoundSmem zs = zip_smem();
-  int grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, zs.bytes));
-  if ((s = ensure(ctx, "zip_scratch", sizeof(cd) * (size_t)SFFT_ZIP_SCRATCH * grid, &p))) return s;
+  const int zg1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, zs1.bytes, kThreadsSmall));
+  const int zg2 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, zs.bytes));
+  if ((s = ensure(ctx, "zip_scratch", sizeof(cd) * (size_t)SFFT_ZIP_SCRATCH * std::max(zg1, zg2), &p)))
+    return s;
   {
     PhaseScope ps(ctx, PH_ZIPUP);
-    k_zipup<<<grid, kThreads, zs.bytes, ctx->stream>>>(
+    k_zipup<<<zg1, kThreadsSmall, zs1.bytes, ctx->stream>>>(
         all_dev, cnt, ctr + 3, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
         reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
         SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
-        SFFT_ZIP_SCRATCH, b.status, zs.hb, acc_ptr(ctx));
+        SFFT_ZIP_SCRATCH, b.status, zs1.hb, acc_ptr(ctx), zs1.vcap, defer_zip, nullptr);
+  }
+  CK(cudaGetLastError());
+  {
+    PhaseScope ps(ctx, PH_ZIPUP);
+    k_zipup<<<zg2, kThreads, zs.bytes, ctx->stream>>>(
+        defer_zip + 1, 0, ctr + 9, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
+        reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
+        SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
+        SFFT_ZIP_SCRATCH, b.status, zs.hb, acc_ptr(ctx), zs.vcap, nullptr, defer_zip);
   }
   CK(cudaGetLastError());
   // tier 1: ranks up to kSmallRoundR in 128-thread CTAs; tier 2: the rest
@@ -901,7 +920,7 @@ sfft_status sfft_tt_apply_qft(sfft_ctx* ctx, int32_t n, const int32_t* in_ranks,
       nullptr, 1, nullptr, nd, td, md, A, od, reinterpret_cast<int*>(ra), reinterpret_cast<const cd*>(ctx->mpo_pool.p), wd,
       reinterpret_cast<int*>(rw), B, od, reinterpret_cast<int*>(rb), SFFT_CORE_STRIDE_D2,
       SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(scr), SFFT_ZIP_SCRATCH, sd, zs.hb,
-      nullptr);
+      nullptr, zs.vcap, nullptr, nullptr);
   CK(cudaGetLastError());
   const RoundSmem rs = round_smem(2, false);
   k_tt_round<<<1, kThreads, rs.bytes, ctx->stream>>>(nullptr, 1, nullptr, nd, 2, 0, td, md, B, od,

@@ -732,15 +732,20 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
                         const long long* b_off, int* b_ranks_all,
                         int core_stride_a, int core_stride_w, int core_stride_b,
                         cd* scratch, long long scratch_stride,
-                        int* status, int hb, double* acc) {
-  // shared memory: W for row blocks of the panel ((LA_MAXP + hb) x LA_MAXP),
-  // V for the p x (rank + 1) block of the basis step (see zip_smem on the host)
+                        int* status, int hb, double* acc, int vcap, int* defer, const int* dcount) {
+  // shared memory: W ((LA_MAXP + hb) x LA_MAXP) for the panel T and, behind
+  // it when there is room, the explicit Q; V (vcap elements) for Q otherwise
+  // and for the streaming fallback. A launch without V (vcap <= 1) hands the
+  // instances that need it to the full-size launch (defer).
   extern __shared__ double4 smem_raw[];
-  SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb, LA_MAXP * (SFFT_SLOT_RANK_DEV + 1));
+  SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb, vcap);
+  const int wcap = (LA_MAXP + hb) * LA_MAXP;
+  const bool has_v = vcap > 1;
   __shared__ int zperm[LA_MAXQ];
   __shared__ double zcn[LA_MAXQ];
+  const int count_ = dcount ? *dcount : count;
   double fl = 0.0;
-  WORK_LOOP_BEGIN(list, count, counter)
+  WORK_LOOP_BEGIN(list, count_, counter)
     const int n = n_arr[inst];
     const double ztol = tol_arr[inst] / sqrt((double)max(n - 1, 1));
     const int rmax = maxrank_arr[inst];
@@ -762,8 +767,19 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
     }
     __syncthreads();
     int rc = 1;
+    bool deferred = false;
     for (int s = 0; s < n; ++s) {
       const int rA0 = ra[s], rA1 = ra[s + 1], s0 = rw[s], s1 = rw[s + 1];
+      {
+        // does this site fit the launch's carve? (uniform over the CTA)
+        const int q = s1 * rA1, p = 2 * rc;
+        const bool fits = q <= LA_MAXQ && p * (q + min(p, q)) <= wcap;
+        if (defer && !fits && s < n - 1) {
+          defer_instance(defer, inst);
+          deferred = true;
+          break;
+        }
+      }
       const cd* As = Ab + (size_t)s * core_stride_a;
       const cd* Ws = Wb + (size_t)s * core_stride_w;
       // Dt
@@ -782,7 +798,9 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
       const int q = s1 * rA1, p = 2 * rc;
       // T = Z^H (p x q, column-major) goes straight to shared memory when it
       // fits: Z's row-major buffer and T's column-major one share the index
-      const bool direct = q <= LA_MAXQ && p * q <= SVD_WCAP(hb);
+      const bool direct = q <= LA_MAXQ && p * q <= wcap && (has_v || p * (q + min(p, q)) <= wcap);
+      // the explicit Q goes behind T in W when it fits there, else into V
+      cd* Qd = (p * (q + min(p, q)) <= wcap) ? sm.W + (size_t)p * q : sm.V;
       for (int idx = threadIdx.x; idx < q * p; idx += blockDim.x) {
         const int row = idx / p, col = idx - row * p;
         const int ap = row / rA1, bp = row - ap * rA1;
@@ -813,7 +831,7 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
       if (direct) {
         // column-pivoted QR of T: B = Q[:, :k] is the output core and the
         // next carry is CH = Z B = (R[:k] P^T)^H, read from R
-        const RowBasis rbz = colpiv_basis(sm.W, p, q, sm.V, ztol, SFFT_SLOT_RANK_DEV + 1, sm.tau, zcn, zperm);
+        const RowBasis rbz = colpiv_basis(sm.W, p, q, Qd, ztol, SFFT_SLOT_RANK_DEV + 1, sm.tau, zcn, zperm);
         int k = rbz.k;
         if (k > SFFT_SLOT_RANK_DEV) {
           st = SFFT_ERANK_DEV;
@@ -821,7 +839,7 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
         }
         for (int idx = threadIdx.x; idx < p * k; idx += blockDim.x) {
           const int row = idx / k, cc = idx - row * k;
-          Bs[idx] = sm.V[(size_t)cc * p + row];
+          Bs[idx] = Qd[(size_t)cc * p + row];
         }
         for (int idx = threadIdx.x; idx < q * k; idx += blockDim.x) {
           const int i = idx / k, c = idx - i * k;
@@ -835,7 +853,7 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
       }
       // otherwise: rank-revealing QR of the panel in global memory gives the
       // kept left subspace of T, and the carry is the product Z B
-      const RowBasis rbz = rrqr_basis(Z, q, p, p, sm.W, SVD_WCAP(hb), sm.V, ztol, SFFT_SLOT_RANK_DEV + 1,
+      const RowBasis rbz = rrqr_basis(Z, q, p, p, sm.W, wcap, sm.V, ztol, SFFT_SLOT_RANK_DEV + 1,
                                       sm.tau, zcn, zperm);
       int k = rbz.k;
       if (k > SFFT_SLOT_RANK_DEV) {
@@ -854,6 +872,7 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
       fl += rbz.flops + flops_gemm(q, p, k);
       rc = k;
     }
+    if (deferred) continue;
     if (threadIdx.x == 0) status[inst] = max(status[inst], st);
     __syncthreads();
   WORK_LOOP_END
