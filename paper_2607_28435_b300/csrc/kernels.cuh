@@ -58,7 +58,8 @@ struct RoundSmem {
 // Shared memory of k_zipup: 8-row panel blocks at 64 columns and a
 // 64 x (rank cap + 1) basis block, small enough for two CTAs per SM.
 inline RoundSmem zip_smem(bool small = false) {
-  // small: W only (70 x 64, Q behind T), three CTAs per SM at 128 threads
+  // small: W only (70 x 64; the explicit Q is formed in T's spent columns),
+  // three CTAs per SM at 128 threads
   RoundSmem r;
   r.pmax = LA_MAXP;
   r.hb = small ? 6 : 8;

@@ -771,18 +771,4 @@ static __device__ RowBasis rrqr_basis(const cd* Z, long long q, int p, int ldz, 
   return out;
 }
 
-// Dominant column space of T (p x q, column-major with leading dim p, placed
-// in W by the caller; q <= LA_MAXQ): T P = Q R by pivqr_trunc, and
-// B = Q[:, :k] (p x k, column-major, leading dim p) into V. Then
-// ||T - B B^H T||_F = ||R[k:, k:]||_F <= delta_rel ||T||_F, and
-// B^H T = R[:k, :] P^T exactly, which the caller reads from W: pivoted column
-// i of R (original column perm[i]) has rows 0..min(i, k-1) in W[i * p + ...].
-static __device__ RowBasis colpiv_basis(cd* W, int p, int q, cd* V, double delta_rel, int kmax, cd* taus,
-                                        double* cn, int* perm) {
-  RowBasis out = pivqr_trunc(W, p, p, q, delta_rel, kmax, taus, cn, perm);
-  form_q(W, p, p, out.k, taus, V, p);
-  out.flops += flops_formq(p, out.k);
-  return out;
-}
-
 }  // namespace la

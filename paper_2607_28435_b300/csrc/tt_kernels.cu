@@ -733,10 +733,10 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
                         int core_stride_a, int core_stride_w, int core_stride_b,
                         cd* scratch, long long scratch_stride,
                         int* status, int hb, double* acc, int vcap, int* defer, const int* dcount) {
-  // shared memory: W ((LA_MAXP + hb) x LA_MAXP) for the panel T and, behind
-  // it when there is room, the explicit Q; V (vcap elements) for Q otherwise
-  // and for the streaming fallback. A launch without V (vcap <= 1) hands the
-  // instances that need it to the full-size launch (defer).
+  // shared memory: W ((LA_MAXP + hb) x LA_MAXP) for the panel T and, in its
+  // spent columns, the explicit Q; V (vcap elements) for the streaming
+  // fallback of panels larger than W. A launch without V (vcap <= 1) hands
+  // the instances that need it to the full-size launch (defer).
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb, vcap);
   const int wcap = (LA_MAXP + hb) * LA_MAXP;
@@ -773,7 +773,7 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
       {
         // does this site fit the launch's carve? (uniform over the CTA)
         const int q = s1 * rA1, p = 2 * rc;
-        const bool fits = q <= LA_MAXQ && p * (q + min(p, q)) <= wcap;
+        const bool fits = q <= LA_MAXQ && p * q <= wcap;
         if (defer && !fits && s < n - 1) {
           defer_instance(defer, inst);
           deferred = true;
@@ -798,9 +798,7 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
       const int q = s1 * rA1, p = 2 * rc;
       // T = Z^H (p x q, column-major) goes straight to shared memory when it
       // fits: Z's row-major buffer and T's column-major one share the index
-      const bool direct = q <= LA_MAXQ && p * q <= wcap && (has_v || p * (q + min(p, q)) <= wcap);
-      // the explicit Q goes behind T in W when it fits there, else into V
-      cd* Qd = (p * (q + min(p, q)) <= wcap) ? sm.W + (size_t)p * q : sm.V;
+      const bool direct = q <= LA_MAXQ && p * q <= wcap;
       for (int idx = threadIdx.x; idx < q * p; idx += blockDim.x) {
         const int row = idx / p, col = idx - row * p;
         const int ap = row / rA1, bp = row - ap * rA1;
@@ -829,25 +827,36 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
         break;
       }
       if (direct) {
-        // column-pivoted QR of T: B = Q[:, :k] is the output core and the
-        // next carry is CH = Z B = (R[:k] P^T)^H, read from R
-        const RowBasis rbz = colpiv_basis(sm.W, p, q, Qd, ztol, SFFT_SLOT_RANK_DEV + 1, sm.tau, zcn, zperm);
+        // column-pivoted QR of T stopped at the truncation rank k: the next
+        // carry is CH = Z B = (R[:k] P^T)^H, read from R first; then T's
+        // columns k.. are free and the explicit Q = B (the output core) is
+        // formed there, behind the reflectors (else in V)
+        const RowBasis rbz = pivqr_trunc(sm.W, p, p, q, ztol, SFFT_SLOT_RANK_DEV + 1, sm.tau, zcn, zperm);
         int k = rbz.k;
         if (k > SFFT_SLOT_RANK_DEV) {
           st = SFFT_ERANK_DEV;
           k = SFFT_SLOT_RANK_DEV;
         }
-        for (int idx = threadIdx.x; idx < p * k; idx += blockDim.x) {
-          const int row = idx / k, cc = idx - row * k;
-          Bs[idx] = Qd[(size_t)cc * p + row];
-        }
         for (int idx = threadIdx.x; idx < q * k; idx += blockDim.x) {
           const int i = idx / k, c = idx - i * k;
           CH[(size_t)zperm[i] * k + c] = (c <= i) ? cconj(sm.W[(size_t)i * p + c]) : mkc(0.0, 0.0);
         }
+        __syncthreads();
+        // 2 k p <= 2 * 33 * 64 fits the smallest carve (70 x 64); V backs it up
+        cd* Qd = (2 * k * p <= wcap) ? sm.W + (size_t)p * k : (has_v ? sm.V : nullptr);
+        if (!Qd) {
+          defer_instance(defer, inst);
+          deferred = true;
+          break;
+        }
+        form_q(sm.W, p, p, k, sm.tau, Qd, p);
+        for (int idx = threadIdx.x; idx < p * k; idx += blockDim.x) {
+          const int row = idx / k, cc = idx - row * k;
+          Bs[idx] = Qd[(size_t)cc * p + row];
+        }
         if (threadIdx.x == 0) rb[s + 1] = k;
         __syncthreads();
-        fl += rbz.flops;
+        fl += rbz.flops + flops_formq(p, k);
         rc = k;
         continue;
       }
