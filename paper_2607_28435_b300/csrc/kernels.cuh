@@ -59,7 +59,7 @@ struct RoundSmem {
 // 64 x (rank cap + 1) basis block, small enough for two CTAs per SM.
 inline RoundSmem zip_smem(bool small = false) {
   // small: W only (70 x 64; the explicit Q is formed in T's spent columns),
-  // three CTAs per SM at 128 threads
+  // three CTAs per SM (with the kernel's 85-register bound)
   RoundSmem r;
   r.pmax = LA_MAXP;
   r.hb = small ? 6 : 8;

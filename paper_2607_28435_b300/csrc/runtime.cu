@@ -544,7 +544,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   if ((s = upload(ctx, "w_off", w_off, &b.w_off))) return s;
   CK(cudaMemcpyAsync(b.w_ranks, w_ranks.data(), sizeof(int) * w_ranks.size(), cudaMemcpyHostToDevice,
                      ctx->stream));
-  // tier 1: W-only carve, 128-thread CTAs; tier 2: the full carve for the
+  // tier 1: W-only carve, three CTAs per SM; tier 2: the full carve for the
   // instances whose panels (with their explicit Q) outgrow it
   int* defer_zip;
   if ((s = ensure(ctx, "defer_zip", sizeof(int) * (cnt + 1), &p))) return s;
@@ -552,13 +552,13 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   CK(cudaMemsetAsync(defer_zip, 0, sizeof(int), ctx->stream));
   const RoundSmem zs1 = zip_smem(true);
   const RoundSmem zs = zip_smem();
-  const int zg1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, zs1.bytes, kThreadsSmall));
+  const int zg1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, zs1.bytes));
   const int zg2 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, zs.bytes));
   if ((s = ensure(ctx, "zip_scratch", sizeof(cd) * (size_t)SFFT_ZIP_SCRATCH * std::max(zg1, zg2), &p)))
     return s;
   {
     PhaseScope ps(ctx, PH_ZIPUP);
-    k_zipup<<<zg1, kThreadsSmall, zs1.bytes, ctx->stream>>>(
+    k_zipup<<<zg1, kThreads, zs1.bytes, ctx->stream>>>(
         all_dev, cnt, ctr + 3, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
         reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
         SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),

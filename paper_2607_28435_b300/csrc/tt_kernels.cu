@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count,
 // vectors V of Z are the left singular vectors of T: V becomes the output core
 // B_s[c][mu][c''] and Z V = T^H V the next carry CH. Singular values below
 // ztol * ||T|| are dropped; the final rounding sweep sets the ranks.
-__global__ void k_zipup(const int* list, int count, int* counter, const int* n_arr, const double* tol_arr,
+__global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, int* counter, const int* n_arr, const double* tol_arr,
                         const int* maxrank_arr, const cd* A,
                         const long long* a_off, const int* a_ranks_all,
                         const cd* Wmpo, const long long* w_off,
