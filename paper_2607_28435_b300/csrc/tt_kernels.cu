@@ -771,9 +771,9 @@ __global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, in
     for (int s = 0; s < n; ++s) {
       const int rA0 = ra[s], rA1 = ra[s + 1], s0 = rw[s], s1 = rw[s + 1];
       {
-        // does this site fit the launch's carve? (uniform over the CTA)
-        const int q = s1 * rA1, p = 2 * rc;
-        const bool fits = q <= LA_MAXQ && p * q <= wcap;
+        // a launch without V handles panels of up to LA_MAXQ columns (in W,
+        // or in global scratch when larger); the rest go on (uniform over the CTA)
+        const bool fits = s1 * rA1 <= LA_MAXQ;
         if (defer && !fits && s < n - 1) {
           defer_instance(defer, inst);
           deferred = true;
@@ -799,6 +799,10 @@ __global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, in
       // T = Z^H (p x q, column-major) goes straight to shared memory when it
       // fits: Z's row-major buffer and T's column-major one share the index
       const bool direct = q <= LA_MAXQ && p * q <= wcap;
+      // without V, a panel larger than W is factored in place in the CTA's
+      // global scratch instead (same steps, L2-resident)
+      const bool gdirect = !direct && !has_v && q <= LA_MAXQ;
+      cd* Tp = direct ? sm.W : Z;
       for (int idx = threadIdx.x; idx < q * p; idx += blockDim.x) {
         const int row = idx / p, col = idx - row * p;
         const int ap = row / rA1, bp = row - ap * rA1;
@@ -815,23 +819,24 @@ __global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, in
         if (direct)
           sm.W[idx] = cconj(acc);
         else
-          Z[idx] = acc;
+          Z[idx] = gdirect ? cconj(acc) : acc;
       }
       __syncthreads();
       fl += flops_gemm(nd, rA0, 1) + flops_gemm((long long)q * p, 2 * s0, 1);
       cd* Bs = Bb + (size_t)s * core_stride_b;
       if (s == n - 1) {
         // q == 1: B[c][mu][0] = conj(Z[0, (c, mu)])
-        for (int idx = threadIdx.x; idx < p; idx += blockDim.x) Bs[idx] = direct ? sm.W[idx] : cconj(Z[idx]);
+        for (int idx = threadIdx.x; idx < p; idx += blockDim.x)
+          Bs[idx] = direct ? sm.W[idx] : (gdirect ? Z[idx] : cconj(Z[idx]));
         __syncthreads();
         break;
       }
-      if (direct) {
+      if (direct || gdirect) {
         // column-pivoted QR of T stopped at the truncation rank k: the next
         // carry is CH = Z B = (R[:k] P^T)^H, read from R first; then T's
         // columns k.. are free and the explicit Q = B (the output core) is
         // formed there, behind the reflectors (else in V)
-        const RowBasis rbz = pivqr_trunc(sm.W, p, p, q, ztol, SFFT_SLOT_RANK_DEV + 1, sm.tau, zcn, zperm);
+        const RowBasis rbz = pivqr_trunc(Tp, p, p, q, ztol, SFFT_SLOT_RANK_DEV + 1, sm.tau, zcn, zperm);
         int k = rbz.k;
         if (k > SFFT_SLOT_RANK_DEV) {
           st = SFFT_ERANK_DEV;
@@ -839,17 +844,18 @@ __global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, in
         }
         for (int idx = threadIdx.x; idx < q * k; idx += blockDim.x) {
           const int i = idx / k, c = idx - i * k;
-          CH[(size_t)zperm[i] * k + c] = (c <= i) ? cconj(sm.W[(size_t)i * p + c]) : mkc(0.0, 0.0);
+          CH[(size_t)zperm[i] * k + c] = (c <= i) ? cconj(Tp[(size_t)i * p + c]) : mkc(0.0, 0.0);
         }
         __syncthreads();
-        // 2 k p <= 2 * 33 * 64 fits the smallest carve (70 x 64); V backs it up
-        cd* Qd = (2 * k * p <= wcap) ? sm.W + (size_t)p * k : (has_v ? sm.V : nullptr);
+        // 2 k p <= 2 * 33 * 64 fits the smallest carve (70 x 64); V backs it
+        // up; a panel in global memory leaves all of W to Q
+        cd* Qd = gdirect ? sm.W : (2 * k * p <= wcap) ? sm.W + (size_t)p * k : (has_v ? sm.V : nullptr);
         if (!Qd) {
           defer_instance(defer, inst);
           deferred = true;
           break;
         }
-        form_q(sm.W, p, p, k, sm.tau, Qd, p);
+        form_q(Tp, p, p, k, sm.tau, Qd, p);
         for (int idx = threadIdx.x; idx < p * k; idx += blockDim.x) {
           const int row = idx / k, cc = idx - row * k;
           Bs[idx] = Qd[(size_t)cc * p + row];
