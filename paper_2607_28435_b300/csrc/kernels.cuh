@@ -40,7 +40,8 @@ __global__ void k_integrand_ttsvd(const InstParams* P, const int* m_arr, const i
 __global__ void k_integrand_cross(const InstParams* P, const int* list, int count, int* counter,
                                   cd* scratch, long long scratch_stride, cd* tt,
                                   const long long* tt_off, int core_stride, int* ranks_all,
-                                  int* status, int hb, double* acc, int max_sweeps);
+                                  int* status, int hb, double* acc, int max_sweeps, int pmax,
+                                  int rcap, int* defer, const int* dcount);
 __global__ void k_mpo_interp(int n, int P, cd* W, int core_stride, int* ranks);
 __global__ void k_tt_round(const int* list, int count, int* counter, const int* n_arr, int d,
                            int left_orth, const double* tol_arr,

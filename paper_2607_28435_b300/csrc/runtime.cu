@@ -31,6 +31,11 @@ const int kThreads = 256;
 const int kThreadsSmall = 128;
 const int kSmallP = 32;
 const int kSmallRoundR = 24;
+// Cross tier 1: ranks up to 16, so supercores of 32 x 32 and the assembly's
+// maxvol work (2 N r + 2 r^2 + N = 1568 for N = 32, r = 16) fit W = (32 + 17) x 32.
+const int kCrossSmallR = 16;
+const int kCrossSmallHb = 17;
+const int CROSS_RANK_CAP = SFFT_SLOT_RANK_DEV;
 const int kHb = 36;  // row-block height reserved next to the 64-column panel
 const int kSvdMaxBits = 14;  // support blocks up to 2^14 points: TT-SVD; wider: cross
 const int kCrossSweeps = 6;
@@ -474,7 +479,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   // work-queue counters, one per launch of a step: 0 TT-SVD builder (tier 1),
   // 1 cross builder, 2 rounding of the cross output, 3 zip-up, 4 output
   // rounding (tier 1), 5 readout, 7 builder tier 2, 8 rounding tier 2,
-  // 9 zip-up tier 2
+  // 9 zip-up tier 2, 10 cross tier 2
   b.counters = ctr;
   const size_t smem = svd_smem();
   // hand-off lists of the two-tier launches: [count, instances...]
@@ -509,14 +514,32 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   }
   CK(cudaGetLastError());
   if (!cross_list.empty()) {
+    // tier 1: ranks up to kCrossSmallR (panels of 2 kCrossSmallR columns),
+    // 128-thread CTAs, every instance in flight at once; tier 2: the rest
     const int ncr = (int)cross_list.size();
+    int* defer_cross;
+    if ((s = ensure(ctx, "defer_cross", sizeof(int) * (ncr + 1), &p))) return s;
+    defer_cross = reinterpret_cast<int*>(p);
+    CK(cudaMemsetAsync(defer_cross, 0, sizeof(int), ctx->stream));
+    const int xp = 2 * kCrossSmallR;
+    const int xhb = kCrossSmallHb;
+    const size_t smem1 = la::ts_svd_smem_bytes(xp, xhb) + 256;
+    const int grid1 = std::min(ncr, ctx->num_sms * blocks_per_sm((const void*)k_integrand_cross, smem1,
+                                                                 kThreadsSmall));
     const int grid = std::min(ncr, ctx->num_sms * blocks_per_sm((const void*)k_integrand_cross, smem));
-    if ((s = ensure(ctx, "cross_scratch", sizeof(cd) * (size_t)4096 * grid, &p))) return s;
+    if ((s = ensure(ctx, "cross_scratch", sizeof(cd) * (size_t)4096 * std::max(grid1, grid), &p))) return s;
+    {
+      PhaseScope ps(ctx, PH_CROSS);
+      k_integrand_cross<<<grid1, kThreadsSmall, smem1, ctx->stream>>>(
+          b.P, cross_dev, ncr, ctr + 1, reinterpret_cast<cd*>(p), 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
+          b.a_ranks, b.status, xhb, acc_ptr(ctx), kCrossSweeps, xp, kCrossSmallR, defer_cross, nullptr);
+    }
+    CK(cudaGetLastError());
     {
       PhaseScope ps(ctx, PH_CROSS);
       k_integrand_cross<<<grid, kThreads, smem, ctx->stream>>>(
-          b.P, cross_dev, ncr, ctr + 1, reinterpret_cast<cd*>(p), 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
-          b.a_ranks, b.status, kHb, acc_ptr(ctx), kCrossSweeps);
+          b.P, defer_cross + 1, 0, ctr + 10, reinterpret_cast<cd*>(p), 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
+          b.a_ranks, b.status, kHb, acc_ptr(ctx), kCrossSweeps, LA_MAXP, CROSS_RANK_CAP, nullptr, defer_cross);
     }
     CK(cudaGetLastError());
     // interpolatory cores -> right-orthonormal, truncated to tol

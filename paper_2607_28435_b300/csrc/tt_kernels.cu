@@ -305,11 +305,12 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
 // Oseledets 2011). Rounding afterwards makes the cores right-orthonormal.
 // Index choice of a cross step: the k columns of Z (q x p) picked by a
 // column-pivoted QR truncated at ctol (the greedy maximum-volume column
-// subset, as in Q-DEIM), k capped at rmax; returns k, the columns in piv.
+// subset, as in Q-DEIM), k capped at rmax; returns k, the columns in piv, and
+// sets *over when the rank wanted more than rmax columns.
 // Pivoting Z and pivoting R of Z = Q R choose the same columns, so the rank
 // is the one a rank-revealing QR of the supercore gives.
 __device__ int dominant_basis(const cd* Z, int q, int p, SvdSmem& sm, int hb, double ctol, int rmax,
-                              int* piv, int* iw, double* red_d, int* red_i, int* st, double* fl) {
+                              int* piv, int* iw, double* red_d, int* red_i, bool* over, double* fl) {
   __shared__ int perm_[LA_MAXP];
   (void)hb;
   (void)iw;
@@ -323,10 +324,8 @@ __device__ int dominant_basis(const cd* Z, int q, int p, SvdSmem& sm, int hb, do
   __syncthreads();
   const RowBasis rb = pivqr_trunc(sm.W, q, q, p, ctol, rmax + 1, sm.tau, sm.sig, perm_);
   int k = rb.k;
-  if (k > rmax) {
-    *st = SFFT_ERANK_DEV;
-    k = rmax;
-  }
+  *over = k > rmax;
+  if (k > rmax) k = rmax;
   for (int c = threadIdx.x; c < k; c += blockDim.x) piv[c] = perm_[c];
   __syncthreads();
   *fl += rb.flops;
@@ -355,9 +354,13 @@ __device__ __forceinline__ long long cross_seed(int t, int L) {
 __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* list, int count,
                                   int* counter, cd* scratch, long long scratch_stride, cd* tt,
                                   const long long* tt_off, int core_stride, int* ranks_all,
-                                  int* status, int hb, double* acc, int max_sweeps) {
+                                  int* status, int hb, double* acc, int max_sweeps, int pmax,
+                                  int rcap, int* defer, const int* dcount) {
+  // panels of at most pmax columns (carve sized by the launch); with defer
+  // set, ranks are capped at rcap and an instance that needs more goes to the
+  // full-size launch before anything of it is written
   extern __shared__ double4 smem_raw[];
-  SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb);
+  SvdSmem sm = carve_svd_smem(smem_raw, pmax, hb);
   __shared__ long long Iset[(SFFT_MAXN_DEV + 1) * CROSS_R];
   __shared__ long long Jset[(SFFT_MAXN_DEV + 1) * CROSS_R];
   __shared__ int rk[SFFT_MAXN_DEV + 1];
@@ -368,10 +371,13 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
   __shared__ int red_i[32];
   double fl = 0.0, evals = 0.0;
   cd* Z = scratch + (size_t)blockIdx.x * scratch_stride;
-  WORK_LOOP_BEGIN(list, count, counter)
+  const int count_ = dcount ? *dcount : count;
+  WORK_LOOP_BEGIN(list, count_, counter)
     const InstParams prm = P[inst];
     const int n = prm.n;
-    const int rmax = min(prm.max_rank, CROSS_R);
+    const int rmax_i = min(prm.max_rank, CROSS_R);
+    const int rmax = defer ? min(rmax_i, rcap) : rmax_i;
+    bool hand_off = false;
     const double ctol = 0.01 * prm.tol;
     int st = 0;
     cd* base = tt + tt_off[inst];
@@ -403,12 +409,21 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
         }
         __syncthreads();
         evals += (double)p * q;
-        int k = dominant_basis(Z, q, p, sm, hb, ctol, rmax, piv, iw, red_d, red_i, &st, &fl);
+        bool over;
+        int k = dominant_basis(Z, q, p, sm, hb, ctol, rmax, piv, iw, red_d, red_i, &over, &fl);
+        if (over) {
+          if (rmax < rmax_i) {
+            hand_off = true;
+            break;
+          }
+          st = SFFT_ERANK_DEV;
+        }
         for (int c = threadIdx.x; c < k; c += blockDim.x)
           Iset[b * CROSS_R + c] = (Iset[(b - 1) * CROSS_R + (piv[c] >> 1)] << 1) | (piv[c] & 1);
         if (threadIdx.x == 0) rk[b] = k;
         __syncthreads();
       }
+      if (hand_off) break;
       // ---- right to left: choose J[b]
       for (int b = n - 1; b >= 1; --b) {
         const int rl = rk[b - 1], rr = rk[b + 1];
@@ -422,7 +437,15 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
         }
         __syncthreads();
         evals += (double)p * q;
-        int k = dominant_basis(Z, q, p, sm, hb, ctol, rmax, piv, iw, red_d, red_i, &st, &fl);
+        bool over;
+        int k = dominant_basis(Z, q, p, sm, hb, ctol, rmax, piv, iw, red_d, red_i, &over, &fl);
+        if (over) {
+          if (rmax < rmax_i) {
+            hand_off = true;
+            break;
+          }
+          st = SFFT_ERANK_DEV;
+        }
         for (int c = threadIdx.x; c < k; c += blockDim.x) {
           const int l2 = piv[c] / rr, t = piv[c] - l2 * rr;
           Jset[b * CROSS_R + c] = ((long long)l2 << sh) | Jset[(b + 1) * CROSS_R + t];
@@ -430,6 +453,7 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
         if (threadIdx.x == 0) rk[b] = k;
         __syncthreads();
       }
+      if (hand_off) break;
       // converged when the ranks repeat
       int same = 1;
       for (int b = 0; b <= n; ++b) same &= (rk[b] == rprev[b]);
@@ -437,6 +461,10 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
       for (int b = threadIdx.x; b <= n; b += blockDim.x) rprev[b] = rk[b];
       __syncthreads();
       if (same && sw >= 1) break;
+    }
+    if (hand_off) {
+      defer_instance(defer, inst);
+      continue;
     }
     // ---- assembly: interpolatory cores, left to right
     if (threadIdx.x == 0) Iset[0] = 0;
