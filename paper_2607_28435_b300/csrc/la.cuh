@@ -238,6 +238,8 @@ static __device__ void form_q(const cd* W, int ld, int h, int kq, const cd* taus
 // sp = c t conj(g)/|g| the update is a <- c a - sp b, b <- conj(sp) a + c b.
 // (Rutishauser's rotation with the phase of g moved onto the new b; b is
 // then a singular direction up to a unit factor, which no caller depends on.)
+// A sweep whose rotations were all below 1e-8 relative ends the iteration:
+// cyclic Jacobi converges quadratically, so it leaves the pairs near 1e-16.
 // Returns the number of sweeps used, or -1 if max_sweeps did not reach
 // convergence.
 __device__ __forceinline__ int jacobi_group_log2(int npair, int p) {
@@ -331,14 +333,16 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
             ca[i] = mkc(fma(c, x.x, -fma(spx, y.x, -spy * y.y)), fma(c, x.y, -fma(spx, y.y, spy * y.x)));
             cb[i] = mkc(fma(c, y.x, fma(spx, x.x, spy * x.y)), fma(c, y.y, fma(spx, x.y, -spy * x.x)));
           }
-          if (sub == 0) atomicOr(sh_flag, (g2 > 1e-20 * ab) ? 3 : 1);
+          if (sub == 0) atomicOr(sh_flag, (g2 > 1e-16 * ab) ? 7 : (g2 > 1e-20 * ab) ? 3 : 1);
         }
       }
       __syncthreads();
     }
     const int any = *sh_flag;
     __syncthreads();
-    if (!any) return sweep + 1;
+    // every rotation of this sweep was below 1e-8 relative: Jacobi's quadratic
+    // convergence leaves all pairs near 1e-16 after it, so no check sweep
+    if (!(any & 4)) return sweep + 1;
     if (sweep == max_sweeps - 1) return (any & 2) ? -1 : max_sweeps;
   }
   return -1;
