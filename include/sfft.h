@@ -154,6 +154,20 @@ sfft_status sfft_dense_price_batch(sfft_ctx *ctx, const sfft_problem *probs, int
                                    const int32_t *q, double *prices, double *log_strikes,
                                    int32_t *inst_status, sfft_info *info);
 
+/* Same contract, the QFT route of Sec. 3 (QFT-based option pricing) by exact
+ * statevector emulation: x is normalised to the amplitudes x/||x|| of
+ * Eq. qft_input_state, the inverse QFT is applied (the unitary DFT of
+ * Eq. dft, as M-point FFT passes in device memory), the measurement
+ * probabilities p_l = |y~_l|^2 of Eq. qft_probabilities are formed, and each
+ * price is read from sqrt(p_l) under the positive-phase assumption
+ * (Eqs. qft_phase_assumption, qft_observable_price) with exact probabilities
+ * (no shot noise). Prices therefore equal |.| of the dense route's
+ * discretised sum. n <= SFFT_DENSE_MAX_N; 32*M bytes of device workspace. */
+sfft_status sfft_qft_price_batch(sfft_ctx *ctx, const sfft_problem *probs, int32_t count,
+                                 const int64_t *l_begin, const int64_t *stride,
+                                 const int32_t *q, double *prices, double *log_strikes,
+                                 int32_t *inst_status, sfft_info *info);
+
 /* ---- lower-level entry points (one pipeline step each; used by tests) ---- */
 
 /* Integrand samples x_j (Eq. x or the Simpson variant) at `count` grid

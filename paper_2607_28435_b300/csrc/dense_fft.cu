@@ -90,3 +90,76 @@ __global__ void k_dense_gather(InstParams prm, const cd* y, int n,
     logk[i] = log(prm.S0) + prm.k0 + prm.dk * (double)u;
   }
 }
+
+// ---------------------------------------------------------------------------
+// Statevector emulation of the QFT route (Sec. 3, QFT-based option pricing):
+// the sampled x is normalised to the amplitudes x / ||x|| of
+// Eq. qft_input_state, the passes above apply the inverse QFT (unitary up to
+// the 1/sqrt(M) taken in the gather), the measurement probabilities are
+// p_l = |y~_l|^2 (Eq. qft_probabilities), and the price is read from sqrt(p_l)
+// under the positive-phase assumption (Eqs. qft_phase_assumption,
+// qft_observable_price) with exact probabilities.
+// ---------------------------------------------------------------------------
+
+// ||x||^2 in two deterministic stages: per-block partial sums, then one
+// thread adds the partials in order.
+__global__ void k_norm2_partial(const cd* x, long long M, double* part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
+       i += (long long)gridDim.x * blockDim.x)
+    s = fma(x[i].x, x[i].x, fma(x[i].y, x[i].y, s));
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_norm2_final(const double* part, int nparts, double* nrm2) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < nparts; ++b) t += part[b];
+    *nrm2 = t;
+  }
+}
+
+// x <- x / ||x||: the amplitude-encoded state
+__global__ void k_scale_unit(cd* x, long long M, const double* nrm2) {
+  const double n2 = *nrm2;
+  const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = cscale(x[i], inv);
+}
+
+// Requested strikes of the QFT route: p_l = |y~_l|^2 with y~ the unitary
+// transform of the normalised state (the passes leave it scaled by sqrt(M)),
+// price = S0 f_l ||x|| sqrt(p_l), f_l the same factor as the dense route
+// (e^{-alpha k_l} Delta_v sqrt(M) / (2 pi) on the paper's grid).
+__global__ void k_qft_gather(InstParams prm, const cd* y, int n, const int* digits, int ndig,
+                             long long l_begin, int tbits, int q, const double* nrm2,
+                             double* prices, double* logk) {
+  const double inv_M = ldexp(1.0, -n);
+  const double xnorm = sqrt(*nrm2);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < q; i += gridDim.x * blockDim.x) {
+    const long long u = l_begin + ((long long)i << tbits);
+    long long pos = 0, rem = u;
+    int used = 0;
+    for (int p = 0; p < ndig; ++p) {
+      const int R = digits[p];
+      used += R;
+      const long long k = rem & ((1LL << R) - 1);
+      rem >>= R;
+      pos += k << (n - used);
+    }
+    const double pl = cabs2(y[pos]) * inv_M;
+    double sgn;
+    const double f = price_factor(prm, u, &sgn);
+    prices[i] = prm.S0 * f * xnorm * sqrt(pl);
+    logk[i] = log(prm.S0) + prm.k0 + prm.dk * (double)u;
+  }
+}

@@ -102,3 +102,10 @@ __global__ void k_dense_sample(InstParams prm, cd* x, long long M);
 __global__ void k_fft_pass(cd* x, long long M, long long Lp, int R, int cols_per_block);
 __global__ void k_dense_gather(InstParams prm, const cd* y, int n, const int* digits, int ndig,
                                long long l_begin, int tbits, int q, double* prices, double* logk);
+// statevector emulation of the QFT route
+__global__ void k_norm2_partial(const cd* x, long long M, double* part);
+__global__ void k_norm2_final(const double* part, int nparts, double* nrm2);
+__global__ void k_scale_unit(cd* x, long long M, const double* nrm2);
+__global__ void k_qft_gather(InstParams prm, const cd* y, int n, const int* digits, int ndig,
+                             long long l_begin, int tbits, int q, const double* nrm2,
+                             double* prices, double* logk);

@@ -961,7 +961,9 @@ sfft_status sfft_tt_apply_qft(sfft_ctx* ctx, int32_t n, const int32_t* in_ranks,
 static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_t count,
                                 const int64_t* l_begin, const int64_t* stride, const int32_t* q,
                                 double* prices, double* log_strikes, int32_t* inst_status,
-                                sfft_info* info, bool dense) {
+                                sfft_info* info, int mode) {
+  // mode 0: TT-SFFT; 1: dense-FFT baseline; 2: QFT route by statevector emulation
+  const bool dense = mode != 0;
   if (!ctx || count < 0 || (count > 0 && (!probs || !l_begin || !stride || !q)))
     return set_err(ctx, SFFT_EINVAL, "bad arguments");
   ctx->err.clear();
@@ -983,7 +985,7 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
     sfft_status s = plan(ctx, probs[i], &P);
     if (s == SFFT_OK) s = check_strikes(ctx, probs[i].n, l_begin[i], stride[i], q[i], &tbits[i]);
     if (s == SFFT_OK && dense && probs[i].n > SFFT_DENSE_MAX_N)
-      s = set_err(ctx, SFFT_EINVAL, "dense baseline limited to n <= %d", SFFT_DENSE_MAX_N);
+      s = set_err(ctx, SFFT_EINVAL, "dense and statevector routes limited to n <= %d", SFFT_DENSE_MAX_N);
     host_status[i] = s;
     if (s != SFFT_OK) continue;
     valid.push_back(i);
@@ -1022,6 +1024,13 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
     CK(cudaMemsetAsync(st_dev, 0, sizeof(int) * cnt, ctx->stream));
     void* dg;
     if ((s = ensure(ctx, "dense_digits", sizeof(int) * 16, &dg))) return s;
+    const int nparts = ctx->num_sms * 8;
+    double* nrm_part = nullptr;
+    if (mode == 2) {
+      void* np;
+      if ((s = ensure(ctx, "qft_norm", sizeof(double) * (nparts + 1), &np))) return s;
+      nrm_part = reinterpret_cast<double*>(np);
+    }
     for (int k = 0; k < cnt; ++k) {
       const InstParams& P = prm[k];
       const long long M = 1LL << P.n;
@@ -1031,6 +1040,14 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
         k_dense_sample<<<ctx->num_sms * 8, kThreads, 0, ctx->stream>>>(P, x, M);
       }
       CK(cudaGetLastError());
+      if (mode == 2) {
+        // amplitude encoding: x <- x / ||x|| (Eq. qft_input_state)
+        PhaseScope ps(ctx, PH_DENSE_SAMPLE);
+        k_norm2_partial<<<nparts, kThreads, 0, ctx->stream>>>(x, M, nrm_part);
+        k_norm2_final<<<1, 32, 0, ctx->stream>>>(nrm_part, nparts, nrm_part + nparts);
+        k_scale_unit<<<ctx->num_sms * 8, kThreads, 0, ctx->stream>>>(x, M, nrm_part + nparts);
+        CK(cudaGetLastError());
+      }
       const int npass = (P.n + 7) / 8;
       std::vector<int> dig(npass);
       int left = P.n;
@@ -1056,9 +1073,14 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
       CK(cudaMemcpyAsync(dg, dig.data(), sizeof(int) * npass, cudaMemcpyHostToDevice, ctx->stream));
       if (q_v[k] > 0) {
         PhaseScope ps(ctx, PH_DENSE_GATHER);
-        k_dense_gather<<<(q_v[k] + kThreads - 1) / kThreads, kThreads, 0, ctx->stream>>>(
-            P, x, P.n, reinterpret_cast<int*>(dg), npass, lb_v[k], tb_v[k], q_v[k], prices + off_v[k],
-            log_strikes + off_v[k]);
+        if (mode == 2)
+          k_qft_gather<<<(q_v[k] + kThreads - 1) / kThreads, kThreads, 0, ctx->stream>>>(
+              P, x, P.n, reinterpret_cast<int*>(dg), npass, lb_v[k], tb_v[k], q_v[k], nrm_part + nparts,
+              prices + off_v[k], log_strikes + off_v[k]);
+        else
+          k_dense_gather<<<(q_v[k] + kThreads - 1) / kThreads, kThreads, 0, ctx->stream>>>(
+              P, x, P.n, reinterpret_cast<int*>(dg), npass, lb_v[k], tb_v[k], q_v[k], prices + off_v[k],
+              log_strikes + off_v[k]);
         CK(cudaGetLastError());
       }
     }
@@ -1158,14 +1180,21 @@ sfft_status sfft_profile_read(sfft_ctx* ctx, double* ms, double* flops, double* 
 sfft_status sfft_price_batch(sfft_ctx* ctx, const sfft_problem* probs, int32_t count, const int64_t* l_begin,
                              const int64_t* stride, const int32_t* q, double* prices, double* log_strikes,
                              int32_t* inst_status, sfft_info* info) {
-  return price_common(ctx, probs, count, l_begin, stride, q, prices, log_strikes, inst_status, info, false);
+  return price_common(ctx, probs, count, l_begin, stride, q, prices, log_strikes, inst_status, info, 0);
 }
 
 sfft_status sfft_dense_price_batch(sfft_ctx* ctx, const sfft_problem* probs, int32_t count,
                                    const int64_t* l_begin, const int64_t* stride, const int32_t* q,
                                    double* prices, double* log_strikes, int32_t* inst_status,
                                    sfft_info* info) {
-  return price_common(ctx, probs, count, l_begin, stride, q, prices, log_strikes, inst_status, info, true);
+  return price_common(ctx, probs, count, l_begin, stride, q, prices, log_strikes, inst_status, info, 1);
+}
+
+sfft_status sfft_qft_price_batch(sfft_ctx* ctx, const sfft_problem* probs, int32_t count,
+                                 const int64_t* l_begin, const int64_t* stride, const int32_t* q,
+                                 double* prices, double* log_strikes, int32_t* inst_status,
+                                 sfft_info* info) {
+  return price_common(ctx, probs, count, l_begin, stride, q, prices, log_strikes, inst_status, info, 2);
 }
 
 }  // extern "C"

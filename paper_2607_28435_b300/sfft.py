@@ -58,6 +58,10 @@ EXPORTS = {
                                          ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
                                          ctypes.POINTER(c_int32), c_void_p, c_void_p,
                                          ctypes.POINTER(c_int32), ctypes.POINTER(SfftInfo)]),
+    "sfft_qft_price_batch": (c_int32, [c_void_p, ctypes.POINTER(SfftProblem), c_int32,
+                                         ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
+                                         ctypes.POINTER(c_int32), c_void_p, c_void_p,
+                                         ctypes.POINTER(c_int32), ctypes.POINTER(SfftInfo)]),
     "sfft_sample_integrand": (c_int32, [c_void_p, ctypes.POINTER(SfftProblem), c_void_p, c_int64,
                                         c_void_p]),
     "sfft_integrand_tt": (c_int32, [c_void_p, ctypes.POINTER(SfftProblem),
@@ -276,6 +280,12 @@ class Pricer:
                           raise_on_error=True):
         """Dense-FFT Carr-Madan baseline prices, same contract."""
         return self._price(self.lib.sfft_dense_price_batch, problems, strikes, prices, log_strikes,
+                           raise_on_error)
+
+    def qft_price_batch(self, problems, strikes=None, prices=None, log_strikes=None,
+                        raise_on_error=True):
+        """QFT route by exact statevector emulation (|amplitude| readout), same contract."""
+        return self._price(self.lib.sfft_qft_price_batch, problems, strikes, prices, log_strikes,
                            raise_on_error)
 
     # -- single steps -------------------------------------------------------
