@@ -162,7 +162,10 @@ sfft_status sfft_dense_price_batch(sfft_ctx *ctx, const sfft_problem *probs, int
  * price is read from sqrt(p_l) under the positive-phase assumption
  * (Eqs. qft_phase_assumption, qft_observable_price) with exact probabilities
  * (no shot noise). Prices therefore equal |.| of the dense route's
- * discretised sum. n <= SFFT_DENSE_MAX_N; 32*M bytes of device workspace. */
+ * discretised sum. The phase assumption holds on the symmetric grid only
+ * (quad = SFFT_QUAD_RECT_SYM, Eq. x): the one-sided Simpson sum has a genuine
+ * imaginary part, so other grids are rejected with SFFT_EINVAL.
+ * n <= SFFT_DENSE_MAX_N; 32*M bytes of device workspace. */
 sfft_status sfft_qft_price_batch(sfft_ctx *ctx, const sfft_problem *probs, int32_t count,
                                  const int64_t *l_begin, const int64_t *stride,
                                  const int32_t *q, double *prices, double *log_strikes,

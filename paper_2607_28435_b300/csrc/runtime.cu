@@ -986,6 +986,10 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
     if (s == SFFT_OK) s = check_strikes(ctx, probs[i].n, l_begin[i], stride[i], q[i], &tbits[i]);
     if (s == SFFT_OK && dense && probs[i].n > SFFT_DENSE_MAX_N)
       s = set_err(ctx, SFFT_EINVAL, "dense and statevector routes limited to n <= %d", SFFT_DENSE_MAX_N);
+    // the positive-phase readout needs the symmetric grid: on the one-sided
+    // Simpson grid the discretised sum has a genuine imaginary part
+    if (s == SFFT_OK && mode == 2 && probs[i].quad != SFFT_QUAD_RECT_SYM)
+      s = set_err(ctx, SFFT_EINVAL, "the QFT route needs the symmetric grid (SFFT_QUAD_RECT_SYM)");
     host_status[i] = s;
     if (s != SFFT_OK) continue;
     valid.push_back(i);

@@ -95,10 +95,12 @@ def test_probabilities_sum_to_one(pricer, n):
     assert abs(np.sum(amp ** 2) / np.vdot(x, x).real - 1.0) <= 1e-12
 
 
-def test_heston_agrees_with_real_part_where_prices_are_positive(pricer):
-    # on a converged Simpson grid the phase assumption holds: the QFT route's
-    # |y| readout matches the dense route's real part to the price tolerance
-    p = wl.config2_heston(16)
+def test_heston_agrees_with_real_part_on_symmetric_grid(pricer):
+    # on the symmetric grid the sum is real up to its one unpaired term, so
+    # the QFT route's |y| readout (the positive-phase assumption) matches the
+    # dense route's real part to the price tolerance
+    p = wl.Problem(wl.HESTON, wl.HESTON_CFG2, S0=100.0, r=0.025, T=1.0, alpha=1.5, eta=0.0,
+                   n=16, quad=wl.RECT_SYM)
     s = cm.strike_window(p)
     cq, _, st1, _ = pricer.qft_price_batch([p], [s])
     cd, _, st2, _ = pricer.dense_price_batch([p], [s])
@@ -106,8 +108,13 @@ def test_heston_agrees_with_real_part_where_prices_are_positive(pricer):
     assert np.max(np.abs(cq.cpu().numpy() - cd.cpu().numpy())) <= 1e-8 * p.S0
 
 
-def test_rejects_beyond_dense_limit(pricer):
+def test_rejects_beyond_dense_limit_and_one_sided_grid(pricer):
     from paper_2607_28435_b300 import sfft
     p = wl.paper_grid_bs(33)
     _, _, st, _ = pricer.qft_price_batch([p], [cm.strike_window(p, qmax=16)], raise_on_error=False)
     assert st == [sfft.SFFT_EINVAL]
+    # the Simpson grid's sum is not real: |y| would not be a price
+    q = wl.config2_heston(16)
+    c, _, st, _ = pricer.qft_price_batch([q], [cm.strike_window(q, qmax=16)], raise_on_error=False)
+    assert st == [sfft.SFFT_EINVAL]
+    assert np.all(np.isnan(c.cpu().numpy()))
