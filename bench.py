@@ -60,7 +60,7 @@ def _oracle_task(args):
     return q, time.perf_counter() - t0
 
 
-def oracle_sample(pool, problems, strikes, seconds, cores):
+def oracle_sample(pool, problems, strikes, seconds, cores, one_core=False):
     """Run the oracle on consecutive instances of the batch (skipping those
     whose integrand support exceeds 2^20 points, where a direct sum would take
     minutes) until about `seconds` of wall time; returns strikes/s."""
@@ -86,7 +86,17 @@ def oracle_sample(pool, problems, strikes, seconds, cores):
             done_q += q
             done_n += 1
     wall = time.perf_counter() - t0
-    return done_q / wall, done_n, skipped, wall
+    if not one_core:
+        return done_q / wall, done_n, skipped, wall, None
+    # the same oracle on one core, in this process, for a few seconds
+    t1 = time.perf_counter()
+    one_q = 0
+    for task in tasks:
+        one_q += _oracle_task(task)[0]
+        if time.perf_counter() - t1 > min(5.0, seconds / 3):
+            break
+    one_rate = one_q / (time.perf_counter() - t1)
+    return done_q / wall, done_n, skipped, wall, one_rate
 
 
 # --------------------------------------------------------------------------- clocks
@@ -225,8 +235,9 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
 
     cpu = None
     if pool is not None and rank == 0:
-        rate, n_inst, skipped, wall = oracle_sample(pool, problems, strikes, args.cpu_seconds, ncores)
-        cpu = {"value": rate, "unit": UNIT, "cores": ncores, "kind": "oracle",
+        rate, n_inst, skipped, wall, one_rate = oracle_sample(pool, problems, strikes, args.cpu_seconds,
+                                                              ncores, one_core=True)
+        cpu = {"value": rate, "unit": UNIT, "cores": ncores, "kind": "oracle", "one_core_value": one_rate,
                "sample": f"{n_inst} consecutive instances of the batch at all their strikes "
                          f"(direct sum over the integrand support, {wall:.1f} s wall; "
                          f"{skipped} instances with support > 2^20 skipped)"}
@@ -234,6 +245,7 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
     phases = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                   "gflop_per_step": v["flops"] / args.steps / 1e9}
               for k, v in prof.items() if v["launches"]}
+    rep_pts = float(sum(2.0 ** p.n for p, o in zip(problems, ok) if o)) * max(world, 1)
     ranks_out = [i["out_rank"] for i in info if i["status"] == 0]
     ranks_int = [i["int_rank"] for i in info if i["status"] == 0]
     line = {
@@ -254,6 +266,11 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
                      "frac": achieved / fp64_peak if fp64_peak else None, "traffic": None,
                      "peak_source": "measured FP64 FMA calibration (sfft_calibrate_fp64)"},
         "phases": phases,
+        # secondary, as the metric's definition asks: grid points the priced
+        # instances represent (sum of 2^n) per second, and FP64 work per strike
+        "represented": {"value": rep_pts * args.steps / tot_s if tot_s > 0 else None,
+                        "unit": "grid points/s"},
+        "per_strike": {"fp64_flop": sum(v["flops"] for v in prof.values()) / args.steps / max(q_ok, 1)},
         "cpu_baseline": cpu,
         "dense_fft": dense,
     }
@@ -303,7 +320,25 @@ def dense_baseline(pricer, problems, strikes, torch, dev):
         t_n[n] = e0.elapsed_time(e1) / 1e3
     if not t_n:
         return None
+    # external reference point: cuFFT's complex-to-complex transform of the
+    # same length (torch.fft on the device), FFT only, beside our sample+FFT+gather
+    cufft = {}
+    for n in sorted(t_n):
+        xr = torch.zeros(1 << n, dtype=torch.complex128, device=dev)
+        torch.fft.fft(xr)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.fft.fft(xr)
+        e1.record()
+        torch.cuda.synchronize()
+        cufft[str(n)] = e0.elapsed_time(e1) / 1e3
+        del xr
     top = max(t_n)
+    # HBM traffic of our dense route at the largest measured n: the sample
+    # writes 16 M bytes, each of the ceil(n/8) passes reads and writes 16 M
+    m_top = 1 << top
+    hbm_bytes = 16.0 * m_top * (1 + 2 * ((top + 7) // 8))
     est = 0.0
     extrapolated = []
     for n, items in by_n.items():
@@ -316,8 +351,11 @@ def dense_baseline(pricer, problems, strikes, torch, dev):
     return {"value": q / est, "unit": UNIT, "batch_seconds": est, "measured_n": sorted(t_n),
             "seconds_per_n": {str(k): v for k, v in sorted(t_n.items())},
             "extrapolated_n": sorted(extrapolated),
+            "hbm_gbs_at_top_n": hbm_bytes / t_n[top] / 1e9,
+            "cufft_z2z_seconds_per_n": cufft,
             "how": "one instance per n timed (CUDA events); batch time = sum_n count_n t_n; "
-                   "n > 30 scaled as M log M from n = 30"}
+                   "n > 30 scaled as M log M from n = 30; cuFFT (torch.fft) of the same "
+                   "lengths as an external reference"}
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -328,8 +366,8 @@ def run_reference(args, pool, ncores):
     strikes = [cm.strike_window(p) for p in problems]
     rates = []
     for i in range(args.warmup + args.steps):
-        rate, n_inst, skipped, wall = oracle_sample(pool, problems, strikes,
-                                                     max(3.0, args.cpu_seconds / 3), ncores)
+        rate, n_inst, skipped, wall, _ = oracle_sample(pool, problems, strikes,
+                                                        max(3.0, args.cpu_seconds / 3), ncores)
         if i >= args.warmup:
             rates.append(rate)
     value = statistics.mean(rates)
