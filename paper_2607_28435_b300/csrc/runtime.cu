@@ -450,28 +450,21 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     k_support_probe<<<cnt, 64, 0, ctx->stream>>>(b.P, cnt, 1e-2, 4, m_dev);
   }
   CK(cudaGetLastError());
-  std::vector<int> m_host(cnt);
-  CK(cudaMemcpyAsync(m_host.data(), m_dev, sizeof(int) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  std::vector<int> svd_list, cross_list, all_list(cnt);
-  int mmax = 1;
-  for (int i = 0; i < cnt; ++i) {
-    all_list[i] = i;
-    if (m_host[i] <= kSvdMaxBits) {
-      svd_list.push_back(i);
-      mmax = std::max(mmax, m_host[i]);
-    } else {
-      cross_list.push_back(i);
-    }
-  }
-  // largest work first
-  std::stable_sort(svd_list.begin(), svd_list.end(), [&](int a, int c) { return m_host[a] > m_host[c]; });
-  std::stable_sort(cross_list.begin(), cross_list.end(), [&](int a, int c) { return prm[a].n > prm[c].n; });
+  // work lists of the builders, split and ordered on the device
+  int *svd_dev, *cross_dev, *list_counts, *all_dev, *ctr;
+  if ((s = ensure(ctx, "svd_list", sizeof(int) * cnt, &p))) return s;
+  svd_dev = reinterpret_cast<int*>(p);
+  if ((s = ensure(ctx, "cross_list", sizeof(int) * cnt, &p))) return s;
+  cross_dev = reinterpret_cast<int*>(p);
+  if ((s = ensure(ctx, "list_counts", sizeof(int) * 2, &p))) return s;
+  list_counts = reinterpret_cast<int*>(p);
+  k_build_lists<<<1, 1024, 0, ctx->stream>>>(m_dev, b.n_arr, cnt, kSvdMaxBits, svd_dev, cross_dev, list_counts);
+  CK(cudaGetLastError());
+  // the zip-up, rounding and readout take every instance, largest n first
+  std::vector<int> all_list(cnt);
+  for (int i = 0; i < cnt; ++i) all_list[i] = i;
   std::stable_sort(all_list.begin(), all_list.end(), [&](int a, int c) { return prm[a].n > prm[c].n; });
-  int *svd_dev, *cross_dev, *all_dev, *ctr;
-  if ((s = upload(ctx, "svd_list", svd_list, &svd_dev)) || (s = upload(ctx, "cross_list", cross_list, &cross_dev)) ||
-      (s = upload(ctx, "all_list", all_list, &all_dev)))
-    return s;
+  if ((s = upload(ctx, "all_list", all_list, &all_dev))) return s;
   if ((s = ensure(ctx, "counters", sizeof(int) * 16, &p))) return s;
   ctr = reinterpret_cast<int*>(p);
   CK(cudaMemsetAsync(ctr, 0, sizeof(int) * 16, ctx->stream));
@@ -490,21 +483,21 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   defer_round = reinterpret_cast<int*>(p);
   CK(cudaMemsetAsync(defer_build, 0, sizeof(int), ctx->stream));
   CK(cudaMemsetAsync(defer_round, 0, sizeof(int), ctx->stream));
-  if (!svd_list.empty()) {
-    // tier 1: panels up to kSmallP columns, 128-thread CTAs, several per SM;
-    // tier 2: the full carve for the instances tier 1 handed on
-    const int nsvd = (int)svd_list.size();
+  {
+    // TT-SVD builder. tier 1: panels up to kSmallP columns, 128-thread CTAs,
+    // several per SM; tier 2: the full carve for the instances tier 1 handed
+    // on. The list length is read on the device (list_counts[0]).
     const size_t smem1 = la::ts_svd_smem_bytes(kSmallP, kSmallP) + 256;
-    const int grid1 = std::min(nsvd, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem1,
-                                                                  kThreadsSmall));
-    const int grid2 = std::min(nsvd, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem));
-    const long long sstride = 2LL << mmax;
+    const int grid1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem1,
+                                                                 kThreadsSmall));
+    const int grid2 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem));
+    const long long sstride = 2LL << kSvdMaxBits;
     if ((s = ensure(ctx, "build_scratch", sizeof(cd) * sstride * std::max(grid1, grid2), &p))) return s;
     {
       PhaseScope ps(ctx, PH_BUILD);
       k_integrand_ttsvd<<<grid1, kThreadsSmall, smem1, ctx->stream>>>(
-          b.P, m_dev, svd_dev, nsvd, ctr + 0, reinterpret_cast<cd*>(p), sstride, b.A, b.a_off,
-          SFFT_CORE_STRIDE_D2, b.a_ranks, b.status, kSmallP, acc_ptr(ctx), kSmallP, defer_build, nullptr);
+          b.P, m_dev, svd_dev, cnt, ctr + 0, reinterpret_cast<cd*>(p), sstride, b.A, b.a_off,
+          SFFT_CORE_STRIDE_D2, b.a_ranks, b.status, kSmallP, acc_ptr(ctx), kSmallP, defer_build, list_counts);
     }
     CK(cudaGetLastError());
     PhaseScope ps(ctx, PH_BUILD);
@@ -513,26 +506,26 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
         SFFT_CORE_STRIDE_D2, b.a_ranks, b.status, kHb, acc_ptr(ctx), LA_MAXP, nullptr, defer_build);
   }
   CK(cudaGetLastError());
-  if (!cross_list.empty()) {
-    // tier 1: ranks up to kCrossSmallR (panels of 2 kCrossSmallR columns),
-    // 128-thread CTAs, every instance in flight at once; tier 2: the rest
-    const int ncr = (int)cross_list.size();
+  {
+    // cross builder (list_counts[1] instances): tier 1 ranks up to
+    // kCrossSmallR in 128-thread CTAs, every instance in flight at once;
+    // tier 2 the rest; then the rounding of the interpolatory cores
     int* defer_cross;
-    if ((s = ensure(ctx, "defer_cross", sizeof(int) * (ncr + 1), &p))) return s;
+    if ((s = ensure(ctx, "defer_cross", sizeof(int) * (cnt + 1), &p))) return s;
     defer_cross = reinterpret_cast<int*>(p);
     CK(cudaMemsetAsync(defer_cross, 0, sizeof(int), ctx->stream));
     const int xp = 2 * kCrossSmallR;
     const int xhb = kCrossSmallHb;
     const size_t smem1 = la::ts_svd_smem_bytes(xp, xhb) + 256;
-    const int grid1 = std::min(ncr, ctx->num_sms * blocks_per_sm((const void*)k_integrand_cross, smem1,
+    const int grid1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_cross, smem1,
                                                                  kThreadsSmall));
-    const int grid = std::min(ncr, ctx->num_sms * blocks_per_sm((const void*)k_integrand_cross, smem));
+    const int grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_cross, smem));
     if ((s = ensure(ctx, "cross_scratch", sizeof(cd) * (size_t)4096 * std::max(grid1, grid), &p))) return s;
     {
       PhaseScope ps(ctx, PH_CROSS);
       k_integrand_cross<<<grid1, kThreadsSmall, smem1, ctx->stream>>>(
-          b.P, cross_dev, ncr, ctr + 1, reinterpret_cast<cd*>(p), 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
-          b.a_ranks, b.status, xhb, acc_ptr(ctx), kCrossSweeps, xp, kCrossSmallR, defer_cross, nullptr);
+          b.P, cross_dev, cnt, ctr + 1, reinterpret_cast<cd*>(p), 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
+          b.a_ranks, b.status, xhb, acc_ptr(ctx), kCrossSweeps, xp, kCrossSmallR, defer_cross, list_counts + 1);
     }
     CK(cudaGetLastError());
     {
@@ -544,14 +537,14 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     CK(cudaGetLastError());
     // interpolatory cores -> right-orthonormal, truncated to tol
     const RoundSmem rs = round_smem(2);
-    const int g2 = std::min(ncr, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, rs.bytes));
+    const int g2 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, rs.bytes));
     if ((s = ensure(ctx, "xround_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * g2, &p))) return s;
     PhaseScope ps(ctx, PH_CROSS);
-    k_tt_round<<<g2, kThreads, rs.bytes, ctx->stream>>>(cross_dev, ncr, ctr + 2, b.n_arr, 2, 1, b.tol_arr,
+    k_tt_round<<<g2, kThreads, rs.bytes, ctx->stream>>>(cross_dev, cnt, ctr + 2, b.n_arr, 2, 1, b.tol_arr,
                                                         b.maxr_arr, b.A, b.a_off, SFFT_CORE_STRIDE_D2, b.a_ranks,
                                                         reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH, b.status,
                                                         rs.hb, acc_ptr(ctx), PH_CROSS, rs.pmax, rs.vcap, nullptr,
-                                                        nullptr);
+                                                        list_counts + 1);
   }
   CK(cudaGetLastError());
   if (!apply) return SFFT_OK;

@@ -171,6 +171,53 @@ __global__ void k_support_probe(const InstParams* __restrict__ P, int count, dou
 }
 
 // ---------------------------------------------------------------------------
+// Work lists of the two builders, on the device (no host round trip): support
+// exponents m <= svd_max_bits go to the TT-SVD builder, largest m first, the
+// rest to the cross builder, largest n first; counts[0] and counts[1] receive
+// the list lengths. One block, bucketed by key with shared-memory counters;
+// the order among equal keys is arbitrary, which changes no result (every
+// instance is built by one CTA alone).
+// ---------------------------------------------------------------------------
+__global__ void k_build_lists(const int* m_arr, const int* n_arr, int count, int svd_max_bits,
+                              int* svd_list, int* cross_list, int* counts) {
+  __shared__ int hs[64], hc[64];
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+    hs[i] = 0;
+    hc[i] = 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const int m = m_arr[i];
+    if (m <= svd_max_bits)
+      atomicAdd(&hs[max(m, 0)], 1);
+    else
+      atomicAdd(&hc[min(n_arr[i], 63)], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // bucket offsets, largest key first
+    int os = 0, oc = 0;
+    for (int k = 63; k >= 0; --k) {
+      const int ts = hs[k], tc = hc[k];
+      hs[k] = os;
+      hc[k] = oc;
+      os += ts;
+      oc += tc;
+    }
+    counts[0] = os;
+    counts[1] = oc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const int m = m_arr[i];
+    if (m <= svd_max_bits)
+      svd_list[atomicAdd(&hs[max(m, 0)], 1)] = i;
+    else
+      cross_list[atomicAdd(&hc[min(n_arr[i], 63)], 1)] = i;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K2: integrand TT by TT-SVD of the support block (Sec. 3.1; Oseledets 2011)
 // ---------------------------------------------------------------------------
 // The block x_j, j < 2^m, is swept from its least significant bit: at step t
