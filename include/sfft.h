@@ -171,6 +171,36 @@ sfft_status sfft_qft_price_batch(sfft_ctx *ctx, const sfft_problem *probs, int32
                                  const int32_t *q, double *prices, double *log_strikes,
                                  int32_t *inst_status, sfft_info *info);
 
+/* ---- captured batches (CUDA graphs) ----
+ * The device work of one sfft_price_batch call, recorded as a CUDA graph and
+ * replayed: repeated pricing of a batch of fixed shape without host planning
+ * or per-kernel launch cost. The shape is every instance's n, tol, quad,
+ * max_rank, k0 and strike set; model parameters, S0, r, T, alpha and eta may
+ * change between replays through sfft_graph_update. (Sec. 3.2 builds the
+ * transform once for reuse across evaluations; this carries the reuse to the
+ * whole pricing step.)
+ * sfft_graph_create runs the batch once in a private context, whose
+ * workspaces, MPO cache and stream belong to the graph alone and never move,
+ * then captures the same call; every instance must price (else the status of
+ * the first failure is returned and *out stays NULL). prices and log_strikes
+ * (device, sum(q) doubles each) stay bound to the graph. */
+typedef struct sfft_graph sfft_graph;
+sfft_status sfft_graph_create(sfft_ctx *ctx, const sfft_problem *probs, int32_t count,
+                              const int64_t *l_begin, const int64_t *stride,
+                              const int32_t *q, double *prices, double *log_strikes,
+                              sfft_graph **out);
+/* Enqueue one replay on `stream` (a cudaStream_t; NULL = legacy stream).
+ * A replay on a different stream than the previous one first waits for it. */
+sfft_status sfft_graph_launch(sfft_graph *g, void *stream);
+/* New problem statements (count as at creation; the shape fields must match)
+ * for the following replays. Waits for the previous replay to finish. */
+sfft_status sfft_graph_update(sfft_graph *g, const sfft_problem *probs);
+/* Per-instance status and diagnostics of the last replay (host arrays, may be
+ * NULL); waits for it. Returns the first failing status, as sfft_price_batch. */
+sfft_status sfft_graph_status(sfft_graph *g, int32_t *inst_status, sfft_info *info);
+const char *sfft_graph_last_error(const sfft_graph *g);
+sfft_status sfft_graph_destroy(sfft_graph *g);
+
 /* ---- lower-level entry points (one pipeline step each; used by tests) ---- */
 
 /* Integrand samples x_j (Eq. x or the Simpson variant) at `count` grid

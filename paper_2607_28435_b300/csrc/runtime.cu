@@ -79,6 +79,15 @@ struct sfft_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;
   double prof_ms[SFFT_NPHASE_DEV] = {0};
   long long prof_launches[SFFT_NPHASE_DEV] = {0};
+  // while a graph is being captured: host data of every upload is first
+  // copied into this pinned arena (a captured copy must read pinned memory
+  // that outlives the capture)
+  struct Stage {
+    char* base = nullptr;
+    size_t cap = 0, used = 0;
+    size_t p_off = 0, p_bytes = 0;  // where the instance parameters went
+    bool overflow = false;
+  }* stage = nullptr;
 };
 
 namespace {
@@ -371,12 +380,34 @@ sfft_status get_mpo(sfft_ctx* ctx, int n, double tol, const MpoEntry** out) {
   return SFFT_OK;
 }
 
+// Host-to-device copy on the context's stream; during graph capture the
+// source is first staged in the pinned arena.
+sfft_status h2d(sfft_ctx* ctx, void* dst, const void* src, size_t bytes, bool is_params = false) {
+  if (ctx->stage) {
+    auto* st = ctx->stage;
+    const size_t off = (st->used + 255) & ~(size_t)255;
+    if (off + bytes > st->cap) {
+      st->overflow = true;
+      return set_err(ctx, SFFT_ENOMEM, "graph staging arena too small");
+    }
+    memcpy(st->base + off, src, bytes);
+    if (is_params) {
+      st->p_off = off;
+      st->p_bytes = bytes;
+    }
+    st->used = off + bytes;
+    src = st->base + off;
+  }
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  return SFFT_OK;
+}
+
 template <class T>
 sfft_status upload(sfft_ctx* ctx, const char* name, const std::vector<T>& v, T** out) {
   void* p;
   sfft_status s = ensure(ctx, name, sizeof(T) * std::max<size_t>(v.size(), 1), &p);
   if (s) return s;
-  if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, ctx->stream));
+  if (!v.empty() && (s = h2d(ctx, p, v.data(), sizeof(T) * v.size(), strcmp(name, "P") == 0))) return s;
   *out = reinterpret_cast<T*>(p);
   return SFFT_OK;
 }
@@ -558,8 +589,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     std::copy(e->ranks.begin(), e->ranks.end(), w_ranks.begin() + (size_t)i * (SFFT_MAX_N + 1));
   }
   if ((s = upload(ctx, "w_off", w_off, &b.w_off))) return s;
-  CK(cudaMemcpyAsync(b.w_ranks, w_ranks.data(), sizeof(int) * w_ranks.size(), cudaMemcpyHostToDevice,
-                     ctx->stream));
+  if ((s = h2d(ctx, b.w_ranks, w_ranks.data(), sizeof(int) * w_ranks.size()))) return s;
   // tier 1: W-only carve, three CTAs per SM; tier 2: the full carve for the
   // instances whose panels (with their explicit Q) outgrow it
   int* defer_zip;
@@ -951,10 +981,17 @@ sfft_status sfft_tt_apply_qft(sfft_ctx* ctx, int32_t n, const int32_t* in_ranks,
   return copy_tt_out(ctx, B, reinterpret_cast<int*>(rb), n, 2, SFFT_CORE_STRIDE_D2, out_ranks, out_cores, cap);
 }
 
+// What a captured pricing call leaves for reading its statuses later.
+struct GraphCapture {
+  Batch b;
+  std::vector<int> valid, host_status;
+  std::vector<const MpoEntry*> mp;
+};
+
 static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_t count,
                                 const int64_t* l_begin, const int64_t* stride, const int32_t* q,
                                 double* prices, double* log_strikes, int32_t* inst_status,
-                                sfft_info* info, int mode) {
+                                sfft_info* info, int mode, GraphCapture* gc = nullptr) {
   // mode 0: TT-SFFT; 1: dense-FFT baseline; 2: QFT route by statevector emulation
   const bool dense = mode != 0;
   if (!ctx || count < 0 || (count > 0 && (!probs || !l_begin || !stride || !q)))
@@ -1105,6 +1142,13 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
                                                   reinterpret_cast<cd*>(p), SFFT_READOUT_SCRATCH);
   }
   CK(cudaGetLastError());
+  if (gc) {  // being captured: the statuses are read after each replay
+    gc->b = b;
+    gc->valid = valid;
+    gc->host_status = host_status;
+    gc->mp = mp;
+    return SFFT_OK;
+  }
   return finish_status(ctx, count, valid, host_status, b.status, inst_status, info, &b, &mp);
 }
 
@@ -1193,5 +1237,145 @@ sfft_status sfft_qft_price_batch(sfft_ctx* ctx, const sfft_problem* probs, int32
                                  sfft_info* info) {
   return price_common(ctx, probs, count, l_begin, stride, q, prices, log_strikes, inst_status, info, 2);
 }
+
+
+// ---------------------------------------------------------------------------
+// Captured batches (CUDA graphs)
+// ---------------------------------------------------------------------------
+struct sfft_graph {
+  sfft_ctx* own = nullptr;  // private context: its buffers never move while the graph lives
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  sfft_ctx::Stage stage;
+  int count = 0;
+  std::vector<sfft_problem> probs;
+  GraphCapture gc;
+  cudaStream_t last = nullptr;
+  bool launched = false;
+};
+
+sfft_status sfft_graph_destroy(sfft_graph* g) {
+  if (!g) return SFFT_OK;
+  if (g->own) cudaSetDevice(g->own->device);
+  if (g->launched) cudaStreamSynchronize(g->last);
+  if (g->ge) cudaGraphExecDestroy(g->ge);
+  if (g->g) cudaGraphDestroy(g->g);
+  if (g->stage.base) cudaFreeHost(g->stage.base);
+  if (g->own) sfft_destroy(g->own);
+  delete g;
+  return SFFT_OK;
+}
+
+sfft_status sfft_graph_create(sfft_ctx* ctx, const sfft_problem* probs, int32_t count,
+                              const int64_t* l_begin, const int64_t* stride, const int32_t* q,
+                              double* prices, double* log_strikes, sfft_graph** out) {
+  if (!ctx || !out || count < 1 || !probs || !l_begin || !stride || !q || !prices || !log_strikes)
+    return set_err(ctx, SFFT_EINVAL, "bad arguments");
+  *out = nullptr;
+  if (ctx->prof) return set_err(ctx, SFFT_EINVAL, "turn profiling off before capturing a graph");
+  sfft_graph* g = new sfft_graph;
+  g->count = count;
+  g->probs.assign(probs, probs + count);
+  sfft_status s = sfft_create(&g->own, ctx->device);
+  if (s) {
+    delete g;
+    return set_err(ctx, s, "graph: context creation failed");
+  }
+  // 1. a plain run sizes every workspace and builds the MPOs
+  std::vector<int32_t> st(count);
+  s = price_common(g->own, probs, count, l_begin, stride, q, prices, log_strikes, st.data(), nullptr, 0);
+  for (int i = 0; s == SFFT_OK && i < count; ++i)
+    if (st[i] != SFFT_OK) s = (sfft_status)st[i];
+  if (s) {
+    set_err(ctx, s, "graph: every instance must price (%s)", g->own->err.c_str());
+    sfft_graph_destroy(g);
+    return s;
+  }
+  // 2. capture the same call on a private stream, uploads staged in pinned memory
+  g->stage.cap = (size_t)count * 2048 + (1 << 20);
+  if (cudaMallocHost(reinterpret_cast<void**>(&g->stage.base), g->stage.cap) != cudaSuccess) {
+    sfft_graph_destroy(g);
+    return set_err(ctx, SFFT_ENOMEM, "graph: pinned staging arena");
+  }
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    sfft_graph_destroy(g);
+    return set_err(ctx, SFFT_ECUDA, "graph: stream creation");
+  }
+  cudaStream_t keep = g->own->stream;
+  g->own->stream = cs;
+  g->own->stage = &g->stage;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    s = price_common(g->own, probs, count, l_begin, stride, q, prices, log_strikes, nullptr, nullptr, 0,
+                     &g->gc);
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g->g);
+    if (s == SFFT_OK && e2 != cudaSuccess) s = SFFT_ECUDA;
+  } else {
+    s = SFFT_ECUDA;
+  }
+  g->own->stage = nullptr;
+  g->own->stream = keep;
+  cudaStreamDestroy(cs);
+  if (s == SFFT_OK && cudaGraphInstantiate(&g->ge, g->g, 0) != cudaSuccess) s = SFFT_ECUDA;
+  if (s) {
+    set_err(ctx, s, "graph: capture failed (%s)", g->own->err.c_str());
+    cudaGetLastError();
+    sfft_graph_destroy(g);
+    return s;
+  }
+  *out = g;
+  return SFFT_OK;
+}
+
+sfft_status sfft_graph_launch(sfft_graph* g, void* stream) {
+  if (!g) return SFFT_EINVAL;
+  sfft_ctx* ctx = g->own;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t sm = reinterpret_cast<cudaStream_t>(stream);
+  if (g->launched && g->last != sm) CK(cudaStreamSynchronize(g->last));
+  CK(cudaGraphLaunch(g->ge, sm));
+  g->last = sm;
+  g->launched = true;
+  return SFFT_OK;
+}
+
+sfft_status sfft_graph_update(sfft_graph* g, const sfft_problem* probs) {
+  if (!g || !probs) return SFFT_EINVAL;
+  sfft_ctx* ctx = g->own;
+  CK(cudaSetDevice(ctx->device));
+  std::vector<InstParams> prm(g->count);
+  for (int i = 0; i < g->count; ++i) {
+    const sfft_problem& a = g->probs[i];
+    const sfft_problem& b = probs[i];
+    if (a.n != b.n || a.tol != b.tol || a.quad != b.quad || a.max_rank != b.max_rank ||
+        (isnan(a.k0) != isnan(b.k0)) || (!isnan(a.k0) && a.k0 != b.k0))
+      return set_err(ctx, SFFT_EINVAL, "instance %d: n, tol, quad, max_rank and k0 are fixed by the graph", i);
+    sfft_status s = plan(ctx, b, &prm[i]);
+    if (s) return s;
+  }
+  if (sizeof(InstParams) * prm.size() != g->stage.p_bytes)
+    return set_err(ctx, SFFT_EINVAL, "graph: parameter block size changed");
+  // the previous replay may still be reading the arena
+  if (g->launched) CK(cudaStreamSynchronize(g->last));
+  memcpy(g->stage.base + g->stage.p_off, prm.data(), g->stage.p_bytes);
+  for (int i = 0; i < g->count; ++i) g->probs[i] = probs[i];
+  return SFFT_OK;
+}
+
+sfft_status sfft_graph_status(sfft_graph* g, int32_t* inst_status, sfft_info* info) {
+  if (!g) return SFFT_EINVAL;
+  sfft_ctx* ctx = g->own;
+  if (!g->launched) return set_err(ctx, SFFT_EINVAL, "graph not launched yet");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t keep = g->own->stream;
+  g->own->stream = g->last;
+  const sfft_status s = finish_status(g->own, g->count, g->gc.valid, g->gc.host_status, g->gc.b.status,
+                                      inst_status, info, &g->gc.b, &g->gc.mp);
+  g->own->stream = keep;
+  return s;
+}
+
+const char* sfft_graph_last_error(const sfft_graph* g) { return (g && g->own) ? g->own->err.c_str() : ""; }
 
 }  // extern "C"

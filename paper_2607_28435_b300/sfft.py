@@ -62,6 +62,15 @@ EXPORTS = {
                                          ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
                                          ctypes.POINTER(c_int32), c_void_p, c_void_p,
                                          ctypes.POINTER(c_int32), ctypes.POINTER(SfftInfo)]),
+    "sfft_graph_create": (c_int32, [c_void_p, ctypes.POINTER(SfftProblem), c_int32,
+                                    ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
+                                    ctypes.POINTER(c_int32), c_void_p, c_void_p,
+                                    ctypes.POINTER(c_void_p)]),
+    "sfft_graph_launch": (c_int32, [c_void_p, c_void_p]),
+    "sfft_graph_update": (c_int32, [c_void_p, ctypes.POINTER(SfftProblem)]),
+    "sfft_graph_status": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(SfftInfo)]),
+    "sfft_graph_last_error": (ctypes.c_char_p, [c_void_p]),
+    "sfft_graph_destroy": (c_int32, [c_void_p]),
     "sfft_sample_integrand": (c_int32, [c_void_p, ctypes.POINTER(SfftProblem), c_void_p, c_int64,
                                         c_void_p]),
     "sfft_integrand_tt": (c_int32, [c_void_p, ctypes.POINTER(SfftProblem),
@@ -154,6 +163,60 @@ class _View(collections.abc.Sequence):
         if not 0 <= i < self._n:
             raise IndexError(i)
         return self._get(i)
+
+
+class Graph:
+    """A batch of fixed shape captured as a CUDA graph (sfft_graph_*): launch()
+    replays it on the current torch stream, update() swaps in new problem
+    statements of the same shape, status() reads the last replay's statuses.
+    The prices and log_strikes tensors stay bound to the graph."""
+
+    def __init__(self, pricer, problems, strikes):
+        torch = pricer.torch
+        self.lib = pricer.lib
+        self.torch = torch
+        self.batch = Batch(problems, strikes)
+        dev = torch.device("cuda", pricer.device)
+        n = max(self.batch.total, 1)
+        self.prices = torch.empty(n, dtype=torch.float64, device=dev)
+        self.log_strikes = torch.empty(n, dtype=torch.float64, device=dev)
+        self.h = c_void_p()
+        b = self.batch
+        s = self.lib.sfft_graph_create(pricer.h, b.problems, b.count, b.l_begin, b.stride, b.q,
+                                       c_void_p(_ptr(self.prices)), c_void_p(_ptr(self.log_strikes)),
+                                       ctypes.byref(self.h))
+        if s != SFFT_OK:
+            raise SfftError(s, pricer.last_error())
+
+    def _check(self, s):
+        if s != SFFT_OK:
+            raise SfftError(s, self.lib.sfft_graph_last_error(self.h).decode())
+
+    def launch(self):
+        stream = self.torch.cuda.current_stream().cuda_stream
+        self._check(self.lib.sfft_graph_launch(self.h, c_void_p(stream)))
+
+    def update(self, problems):
+        arr = (SfftProblem * max(len(problems), 1))(*[to_c_problem(p) for p in problems])
+        self._check(self.lib.sfft_graph_update(self.h, arr))
+
+    def status(self, raise_on_error=False):
+        b = self.batch
+        s = self.lib.sfft_graph_status(self.h, b.status, b.info)
+        if raise_on_error:
+            self._check(s)
+        return b.statuses(), b.infos()
+
+    def close(self):
+        if self.h:
+            self.lib.sfft_graph_destroy(self.h)
+            self.h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class SfftError(RuntimeError):

@@ -1,0 +1,96 @@
+"""Captured batches (sfft_graph_*): a replayed CUDA graph prices exactly what
+sfft_price_batch prices, before and after a parameter update, and keeps
+working after the calling context has priced other, larger batches."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import carr_madan as cm
+from paper_2607_28435_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pricer():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_28435_b300 import build, sfft
+    build.build()
+    p = sfft.Pricer(0)
+    yield p
+    p.close()
+
+
+def _batch(count, seed):
+    probs = wl.config3_batch(count, seed=seed)
+    return probs, [cm.strike_window(p) for p in probs]
+
+
+def _prices(pricer, probs, strikes):
+    c, k, st, _ = pricer.price_batch(probs, strikes)
+    assert all(s == 0 for s in st)
+    return c.cpu().numpy(), k.cpu().numpy()
+
+
+def test_replays_match_price_batch(pricer):
+    from paper_2607_28435_b300 import sfft
+    probs, strikes = _batch(48, 11)
+    ref_c, ref_k = _prices(pricer, probs, strikes)
+    g = sfft.Graph(pricer, probs, strikes)
+    try:
+        for _ in range(2):
+            g.prices.fill_(np.nan)
+            g.launch()
+            st, info = g.status(raise_on_error=True)
+            assert st == [0] * len(probs)
+            assert np.array_equal(g.prices.cpu().numpy(), ref_c)
+            assert np.array_equal(g.log_strikes.cpu().numpy(), ref_k)
+            assert max(i["out_rank"] for i in info) > 0
+    finally:
+        g.close()
+
+
+def test_update_reprices_and_survives_other_batches(pricer):
+    from paper_2607_28435_b300 import sfft
+    probs, strikes = _batch(32, 12)
+    g = sfft.Graph(pricer, probs, strikes)
+    try:
+        # new market data, same shape
+        upd = [p.replace(S0=p.S0 * 1.1, r=p.r + 0.01, T=p.T * 0.9) for p in probs]
+        g.update(upd)
+        # the calling context prices a larger, different batch meanwhile
+        big, big_s = _batch(256, 13)
+        _prices(pricer, big, big_s)
+        g.launch()
+        st, _ = g.status(raise_on_error=True)
+        assert st == [0] * len(probs)
+        ref_c, ref_k = _prices(pricer, upd, strikes)
+        assert np.array_equal(g.prices.cpu().numpy(), ref_c)
+        assert np.array_equal(g.log_strikes.cpu().numpy(), ref_k)
+    finally:
+        g.close()
+
+
+def test_update_rejects_shape_change(pricer):
+    from paper_2607_28435_b300 import sfft
+    probs, strikes = _batch(4, 14)
+    g = sfft.Graph(pricer, probs, strikes)
+    try:
+        bad = [probs[0].replace(n=probs[0].n + 1)] + list(probs[1:])
+        with pytest.raises(sfft.SfftError):
+            g.update(bad)
+        g.launch()
+        st, _ = g.status()
+        assert st == [0] * len(probs)
+    finally:
+        g.close()
+
+
+def test_create_refuses_failing_instance(pricer):
+    from paper_2607_28435_b300 import sfft
+    probs, strikes = _batch(2, 15)
+    # a Variance-Gamma instance whose damping moment does not exist
+    vg = wl.Problem(wl.VG, (0.2, 0.3, -0.1), S0=100.0, r=0.03, T=1.0, alpha=8.0, eta=0.25, n=16)
+    with pytest.raises(sfft.SfftError):
+        sfft.Graph(pricer, probs + [vg], strikes + [cm.strike_window(vg)])
