@@ -90,7 +90,7 @@ def test_update_rejects_shape_change(pricer):
 def test_create_refuses_failing_instance(pricer):
     from paper_2607_28435_b300 import sfft
     probs, strikes = _batch(2, 15)
-    # a Variance-Gamma instance whose damping moment does not exist
-    vg = wl.Problem(wl.VG, (0.2, 0.3, -0.1), S0=100.0, r=0.03, T=1.0, alpha=8.0, eta=0.25, n=16)
+    # an instance that cannot price (negative maturity)
+    bad = probs[0].replace(T=-1.0)
     with pytest.raises(sfft.SfftError):
-        sfft.Graph(pricer, probs + [vg], strikes + [cm.strike_window(vg)])
+        sfft.Graph(pricer, probs + [bad], strikes + [strikes[0]])
