@@ -234,9 +234,7 @@ static __device__ void form_q(const cd* W, int ld, int h, int kq, const cd* taus
 // updates, and are shared by all pairs of a warp.
 // Rotation of a pair (a, b) with alpha = |a|^2, beta = |b|^2, g = a^H b,
 // D = beta - alpha: t = sign(D) 2|g| / (|D| + sqrt(D^2 + 4|g|^2)) is the
-// tangent of the annihilating angle (formed in FP32, see below; an angle
-// off by 1e-7 relative leaves 1e-7 of g, which the next visit removes),
-// c = 1/sqrt(1 + t^2), and with
+// tangent of the annihilating angle, c = 1/sqrt(1 + t^2), and with
 // sp = c t conj(g)/|g| the update is a <- c a - sp b, b <- conj(sp) a + c b.
 // (Rutishauser's rotation with the phase of g moved onto the new b; b is
 // then a singular direction up to a unit factor, which no caller depends on.)
@@ -325,26 +323,8 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
             sy *= inv;
             G2 = fma(sx, sx, sy * sy);
           }
-          // the tangent factor w (t = w |g|) only has to annihilate most of
-          // g: it is formed in FP32 on D and |g|^2 scaled by a power of two
-          // near 1/max(alpha, beta); c and sp below are formed from the same w
-          // in FP64, so the rotation stays unitary to FP64 rounding. Pairs
-          // whose scaled |g|^2 would underflow FP32 take the FP64 formula.
-          double w;
-          {
-            const double bm = big > 1e140 ? 1.0 : big;
-            const int e = (int)((__double_as_longlong(bm) >> 52) & 0x7ff);
-            const double sc = __longlong_as_double((long long)(2046 - max(e, 1)) << 52);  // 2^(1023-e)
-            const float Df = (float)(D * sc);
-            const float G2f = (float)(G2 * sc * sc);
-            if (G2f > 1e-30f) {
-              const float rf = sqrtf(fmaf(Df, Df, 4.0f * G2f));
-              w = (double)(copysignf(2.0f, Df) / (fabsf(Df) + rf)) * sc;
-            } else {
-              const double r = sqrt(fma(D, D, 4.0 * G2));
-              w = copysign(2.0, D) / (fabs(D) + r);
-            }
-          }
+          const double r = sqrt(fma(D, D, 4.0 * G2));
+          const double w = copysign(2.0, D) / (fabs(D) + r);  // t = w |g|
           const double c = rsqrt(fma(w * w, G2, 1.0));
           const double cw = c * w;
           const double spx = cw * sx, spy = -cw * sy;           // sp = c w conj(g)
