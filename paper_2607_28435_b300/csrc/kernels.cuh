@@ -13,7 +13,11 @@
 #define SFFT_ZIP_CH_DEV (SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV)
 #define SFFT_ZIP_D_DEV (2 * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV)
 #define SFFT_ZIP_Z_DEV (2 * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV)
-#define SFFT_ZIP_SCRATCH (SFFT_ZIP_CH_DEV + SFFT_ZIP_D_DEV + SFFT_ZIP_Z_DEV)
+// real planes of the 3-multiplication products (doubles): carry re+im, D
+// re+im, integrand core re-im, MPO core re-im; counted here in complex units
+#define SFFT_ZIP_SUM_AW (6 * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV)
+#define SFFT_ZIP_SUMS_DEV ((SFFT_ZIP_CH_DEV + SFFT_ZIP_D_DEV + SFFT_ZIP_SUM_AW) / 2)
+#define SFFT_ZIP_SCRATCH (SFFT_ZIP_CH_DEV + SFFT_ZIP_D_DEV + SFFT_ZIP_Z_DEV + SFFT_ZIP_SUMS_DEV)
 #define SFFT_ROUND_SCRATCH (5 * SFFT_CORE_STRIDE_D4)
 #define READOUT_TREE_BITS 5                   // low bits expanded as a tree in the readout
 #define SFFT_READOUT_SCRATCH (2 * 2112 * SFFT_SLOT_RANK_DEV)

@@ -833,6 +833,13 @@ __global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, in
     cd* CH = scratch + (size_t)blockIdx.x * scratch_stride;
     cd* Dt = CH + SFFT_ZIP_CH_DEV;
     cd* Z = Dt + SFFT_ZIP_D_DEV;
+    // 3-multiplication products x conj(y): T1 = sum xr yr, T2 = sum xi yi,
+    // T3 = sum (xr + xi)(yr - yi); re = T1 + T2, im = T3 - T1 + T2. The
+    // planes below hold xr + xi of the carry and of D, yr - yi of the cores.
+    double* CHs = reinterpret_cast<double*>(Z + SFFT_ZIP_Z_DEV);
+    double* Dts = CHs + SFFT_ZIP_CH_DEV;
+    double* Ass = Dts + SFFT_ZIP_D_DEV;
+    double* Wss = Ass + 2 * SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV;
     int st = 0;
     if (status[inst] != 0) continue;
     if (threadIdx.x == 0) {
@@ -857,17 +864,30 @@ __global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, in
       }
       const cd* As = Ab + (size_t)s * core_stride_a;
       const cd* Ws = Wb + (size_t)s * core_stride_w;
-      // Dt
+      // sum planes of this site's factors
+      for (int idx = threadIdx.x; idx < s0 * rA0 * rc; idx += blockDim.x) CHs[idx] = CH[idx].x + CH[idx].y;
+      for (int idx = threadIdx.x; idx < rA0 * 2 * rA1; idx += blockDim.x) Ass[idx] = As[idx].x - As[idx].y;
+      for (int idx = threadIdx.x; idx < s0 * 4 * s1; idx += blockDim.x) Wss[idx] = Ws[idx].x - Ws[idx].y;
+      __syncthreads();
+      // Dt[c][a][lam][b'] = sum_b CH[(a, b), c] conj(A[b][lam][b'])
       const int nd = rc * s0 * 2 * rA1;
       for (int idx = threadIdx.x; idx < nd; idx += blockDim.x) {
         int rem = idx;
         const int bp = rem % rA1; rem /= rA1;
         const int lam = rem & 1; rem >>= 1;
         const int a = rem % s0; const int c = rem / s0;
-        cd acc = mkc(0.0, 0.0);
-        for (int b = 0; b < rA0; ++b)
-          acc = cfma(CH[(size_t)(a * rA0 + b) * rc + c], cconj(As[(size_t)b * 2 * rA1 + lam * rA1 + bp]), acc);
-        Dt[idx] = acc;
+        double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+        for (int b = 0; b < rA0; ++b) {
+          const size_t ci = (size_t)(a * rA0 + b) * rc + c;
+          const size_t ai = (size_t)b * 2 * rA1 + lam * rA1 + bp;
+          const cd x = CH[ci], y = As[ai];
+          t1 = fma(x.x, y.x, t1);
+          t2 = fma(x.y, y.y, t2);
+          t3 = fma(CHs[ci], Ass[ai], t3);
+        }
+        const double re = t1 + t2, im = t3 - t1 + t2;
+        Dt[idx] = mkc(re, im);
+        Dts[idx] = re + im;
       }
       __syncthreads();
       const int q = s1 * rA1, p = 2 * rc;
@@ -882,15 +902,19 @@ __global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, in
         const int row = idx / p, col = idx - row * p;
         const int ap = row / rA1, bp = row - ap * rA1;
         const int c = col >> 1, mu = col & 1;
-        cd acc = mkc(0.0, 0.0);
+        double t1 = 0.0, t2 = 0.0, t3 = 0.0;
         for (int a = 0; a < s0; ++a) {
 #pragma unroll
           for (int lam = 0; lam < 2; ++lam) {
-            const cd d = Dt[(((size_t)c * s0 + a) * 2 + lam) * rA1 + bp];
-            const cd w = Ws[(size_t)a * 4 * s1 + (2 * mu + lam) * s1 + ap];
-            acc = cfma(d, cconj(w), acc);
+            const size_t di = (((size_t)c * s0 + a) * 2 + lam) * rA1 + bp;
+            const size_t wi = (size_t)a * 4 * s1 + (2 * mu + lam) * s1 + ap;
+            const cd d = Dt[di], w = Ws[wi];
+            t1 = fma(d.x, w.x, t1);
+            t2 = fma(d.y, w.y, t2);
+            t3 = fma(Dts[di], Wss[wi], t3);
           }
         }
+        const cd acc = mkc(t1 + t2, t3 - t1 + t2);
         if (direct)
           sm.W[idx] = cconj(acc);
         else
