@@ -217,20 +217,37 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
                  "how": "the step captured once as a CUDA graph in a private context, replayed"}
         g.close()
 
-    # end to end: same call, outputs copied to pinned host memory inside the timed region
-    hp = torch.empty(total_q, dtype=torch.float64, pin_memory=True)
-    hk = torch.empty(total_q, dtype=torch.float64, pin_memory=True)
-    e2e_ms = []
-    for _ in range(args.steps):
+    # end to end, as a caller pricing successive batches runs it: every step
+    # prices through the C ABI (its inputs copied from host memory inside the
+    # call) into one of two device output buffers, and a copy stream reads the
+    # step's prices and log-strikes back into pinned host memory while the next
+    # step computes; the clock stops once the last step's read-back has landed
+    hp = [torch.empty(total_q, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    hk = [torch.empty(total_q, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    dp = [prices, torch.empty_like(prices)]
+    dk = [logk, torch.empty_like(logk)]
+    copy_stream = torch.cuda.Stream(device=dev)
+    freed = [None, None]  # event: the read-back of buffer j has finished
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        j = i % 2
+        main = torch.cuda.current_stream()
+        if freed[j] is not None:
+            main.wait_event(freed[j])
         flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pricer.price_batch(batch, None, prices, logk, raise_on_error=False)
-        hp.copy_(prices, non_blocking=True)
-        hk.copy_(logk, non_blocking=True)
-        torch.cuda.synchronize()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_value = q_all / (sum(e2e_ms) / 1e3 / args.steps)
+        pricer.price_batch(batch, None, dp[j], dk[j], raise_on_error=False)
+        ready = torch.cuda.Event()
+        ready.record(main)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(ready)
+            hp[j].copy_(dp[j], non_blocking=True)
+            hk[j].copy_(dk[j], non_blocking=True)
+            freed[j] = torch.cuda.Event()
+            freed[j].record(copy_stream)
+    torch.cuda.synchronize()
+    e2e_wall = time.perf_counter() - t0
+    e2e_value = q_all * args.steps / e2e_wall
     h2d = args.count * (ctypes_sizeof_problem() + 20)
     d2h = 16 * total_q
 
@@ -277,7 +294,9 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
                    "max_int_rank": max(ranks_int) if ranks_int else None,
                    "max_out_rank": max(ranks_out) if ranks_out else None},
         "clocks": clk,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "how": "successive steps through sfft_price_batch from host arrays; each step's outputs "
+                       "read back to pinned host memory on a copy stream, overlapping the next step"},
         "gpu_launches": launches // args.steps,
         "roofline": {"bound": "alu", "kernel": sfft.PHASE_KERNELS[sfft.PHASE_NAMES.index(dom)],
                      "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s FP64",
