@@ -228,7 +228,7 @@ static __device__ void form_q(const cd* W, int ld, int h, int kq, const cd* taus
 // |l_a^H l_b| <= tol * ||l_a|| ||l_b||. Columns are visited in round-robin
 // tournament order, the m/2 pairs of a round in parallel. A pair is handled
 // by a group of G lanes (G a power of two): rows are strided over the group
-// and its four sums reduced in log2(G) shuffle steps. G minimises the FP64
+// and a^H b reduced in log2(G) shuffle steps. G minimises the FP64
 // instruction count of a round (the cost model above hh_group_log2): the
 // rotation parameters cost about as much as 2 rows of dot products and
 // updates, and are shared by all pairs of a warp.
@@ -248,7 +248,7 @@ __device__ __forceinline__ int jacobi_group_log2(int npair, int p) {
   for (int lg = 0; lg <= 5; ++lg) {
     const int G = 1 << lg;
     const long long w = ((long long)npair * G + 31) >> 5;
-    const long long cost = w * (20 * ((p + G - 1) / G) + 4 * lg + 40);
+    const long long cost = w * (16 * ((p + G - 1) / G) + 2 * lg + 40);
     if (cost < best_cost) {
       best_cost = cost;
       best = lg;
@@ -272,8 +272,19 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
   // accepted if no pair is worse than 1e-10 (reported as not converged otherwise)
   const double tol = 1.0e-15 * (double)max(p, 8);
   const double tol2 = tol * tol;
+  // squared column norms: exact at the start of every sweep, then carried
+  // through the sweep's rotations by alpha' = alpha - w|g|^2, beta' =
+  // beta + w|g|^2 (so the rounds only need a^H b); the singular values the
+  // callers use come from the columns themselves after the last sweep
+  __shared__ double cn2[LA_MAXP];
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) *sh_flag = 0;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      const cd* col = L + (size_t)c * ld;
+      double s = 0.0;
+      for (int i = 0; i < p; ++i) s = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, s));
+      cn2[c] = s;
+    }
     __syncthreads();
     for (int t = 0; t < mp - 1; ++t) {
       // the bound is uniform over a warp, so every lane reaches the shuffles
@@ -293,22 +304,19 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
         }
         cd* ca = L + (size_t)a * ld;
         cd* cb = L + (size_t)b * ld;
-        double al = 0.0, be = 0.0, gx = 0.0, gy = 0.0;
+        double gx = 0.0, gy = 0.0;
         if (live)
           for (int i = sub; i < p; i += G) {
             const cd x = ca[i], y = cb[i];
-            al = fma(x.x, x.x, fma(x.y, x.y, al));
-            be = fma(y.x, y.x, fma(y.y, y.y, be));
             gx = fma(x.x, y.x, fma(x.y, y.y, gx));
             gy = fma(x.x, y.y, fma(-x.y, y.x, gy));
           }
         for (int o = G >> 1; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
           gx += __shfl_xor_sync(0xffffffffu, gx, o);
           gy += __shfl_xor_sync(0xffffffffu, gy, o);
         }
         if (!live) continue;
+        const double al = cn2[a], be = cn2[b];
         const double g2 = fma(gx, gx, gy * gy);
         const double ab = al * be;
         if (g2 > tol2 * ab && g2 > 1e-290) {
@@ -328,12 +336,18 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
           const double c = rsqrt(fma(w * w, G2, 1.0));
           const double cw = c * w;
           const double spx = cw * sx, spy = -cw * sy;           // sp = c w conj(g)
+          // w|g|^2 in true units (w G2 carries one factor of the scaling)
+          const double dn = (big > 1e140) ? w * G2 * big : w * G2;
           for (int i = sub; i < p; i += G) {
             const cd x = ca[i], y = cb[i];
             ca[i] = mkc(fma(c, x.x, -fma(spx, y.x, -spy * y.y)), fma(c, x.y, -fma(spx, y.y, spy * y.x)));
             cb[i] = mkc(fma(c, y.x, fma(spx, x.x, spy * x.y)), fma(c, y.y, fma(spx, x.y, -spy * x.x)));
           }
-          if (sub == 0) atomicOr(sh_flag, (g2 > 1e-16 * ab) ? 7 : (g2 > 1e-20 * ab) ? 3 : 1);
+          if (sub == 0) {
+            cn2[a] = fmax(al - dn, 0.0);
+            cn2[b] = be + dn;
+            atomicOr(sh_flag, (g2 > 1e-16 * ab) ? 7 : (g2 > 1e-20 * ab) ? 3 : 1);
+          }
         }
       }
       __syncthreads();
