@@ -23,7 +23,6 @@ __device__ __forceinline__ cd* core_ptr(cd* base, int core_stride, int s) {
   return base + (size_t)s * core_stride;
 }
 
-#define SVD_WCAP(hb) ((LA_MAXP + (hb)) * LA_MAXP)
 
 struct SvdSmem {
   cd* W;
@@ -356,7 +355,7 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
 // sets *over when the rank wanted more than rmax columns.
 // Pivoting Z and pivoting R of Z = Q R choose the same columns, so the rank
 // is the one a rank-revealing QR of the supercore gives.
-__device__ int dominant_basis(const cd* Z, int q, int p, SvdSmem& sm, int hb, double ctol, int rmax,
+__device__ int cross_pick_columns(const cd* Z, int q, int p, SvdSmem& sm, int hb, double ctol, int rmax,
                               int* piv, int* iw, double* red_d, int* red_i, bool* over, double* fl) {
   __shared__ int perm_[LA_MAXP];
   (void)hb;
@@ -457,7 +456,7 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
         __syncthreads();
         evals += (double)p * q;
         bool over;
-        int k = dominant_basis(Z, q, p, sm, hb, ctol, rmax, piv, iw, red_d, red_i, &over, &fl);
+        int k = cross_pick_columns(Z, q, p, sm, hb, ctol, rmax, piv, iw, red_d, red_i, &over, &fl);
         if (over) {
           if (rmax < rmax_i) {
             hand_off = true;
@@ -485,7 +484,7 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
         __syncthreads();
         evals += (double)p * q;
         bool over;
-        int k = dominant_basis(Z, q, p, sm, hb, ctol, rmax, piv, iw, red_d, red_i, &over, &fl);
+        int k = cross_pick_columns(Z, q, p, sm, hb, ctol, rmax, piv, iw, red_d, red_i, &over, &fl);
         if (over) {
           if (rmax < rmax_i) {
             hand_off = true;
