@@ -29,6 +29,24 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) of one tier-1 k_zipup launch on the default
+# 4096-instance batch, from a one-pass ncu capture of that launch
+# (dram__bytes_read.sum 49,275,904 + dram__bytes_write.sum 915,309,312).
+# The figure holds while the kernel's sources hash to "src"; after any change
+# to them the roofline reports traffic as null until it is captured again.
+ZIPUP_TRAFFIC = {"bytes": 49275904 + 915309312, "instances": 4096, "src": "289ffd2ac97da178"}
+KERNEL_SRCS = ("cplx.cuh", "kernels.cuh", "la.cuh", "model.cuh", "tt_kernels.cu")
+
+
+def kernel_src_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SRCS:
+        with open(os.path.join(ROOT, "paper_2607_28435_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 METRIC = "priced strikes/s at <=1e-6*S0 err: batched TT-SFFT vs dense-FFT Carr-Madan, 1 B300"
 UNIT = "strikes/s"
 
@@ -48,9 +66,8 @@ def parse():
 
 # --------------------------------------------------------------------------- CPU oracle
 def _oracle_task(args):
-    """Price one instance with the CPU oracle (direct sum at its strikes)."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    import numpy as np
+    """Price strikes lb + st*i (i < q) of one instance with the CPU oracle
+    (direct sum at each strike)."""
     from oracle import carr_madan as cm
     from paper_2607_28435_b300 import workloads as wl
     prob, (lb, st, q) = args
@@ -60,36 +77,89 @@ def _oracle_task(args):
     return q, time.perf_counter() - t0
 
 
-def oracle_sample(pool, problems, strikes, seconds, cores, one_core=False):
-    """Run the oracle on consecutive instances of the batch (skipping those
-    whose integrand support exceeds 2^20 points, where a direct sum would take
-    minutes) until about `seconds` of wall time; returns strikes/s."""
+def _oracle_pieces(problems, strikes, skipped, seed=0):
+    """Instances of the batch in a seeded random order, one piece each: its
+    first max(32, 2^24 / support) strikes (all of them for small supports), so
+    that no task runs much longer than a second. Instances whose support
+    exceeds 2^20 points are counted in skipped[0] and left out (a direct sum
+    there takes minutes per strike set). Yields (index, task)."""
+    import numpy as np
     from oracle import carr_madan as cm
-    tasks = []
-    skipped = 0
-    for p, s in zip(problems, strikes):
-        if cm.support_limit(p) > (1 << 20):
-            skipped += 1
+    for i in np.random.default_rng(seed).permutation(len(problems)):
+        p, (lb, st, q) = problems[i], strikes[i]
+        m = cm.support_limit(p)
+        if m > (1 << 20):
+            skipped[0] += 1
             continue
-        tasks.append((p, s))
-        if len(tasks) >= 4 * cores:
-            break
+        yield int(i), (p, (lb, st, min(q, max(32, (1 << 24) // m))))
+
+
+def oracle_sample(pool, problems, strikes, seconds, cores):
+    """Time the oracle on a bounded sample of the batch. Each sampled instance
+    prices one piece of its strikes; its whole cost is that piece's time
+    scaled by its strike count (the direct sum costs the same at every strike
+    of an instance). Workers take the next piece as soon as they are free,
+    until about `seconds` of wall time (pieces in flight then finish).
+    Returns (rate on the pool, rate on one core, instances, skipped, wall,
+    strikes timed): one-core rate = sum q_i / sum t_i q_i / piece_i, and the
+    pool's rate multiplies it by the concurrency the pool reached (summed
+    piece seconds over wall)."""
+    skipped = [0]
+    it = _oracle_pieces(problems, strikes, skipped)
     t0 = time.perf_counter()
-    done_q = 0
-    done_n = 0
-    busy = 0.0  # summed per-task seconds: what one core alone would take
-    it = iter(tasks)
-    while time.perf_counter() - t0 < seconds:
-        chunk = [t for _, t in zip(range(cores), it)]
-        if not chunk:
-            break
-        for q, dt in pool.map(_oracle_task, chunk):
-            done_q += q
-            done_n += 1
+    pend = {}
+    q_all = 0       # strikes of the sampled instances
+    t_all = 0.0     # their estimated one-core seconds
+    busy = 0.0      # summed piece seconds
+    timed = 0       # strikes actually priced
+    n_inst = 0
+
+    def submit():
+        nxt = next(it, None)
+        if nxt is not None:
+            i, task = nxt
+            pend[pool.apply_async(_oracle_task, (task,))] = i
+
+    for _ in range(cores):
+        submit()
+    while pend:
+        ready = [r for r in pend if r.ready()]
+        if not ready:
+            time.sleep(0.002)
+            continue
+        for r in ready:
+            i = pend.pop(r)
+            qp, dt = r.get()
+            q = strikes[i][2]
+            q_all += q
+            t_all += dt * q / qp
             busy += dt
+            timed += qp
+            n_inst += 1
+            if time.perf_counter() - t0 < seconds:
+                submit()
     wall = time.perf_counter() - t0
-    one_rate = done_q / busy if (one_core and busy > 0) else None
-    return done_q / wall, done_n, skipped, wall, one_rate
+    one = q_all / t_all if t_all > 0 else 0.0
+    return one * busy / wall, one, n_inst, skipped[0], wall, timed
+
+
+def oracle_pool(ncores):
+    """A spawned pool of `ncores` single-threaded workers: the thread-count
+    variables are set before the spawn so that each worker's numpy starts with
+    one thread and the pool does not oversubscribe the cores."""
+    import multiprocessing as mp
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        return mp.get_context("spawn").Pool(ncores)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 # --------------------------------------------------------------------------- clocks
@@ -260,6 +330,9 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
     dms = prof[dom]["ms"]
     achieved = prof[dom]["flops"] / (dms * 1e-3) / 1e9 if dms > 0 else 0.0
     launches = sum(v["launches"] for v in prof.values())
+    traffic = None
+    if dom == "zipup" and args.count == ZIPUP_TRAFFIC["instances"] and kernel_src_hash() == ZIPUP_TRAFFIC["src"]:
+        traffic = ZIPUP_TRAFFIC["bytes"]
 
     # dense-FFT baseline on the same batch: one instance per n <= 30 timed,
     # the batch time assembled from the per-n times
@@ -269,13 +342,15 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
 
     cpu = None
     if pool is not None and rank == 0:
-        rate, n_inst, skipped, wall, one_rate = oracle_sample(pool, problems, strikes, args.cpu_seconds,
-                                                              ncores, one_core=True)
+        rate, one_rate, n_inst, skipped, wall, timed = oracle_sample(pool, problems, strikes,
+                                                                     args.cpu_seconds, ncores)
         cpu = {"value": rate, "unit": UNIT, "cores": ncores, "kind": "oracle", "one_core_value": one_rate,
-               "sample": f"{n_inst} consecutive instances of the batch at all their strikes "
-                         f"(direct sum over the integrand support, {wall:.1f} s wall; "
-                         f"{skipped} instances with support > 2^20 skipped; one_core_value = the same "
-                         f"strikes over the summed per-instance seconds)"}
+               "sample": f"{n_inst} instances of the batch in a seeded random order, each timed on "
+                         f"its first max(32, 2^24/support) strikes ({timed} strikes, direct sum over "
+                         f"the integrand support, {wall:.1f} s wall) and scaled to all its strikes; "
+                         f"{skipped} drawn instances with support > 2^20 left out; one_core_value = "
+                         f"strikes over the summed scaled seconds, value = that times the pool's "
+                         f"measured concurrency"}
 
     phases = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                   "gflop_per_step": v["flops"] / args.steps / 1e9}
@@ -300,7 +375,8 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
         "gpu_launches": launches // args.steps,
         "roofline": {"bound": "alu", "kernel": sfft.PHASE_KERNELS[sfft.PHASE_NAMES.index(dom)],
                      "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s FP64",
-                     "frac": achieved / fp64_peak if fp64_peak else None, "traffic": None,
+                     "frac": achieved / fp64_peak if fp64_peak else None, "traffic": traffic,
+                     "traffic_unit": "bytes per tier-1 launch (ncu, dram read + write)",
                      "peak_source": "measured FP64 FMA calibration (sfft_calibrate_fp64)"},
         "phases": phases,
         # secondary, as the metric's definition asks: grid points the priced
@@ -404,8 +480,8 @@ def run_reference(args, pool, ncores):
     strikes = [cm.strike_window(p) for p in problems]
     rates = []
     for i in range(args.warmup + args.steps):
-        rate, n_inst, skipped, wall, _ = oracle_sample(pool, problems, strikes,
-                                                        max(3.0, args.cpu_seconds / 3), ncores)
+        rate, _, n_inst, skipped, wall, timed = oracle_sample(pool, problems, strikes,
+                                                              max(3.0, args.cpu_seconds / 3), ncores)
         if i >= args.warmup:
             rates.append(rate)
     value = statistics.mean(rates)
@@ -415,8 +491,10 @@ def run_reference(args, pool, ncores):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": f"batched TT-SFFT, {args.count} instances (Heston/Merton/VG), n 16..34"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
-                         "sample": f"{n_inst} instances per step (direct sum over the support), "
-                                   f"{skipped} with support > 2^20 skipped"},
+                         "sample": f"per step, {n_inst} instances in a seeded random order, each timed on "
+                                   f"its first max(32, 2^24/support) strikes and scaled to all its strikes "
+                                   f"(direct sum over the support); {skipped} drawn instances with support "
+                                   f"> 2^20 left out"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -429,8 +507,7 @@ def main():
     ncores = len(os.sched_getaffinity(0))
     pool = None
     if rank == 0 and (args.impl == "reference" or not args.no_cpu):
-        import multiprocessing as mp
-        pool = mp.get_context("spawn").Pool(ncores)
+        pool = oracle_pool(ncores)
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args, pool, ncores)), flush=True)

@@ -64,6 +64,9 @@ struct sfft_ctx {
   int device = 0;
   int num_sms = 0;
   cudaStream_t stream = nullptr;
+  // the TT-SVD builder runs here, forked from and joined back to `stream`
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   std::string err;
   // MPO cache (pool of fixed-size slots)
   DevBuf mpo_pool;
@@ -507,77 +510,92 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   b.counters = ctr;
   const size_t smem = svd_smem();
   // hand-off lists of the two-tier launches: [count, instances...]
-  int *defer_build, *defer_round;
+  int *defer_build, *defer_round, *defer_cross;
   if ((s = ensure(ctx, "defer_build", sizeof(int) * (cnt + 1), &p))) return s;
   defer_build = reinterpret_cast<int*>(p);
   if ((s = ensure(ctx, "defer_round", sizeof(int) * (cnt + 1), &p))) return s;
   defer_round = reinterpret_cast<int*>(p);
+  if ((s = ensure(ctx, "defer_cross", sizeof(int) * (cnt + 1), &p))) return s;
+  defer_cross = reinterpret_cast<int*>(p);
   CK(cudaMemsetAsync(defer_build, 0, sizeof(int), ctx->stream));
   CK(cudaMemsetAsync(defer_round, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(defer_cross, 0, sizeof(int), ctx->stream));
+  // TT-SVD builder: tier 1 panels up to kSmallP columns in 128-thread CTAs,
+  // several per SM; tier 2 the full carve for the instances tier 1 handed on
+  const size_t bsmem1 = la::ts_svd_smem_bytes(kSmallP, kSmallP) + 256;
+  const int bgrid1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, bsmem1,
+                                                                kThreadsSmall));
+  const int bgrid2 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem));
+  const long long sstride = 2LL << kSvdMaxBits;
+  if ((s = ensure(ctx, "build_scratch", sizeof(cd) * sstride * std::max(bgrid1, bgrid2), &p))) return s;
+  cd* build_scratch = reinterpret_cast<cd*>(p);
+  // cross builder: tier 1 ranks up to kCrossSmallR in 128-thread CTAs, every
+  // instance in flight at once; tier 2 the rest; then the rounding of the
+  // interpolatory cores
+  const int xp = 2 * kCrossSmallR;
+  const int xhb = kCrossSmallHb;
+  const size_t xsmem1 = la::ts_svd_smem_bytes(xp, xhb) + 256;
+  const int xgrid1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_cross, xsmem1,
+                                                                kThreadsSmall));
+  const int xgrid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_cross, smem));
+  if ((s = ensure(ctx, "cross_scratch", sizeof(cd) * (size_t)4096 * std::max(xgrid1, xgrid), &p))) return s;
+  cd* cross_scratch = reinterpret_cast<cd*>(p);
+  const RoundSmem xrs = round_smem(2);
+  const int xgrid_r = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, xrs.bytes));
+  if ((s = ensure(ctx, "xround_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * xgrid_r, &p))) return s;
+  cd* xround_scratch = reinterpret_cast<cd*>(p);
+
+  // The two builders take disjoint instances. The cross builder (a few long
+  // instances, one per CTA) goes first on the caller's stream, where nothing
+  // delays its dispatch; the TT-SVD builder follows on the side stream behind
+  // the fork event, and its persistent CTAs fill every slot the cross CTAs
+  // leave or free. (The other order lets the TT-SVD CTAs take every SM first
+  // and pushes the cross builder behind them.)
+  CK(cudaEventRecord(ctx->fork, ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
   {
-    // TT-SVD builder. tier 1: panels up to kSmallP columns, 128-thread CTAs,
-    // several per SM; tier 2: the full carve for the instances tier 1 handed
-    // on. The list length is read on the device (list_counts[0]).
-    const size_t smem1 = la::ts_svd_smem_bytes(kSmallP, kSmallP) + 256;
-    const int grid1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem1,
-                                                                 kThreadsSmall));
-    const int grid2 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem));
-    const long long sstride = 2LL << kSvdMaxBits;
-    if ((s = ensure(ctx, "build_scratch", sizeof(cd) * sstride * std::max(grid1, grid2), &p))) return s;
-    {
-      PhaseScope ps(ctx, PH_BUILD);
-      k_integrand_ttsvd<<<grid1, kThreadsSmall, smem1, ctx->stream>>>(
-          b.P, m_dev, svd_dev, cnt, ctr + 0, reinterpret_cast<cd*>(p), sstride, b.A, b.a_off,
-          SFFT_CORE_STRIDE_D2, b.a_ranks, b.status, kSmallP, acc_ptr(ctx), kSmallP, defer_build, list_counts);
-    }
-    CK(cudaGetLastError());
-    PhaseScope ps(ctx, PH_BUILD);
-    k_integrand_ttsvd<<<grid2, kThreads, smem, ctx->stream>>>(
-        b.P, m_dev, defer_build + 1, 0, ctr + 7, reinterpret_cast<cd*>(p), sstride, b.A, b.a_off,
-        SFFT_CORE_STRIDE_D2, b.a_ranks, b.status, kHb, acc_ptr(ctx), LA_MAXP, nullptr, defer_build);
-  }
-  CK(cudaGetLastError());
-  {
-    // cross builder (list_counts[1] instances): tier 1 ranks up to
-    // kCrossSmallR in 128-thread CTAs, every instance in flight at once;
-    // tier 2 the rest; then the rounding of the interpolatory cores
-    int* defer_cross;
-    if ((s = ensure(ctx, "defer_cross", sizeof(int) * (cnt + 1), &p))) return s;
-    defer_cross = reinterpret_cast<int*>(p);
-    CK(cudaMemsetAsync(defer_cross, 0, sizeof(int), ctx->stream));
-    const int xp = 2 * kCrossSmallR;
-    const int xhb = kCrossSmallHb;
-    const size_t smem1 = la::ts_svd_smem_bytes(xp, xhb) + 256;
-    const int grid1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_cross, smem1,
-                                                                 kThreadsSmall));
-    const int grid = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_cross, smem));
-    if ((s = ensure(ctx, "cross_scratch", sizeof(cd) * (size_t)4096 * std::max(grid1, grid), &p))) return s;
-    {
-      PhaseScope ps(ctx, PH_CROSS);
-      k_integrand_cross<<<grid1, kThreadsSmall, smem1, ctx->stream>>>(
-          b.P, cross_dev, cnt, ctr + 1, reinterpret_cast<cd*>(p), 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
-          b.a_ranks, b.status, xhb, acc_ptr(ctx), kCrossSweeps, xp, kCrossSmallR, defer_cross, list_counts + 1);
-    }
-    CK(cudaGetLastError());
-    {
-      PhaseScope ps(ctx, PH_CROSS);
-      k_integrand_cross<<<grid, kThreads, smem, ctx->stream>>>(
-          b.P, defer_cross + 1, 0, ctr + 10, reinterpret_cast<cd*>(p), 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
-          b.a_ranks, b.status, kHb, acc_ptr(ctx), kCrossSweeps, LA_MAXP, CROSS_RANK_CAP, nullptr, defer_cross);
-    }
-    CK(cudaGetLastError());
-    // interpolatory cores -> right-orthonormal, truncated to tol
-    const RoundSmem rs = round_smem(2);
-    const int g2 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, rs.bytes));
-    if ((s = ensure(ctx, "xround_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * g2, &p))) return s;
     PhaseScope ps(ctx, PH_CROSS);
-    k_tt_round<<<g2, kThreads, rs.bytes, ctx->stream>>>(cross_dev, cnt, ctr + 2, b.n_arr, 2, 1, b.tol_arr,
-                                                        b.maxr_arr, b.A, b.a_off, SFFT_CORE_STRIDE_D2, b.a_ranks,
-                                                        reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH, b.status,
-                                                        rs.hb, acc_ptr(ctx), PH_CROSS, rs.pmax, rs.vcap, nullptr,
-                                                        list_counts + 1);
+    k_integrand_cross<<<xgrid1, kThreadsSmall, xsmem1, ctx->stream>>>(
+        b.P, cross_dev, cnt, ctr + 1, cross_scratch, 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2, b.a_ranks,
+        b.status, xhb, acc_ptr(ctx), kCrossSweeps, xp, kCrossSmallR, defer_cross, list_counts + 1);
   }
-  CK(cudaGetLastError());
+  {
+    PhaseScope ps(ctx, PH_CROSS);
+    k_integrand_cross<<<xgrid, kThreads, smem, ctx->stream>>>(
+        b.P, defer_cross + 1, 0, ctr + 10, cross_scratch, 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2, b.a_ranks,
+        b.status, kHb, acc_ptr(ctx), kCrossSweeps, LA_MAXP, CROSS_RANK_CAP, nullptr, defer_cross);
+  }
+  {
+    // interpolatory cores -> right-orthonormal, truncated to tol
+    PhaseScope ps(ctx, PH_CROSS);
+    k_tt_round<<<xgrid_r, kThreads, xrs.bytes, ctx->stream>>>(
+        cross_dev, cnt, ctr + 2, b.n_arr, 2, 1, b.tol_arr, b.maxr_arr, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
+        b.a_ranks, xround_scratch, SFFT_ROUND_SCRATCH, b.status, xrs.hb, acc_ptr(ctx), PH_CROSS, xrs.pmax,
+        xrs.vcap, nullptr, list_counts + 1);
+  }
+  const cudaError_t main_err = cudaGetLastError();
+  cudaStream_t main_stream = ctx->stream;
+  ctx->stream = ctx->side;
+  {
+    PhaseScope ps(ctx, PH_BUILD);
+    k_integrand_ttsvd<<<bgrid1, kThreadsSmall, bsmem1, ctx->stream>>>(
+        b.P, m_dev, svd_dev, cnt, ctr + 0, build_scratch, sstride, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
+        b.a_ranks, b.status, kSmallP, acc_ptr(ctx), kSmallP, defer_build, list_counts);
+  }
+  {
+    PhaseScope ps(ctx, PH_BUILD);
+    k_integrand_ttsvd<<<bgrid2, kThreads, smem, ctx->stream>>>(
+        b.P, m_dev, defer_build + 1, 0, ctr + 7, build_scratch, sstride, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
+        b.a_ranks, b.status, kHb, acc_ptr(ctx), LA_MAXP, nullptr, defer_build);
+  }
+  const cudaError_t side_err = cudaGetLastError();
+  ctx->stream = main_stream;
+  // join before anything else can fail, so no side-stream work is left
+  // outside the caller's stream order (or open in a capture)
+  CK(cudaEventRecord(ctx->join, ctx->side));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->join, 0));
+  CK(side_err);
+  CK(main_err);
   if (!apply) return SFFT_OK;
 
   // MPO per instance
@@ -775,8 +793,12 @@ sfft_status sfft_create(sfft_ctx** out, int device) {
   }
   ctx->num_sms = prop.multiProcessorCount;
   sfft_status s = set_smem_attrs(ctx);
+  if (!s && (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) != cudaSuccess ||
+             cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming) != cudaSuccess))
+    s = SFFT_ECUDA;
   if (s) {
-    delete ctx;
+    sfft_destroy(ctx);
     return s;
   }
   *out = ctx;
@@ -787,12 +809,16 @@ sfft_status sfft_destroy(sfft_ctx* ctx) {
   if (!ctx) return SFFT_OK;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->side) cudaStreamSynchronize(ctx->side);
   for (auto& kv : ctx->bufs) kv.second.release();
   for (auto& e : ctx->ev_open) {
     cudaEventDestroy(e.second.first);
     cudaEventDestroy(e.second.second);
   }
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
+  if (ctx->join) cudaEventDestroy(ctx->join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->prof_acc) cudaFree(ctx->prof_acc);
   ctx->mpo_pool.release();
   ctx->mpo_ranks_dev.release();
