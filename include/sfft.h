@@ -19,8 +19,11 @@
  *     device (for example torch.cuda tensors' data_ptr()); pointers marked
  *     "host" are ordinary host memory. The caller owns every buffer it passes.
  *   - Device work is stream-ordered on the stream set with sfft_set_stream
- *     (default: the legacy default stream). Calls that return per-instance
- *     status synchronise that stream before returning.
+ *     (default: the legacy default stream). Inside sfft_price_batch the
+ *     TT-SVD builder runs on a stream of the context's own, forked from and
+ *     joined back to that stream by events, so the call's work as a whole
+ *     stays ordered on it. Calls that return per-instance status
+ *     synchronise that stream before returning.
  *   - Invalid arguments are rejected on the host before any launch
  *     (SFFT_EINVAL); the text of the last error is sfft_last_error(ctx).
  *   - A context is used by one host thread at a time.
