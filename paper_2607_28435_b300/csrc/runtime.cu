@@ -301,85 +301,20 @@ sfft_status set_smem_attrs(sfft_ctx* ctx) {
 }
 
 // MPO of Q_n at tolerance tol: cached; built by k_mpo_interp + k_tt_round.
-sfft_status get_mpo(sfft_ctx* ctx, int n, double tol, const MpoEntry** out) {
+sfft_status build_mpos(sfft_ctx* ctx, const std::vector<std::pair<int, double>>& want);
+
+const MpoEntry* find_mpo(const sfft_ctx* ctx, int n, double tol) {
   for (const auto& e : ctx->mpos)
-    if (e.n == n && e.tol == tol) {
-      *out = &e;
-      return SFFT_OK;
-    }
-  const long long slot = (long long)SFFT_MAX_N * SFFT_CORE_STRIDE_D4;
-  if ((int)ctx->mpos.size() >= ctx->mpo_slots) {
-    // grow the pool (copy existing entries)
-    const int nslots = std::max(16, ctx->mpo_slots * 2);
-    void* np = nullptr;
-    void* nr = nullptr;
-    CK(cudaMalloc(&np, sizeof(cd) * slot * nslots));
-    CK(cudaMalloc(&nr, sizeof(int) * (SFFT_MAX_N + 1) * nslots));
-    if (ctx->mpo_slots) {
-      CK(cudaMemcpyAsync(np, ctx->mpo_pool.p, sizeof(cd) * slot * ctx->mpo_slots,
-                         cudaMemcpyDeviceToDevice, ctx->stream));
-      CK(cudaMemcpyAsync(nr, ctx->mpo_ranks_dev.p, sizeof(int) * (SFFT_MAX_N + 1) * ctx->mpo_slots,
-                         cudaMemcpyDeviceToDevice, ctx->stream));
-      CK(cudaStreamSynchronize(ctx->stream));
-    }
-    ctx->mpo_pool.release();
-    ctx->mpo_ranks_dev.release();
-    ctx->mpo_pool.p = np;
-    ctx->mpo_pool.bytes = sizeof(cd) * slot * nslots;
-    ctx->mpo_ranks_dev.p = nr;
-    ctx->mpo_ranks_dev.bytes = sizeof(int) * (SFFT_MAX_N + 1) * nslots;
-    ctx->mpo_slots = nslots;
+    if (e.n == n && e.tol == tol) return &e;
+  return nullptr;
+}
+
+sfft_status get_mpo(sfft_ctx* ctx, int n, double tol, const MpoEntry** out) {
+  if (!(*out = find_mpo(ctx, n, tol))) {
+    sfft_status s = build_mpos(ctx, {{n, tol}});
+    if (s) return s;
+    *out = find_mpo(ctx, n, tol);
   }
-  const int idx = (int)ctx->mpos.size();
-  MpoEntry e;
-  e.idx = idx;
-  e.n = n;
-  e.tol = tol;
-  e.off = slot * idx;
-  cd* W = reinterpret_cast<cd*>(ctx->mpo_pool.p) + e.off;
-  int* rk = reinterpret_cast<int*>(ctx->mpo_ranks_dev.p) + (SFFT_MAX_N + 1) * idx;
-  {
-    PhaseScope ps(ctx, PH_MPO);
-    k_mpo_interp<<<n, kThreads, 0, ctx->stream>>>(n, SFFT_MPO_NODES, W, SFFT_CORE_STRIDE_D4, rk);
-  }
-  CK(cudaGetLastError());
-  // round: one instance, d = 4, with left orthogonalisation
-  struct H {
-    int n;
-    double tol;
-    int maxr;
-    long long off;
-  } h = {n, tol, SFFT_SLOT_RANK_DEV, 0};
-  void* hb;
-  sfft_status s = ensure(ctx, "mpo_args", 64, &hb);
-  if (s) return s;
-  char* a = reinterpret_cast<char*>(hb);
-  CK(cudaMemcpyAsync(a, &h.n, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(a + 8, &h.tol, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(a + 16, &h.maxr, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(a + 24, &h.off, sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
-  void* scr;
-  s = ensure(ctx, "mpo_scratch", sizeof(cd) * SFFT_ROUND_SCRATCH, &scr);
-  if (s) return s;
-  {
-    PhaseScope ps(ctx, PH_MPO);
-    const RoundSmem rs = round_smem(4);
-    k_tt_round<<<1, kThreads, rs.bytes, ctx->stream>>>(
-        nullptr, 1, nullptr, reinterpret_cast<int*>(a), 4, 1, reinterpret_cast<double*>(a + 8),
-        reinterpret_cast<int*>(a + 16), W, reinterpret_cast<long long*>(a + 24), SFFT_CORE_STRIDE_D4,
-        rk, reinterpret_cast<cd*>(scr), SFFT_ROUND_SCRATCH, nullptr, rs.hb, acc_ptr(ctx), PH_MPO,
-        rs.pmax, rs.vcap, nullptr, nullptr);
-  }
-  CK(cudaGetLastError());
-  e.ranks.resize(SFFT_MAX_N + 1);
-  CK(cudaMemcpyAsync(e.ranks.data(), rk, sizeof(int) * (SFFT_MAX_N + 1), cudaMemcpyDeviceToHost,
-                     ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  for (int i = 0; i <= n; ++i)
-    if (e.ranks[i] < 1 || e.ranks[i] > SFFT_SLOT_RANK_DEV)
-      return set_err(ctx, SFFT_ERANK, "MPO rank %d at bond %d", e.ranks[i], i);
-  ctx->mpos.push_back(e);
-  *out = &ctx->mpos.back();
   return SFFT_OK;
 }
 
@@ -412,6 +347,104 @@ sfft_status upload(sfft_ctx* ctx, const char* name, const std::vector<T>& v, T**
   if (s) return s;
   if (!v.empty() && (s = h2d(ctx, p, v.data(), sizeof(T) * v.size(), strcmp(name, "P") == 0))) return s;
   *out = reinterpret_cast<T*>(p);
+  return SFFT_OK;
+}
+
+// Build every (n, tol) MPO of `want` that is not cached yet. Each new MPO
+// gets its interpolation launch; then one k_tt_round launch rounds all of
+// them side by side (one CTA per MPO, d = 4, with left orthogonalisation),
+// and one read-back fetches their ranks.
+sfft_status build_mpos(sfft_ctx* ctx, const std::vector<std::pair<int, double>>& want) {
+  std::vector<std::pair<int, double>> miss;
+  for (const auto& w : want)
+    if (!find_mpo(ctx, w.first, w.second) && std::find(miss.begin(), miss.end(), w) == miss.end())
+      miss.push_back(w);
+  if (miss.empty()) return SFFT_OK;
+  const long long slot = (long long)SFFT_MAX_N * SFFT_CORE_STRIDE_D4;
+  const int first = (int)ctx->mpos.size();
+  const int nm = (int)miss.size();
+  const int tot = first + nm;
+  if (tot > ctx->mpo_slots) {
+    // grow the pool (copy existing entries)
+    const int nslots = std::max(tot, std::max(16, ctx->mpo_slots * 2));
+    void* np = nullptr;
+    void* nr = nullptr;
+    CK(cudaMalloc(&np, sizeof(cd) * slot * nslots));
+    CK(cudaMalloc(&nr, sizeof(int) * (SFFT_MAX_N + 1) * nslots));
+    if (ctx->mpo_slots) {
+      CK(cudaMemcpyAsync(np, ctx->mpo_pool.p, sizeof(cd) * slot * ctx->mpo_slots,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(nr, ctx->mpo_ranks_dev.p, sizeof(int) * (SFFT_MAX_N + 1) * ctx->mpo_slots,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
+    ctx->mpo_pool.release();
+    ctx->mpo_ranks_dev.release();
+    ctx->mpo_pool.p = np;
+    ctx->mpo_pool.bytes = sizeof(cd) * slot * nslots;
+    ctx->mpo_ranks_dev.p = nr;
+    ctx->mpo_ranks_dev.bytes = sizeof(int) * (SFFT_MAX_N + 1) * nslots;
+    ctx->mpo_slots = nslots;
+  }
+  cd* pool = reinterpret_cast<cd*>(ctx->mpo_pool.p);
+  int* rk = reinterpret_cast<int*>(ctx->mpo_ranks_dev.p);
+  // rounding arguments indexed by pool slot; the list names the new slots
+  std::vector<int> n_v(tot, 0), maxr_v(tot, SFFT_SLOT_RANK_DEV), list(nm);
+  std::vector<double> tol_v(tot, 0.0);
+  std::vector<long long> off_v(tot);
+  for (int i = 0; i < tot; ++i) off_v[i] = slot * i;
+  for (int k = 0; k < nm; ++k) {
+    const int idx = first + k;
+    n_v[idx] = miss[k].first;
+    tol_v[idx] = miss[k].second;
+    list[k] = idx;
+  }
+  int *n_d, *maxr_d, *list_d;
+  double* tol_d;
+  long long* off_d;
+  sfft_status s;
+  if ((s = upload(ctx, "mpo_n", n_v, &n_d)) || (s = upload(ctx, "mpo_maxr", maxr_v, &maxr_d)) ||
+      (s = upload(ctx, "mpo_list", list, &list_d)) || (s = upload(ctx, "mpo_tol", tol_v, &tol_d)) ||
+      (s = upload(ctx, "mpo_off", off_v, &off_d)))
+    return s;
+  void* p;
+  if ((s = ensure(ctx, "mpo_counter", sizeof(int), &p))) return s;
+  int* ctr = reinterpret_cast<int*>(p);
+  CK(cudaMemsetAsync(ctr, 0, sizeof(int), ctx->stream));
+  for (int k = 0; k < nm; ++k) {
+    const int idx = first + k;
+    PhaseScope ps(ctx, PH_MPO);
+    k_mpo_interp<<<n_v[idx], kThreads, 0, ctx->stream>>>(n_v[idx], SFFT_MPO_NODES, pool + off_v[idx],
+                                                         SFFT_CORE_STRIDE_D4, rk + (SFFT_MAX_N + 1) * idx);
+  }
+  CK(cudaGetLastError());
+  const RoundSmem rs = round_smem(4);
+  const int grid = std::min(nm, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, rs.bytes));
+  if ((s = ensure(ctx, "mpo_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * grid, &p))) return s;
+  {
+    PhaseScope ps(ctx, PH_MPO);
+    k_tt_round<<<grid, kThreads, rs.bytes, ctx->stream>>>(
+        list_d, nm, ctr, n_d, 4, 1, tol_d, maxr_d, pool, off_d, SFFT_CORE_STRIDE_D4, rk,
+        reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH, nullptr, rs.hb, acc_ptr(ctx), PH_MPO, rs.pmax,
+        rs.vcap, nullptr, nullptr);
+  }
+  CK(cudaGetLastError());
+  std::vector<int> rr((size_t)(SFFT_MAX_N + 1) * nm);
+  CK(cudaMemcpyAsync(rr.data(), rk + (size_t)(SFFT_MAX_N + 1) * first, sizeof(int) * rr.size(),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int k = 0; k < nm; ++k) {
+    MpoEntry e;
+    e.idx = first + k;
+    e.n = miss[k].first;
+    e.tol = miss[k].second;
+    e.off = off_v[e.idx];
+    e.ranks.assign(rr.begin() + (size_t)(SFFT_MAX_N + 1) * k, rr.begin() + (size_t)(SFFT_MAX_N + 1) * (k + 1));
+    for (int i = 0; i <= e.n; ++i)
+      if (e.ranks[i] < 1 || e.ranks[i] > SFFT_SLOT_RANK_DEV)
+        return set_err(ctx, SFFT_ERANK, "MPO rank %d at bond %d", e.ranks[i], i);
+    ctx->mpos.push_back(e);
+  }
   return SFFT_OK;
 }
 
@@ -1145,6 +1178,11 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
       }
     }
     return finish_status(ctx, count, valid, host_status, st_dev, inst_status, info, nullptr, nullptr);
+  }
+  {
+    std::vector<std::pair<int, double>> want;
+    for (const auto& P : prm) want.push_back({P.n, P.tol});
+    if ((s = build_mpos(ctx, want))) return s;
   }
   std::vector<const MpoEntry*> mp(cnt);
   for (int k = 0; k < cnt; ++k) {
