@@ -15,6 +15,8 @@ Transform Approaches for Large-Scale Carr-Madan Option Pricing"):
   tt.py            tensor-train toolkit on dense numpy arrays (Sec. 3.1):
                    TT-SVD, rounding, contraction, the bit-reversed DFT operator
                    Q_n of Sec. 3.2 written out densely
+  mlp.py           the price surrogate's network (not in the paper): forward,
+                   mean squared error, backpropagation, Adam, bfloat16 rounding
 
 Only tests, the smoke check and the bench's CPU-baseline leg may import this
 package. It shares no code with the CUDA path: the product never imports it and

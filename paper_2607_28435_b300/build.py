@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsfft.so")
-SOURCES = ["runtime.cu", "tt_kernels.cu", "dense_fft.cu", "calib.cu", "noalloc.cu"]
+SOURCES = ["runtime.cu", "tt_kernels.cu", "dense_fft.cu", "calib.cu", "noalloc.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -43,7 +43,27 @@ class SfftInfo(ctypes.Structure):
                 ("out_rank", c_int32), ("tt_bytes", c_int64)]
 
 
+MLP_MAX_LAYERS = 8
+
+
+class SfftMlp(ctypes.Structure):
+    """sfft_mlp of include/sfft_mlp.h: widths and device pointers per layer."""
+    _fields_ = [("n_layers", c_int32), ("width", c_int32 * (MLP_MAX_LAYERS + 1)),
+                ("w", c_void_p * MLP_MAX_LAYERS), ("b", c_void_p * MLP_MAX_LAYERS)]
+
+
+_P_MLP = ctypes.POINTER(SfftMlp)
+
 EXPORTS = {
+    "sfft_mlp_workspace_floats": (c_int64, [_P_MLP, c_int64]),
+    "sfft_mlp_normalize": (c_int32, [c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                     c_void_p]),
+    "sfft_mlp_forward": (c_int32, [_P_MLP, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sfft_mlp_mse_grad": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    "sfft_mlp_backward": (c_int32, [_P_MLP, c_void_p, c_int64, c_void_p, c_void_p,
+                                    ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_void_p, c_void_p]),
+    "sfft_mlp_adam": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_float,
+                                ctypes.c_float, ctypes.c_float, ctypes.c_float, c_int64, c_void_p]),
     "sfft_create": (c_int32, [ctypes.POINTER(c_void_p), c_int32]),
     "sfft_destroy": (c_int32, [c_void_p]),
     "sfft_set_stream": (c_int32, [c_void_p, c_void_p]),

@@ -1,0 +1,281 @@
+"""Price surrogate: a GELU multilayer perceptron fitted to SFFT prices over a
+parameter box, answering repeated queries much faster than pricing each one,
+with the SFFT pricer as the fallback outside the box or when the fit is not
+accurate enough. It is not part of the paper's method (which builds the
+pricing map as a tensor network, Sec. 3).
+
+Inputs (8): the five Heston parameters (kappa, theta, sigma_v, rho, v0), r,
+T and the log-moneyness k = log(K / S0); the box is workloads.SURROGATE_LO/HI.
+Output: C / S0. Weights are kept in float32 for Adam and in bfloat16 for the
+products, which accumulate in float32 (include/sfft_mlp.h). Every step runs in
+the CUDA library; this module marshals pointers and drives the loop.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import time
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+from . import sfft, workloads as wl
+
+c_void_p = ctypes.c_void_p
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+class MLP:
+    """Parameters in one flat float32 buffer [W_1, b_1, W_2, b_2, ...] (each W_l
+    row-major w_l x w_{l-1}), its bfloat16 image for the products, the
+    gradient buffer of the same layout and Adam's two moment buffers."""
+
+    def __init__(self, widths: Sequence[int] = (8, 256, 256, 256, 256, 1), seed: int = 0, device: int = 0):
+        import torch
+        self.torch = torch
+        self.lib = sfft.load_library()
+        if len(widths) - 1 > sfft.MLP_MAX_LAYERS or widths[-1] != 1:
+            raise ValueError("widths: at most 8 layers, one output")
+        self.widths = tuple(int(w) for w in widths)
+        self.L = len(widths) - 1
+        self.dev = torch.device("cuda", device)
+        # Glorot-uniform weights, zero biases, from a seeded generator
+        rng = np.random.Generator(np.random.PCG64(seed))
+        chunks, self.w_off, self.b_off = [], [], []
+        off = 0
+        for l in range(self.L):
+            fi, fo = self.widths[l], self.widths[l + 1]
+            a = math.sqrt(6.0 / (fi + fo))
+            chunks.append(rng.uniform(-a, a, size=fo * fi))
+            self.w_off.append(off)
+            off += fo * fi
+            chunks.append(np.zeros(fo))
+            self.b_off.append(off)
+            off += fo
+        self.count = off
+        self.p = torch.tensor(np.concatenate(chunks), dtype=torch.float32, device=self.dev)
+        self.p16 = torch.empty(self.count, dtype=torch.int16, device=self.dev)
+        self.g = torch.zeros_like(self.p)
+        self.m = torch.zeros_like(self.p)
+        self.v = torch.zeros_like(self.p)
+        self.step = 0
+        self.refresh_bf16()
+        self.net = sfft.SfftMlp()
+        self.net.n_layers = self.L
+        for l in range(self.L + 1):
+            self.net.width[l] = self.widths[l]
+        for l in range(self.L):
+            self.net.w[l] = _ptr(self.p16) + 2 * self.w_off[l]
+            self.net.b[l] = _ptr(self.p) + 4 * self.b_off[l]
+        self.gw = (c_void_p * self.L)(*[_ptr(self.g) + 4 * o for o in self.w_off])
+        self.gb = (c_void_p * self.L)(*[_ptr(self.g) + 4 * o for o in self.b_off])
+        self._ws = {}
+
+    # -- helpers ------------------------------------------------------------
+    def _stream(self):
+        return c_void_p(self.torch.cuda.current_stream(self.dev).cuda_stream)
+
+    def _check(self, s):
+        if s != sfft.SFFT_OK:
+            raise sfft.SfftError(s, self.lib.sfft_status_string(s).decode())
+
+    def _buf(self, name, n):
+        b = self._ws.get(name)
+        if b is None or b.numel() < n:
+            b = self.torch.empty(max(n, 1), dtype=self.torch.float32, device=self.dev)
+            self._ws[name] = b
+        return b
+
+    def refresh_bf16(self):
+        """p16 <- bfloat16(p): an Adam step with learning rate 0 and zero
+        gradients leaves p unchanged and writes its bfloat16 image."""
+        if self.count:
+            gz = self.torch.zeros_like(self.p)
+            mz = self.torch.zeros_like(self.p)
+            vz = self.torch.zeros_like(self.p)
+            self._check(self.lib.sfft_mlp_adam(self.count, c_void_p(_ptr(self.p)), c_void_p(_ptr(self.p16)),
+                                               c_void_p(_ptr(gz)), c_void_p(_ptr(mz)), c_void_p(_ptr(vz)),
+                                               0.0, 0.9, 0.999, 1.0, 1, self._stream()))
+
+    def weights(self) -> Tuple[List[np.ndarray], List[np.ndarray]]:
+        """Host copies (float64) of the bfloat16 weights the products use and
+        of the biases."""
+        p16 = self.p16.cpu().numpy().view(np.uint16).astype(np.uint32) << 16
+        wf = p16.view(np.float32).astype(np.float64)
+        pf = self.p.cpu().numpy().astype(np.float64)
+        W, b = [], []
+        for l in range(self.L):
+            fo, fi = self.widths[l + 1], self.widths[l]
+            W.append(wf[self.w_off[l]:self.w_off[l] + fo * fi].reshape(fo, fi))
+            b.append(pf[self.b_off[l]:self.b_off[l] + fo])
+        return W, b
+
+    # -- passes -------------------------------------------------------------
+    def normalize(self, raw, lo=wl.SURROGATE_LO, hi=wl.SURROGATE_HI):
+        """raw: (B, 8) float64 device tensor -> (x float32 (B, 8), in_box int32 (B,))."""
+        torch = self.torch
+        B = raw.shape[0]
+        lo_d = torch.tensor(lo, dtype=torch.float64, device=self.dev)
+        hi_d = torch.tensor(hi, dtype=torch.float64, device=self.dev)
+        x = torch.empty((B, self.widths[0]), dtype=torch.float32, device=self.dev)
+        ib = torch.empty(B, dtype=torch.int32, device=self.dev)
+        self._check(self.lib.sfft_mlp_normalize(c_void_p(_ptr(raw)), B, self.widths[0], c_void_p(_ptr(lo_d)),
+                                                c_void_p(_ptr(hi_d)), c_void_p(_ptr(x)), c_void_p(_ptr(ib)),
+                                                self._stream()))
+        return x, ib
+
+    def forward(self, x, keep: bool = False):
+        """y = network(x) for x (B, w_0) float32; keep=True fills the workspace
+        a backward pass needs."""
+        B = x.shape[0]
+        y = self.torch.empty(B, dtype=self.torch.float32, device=self.dev)
+        if keep:
+            ws = self._buf("ws", int(self.lib.sfft_mlp_workspace_floats(ctypes.byref(self.net), B)))
+            s = self.lib.sfft_mlp_forward(ctypes.byref(self.net), c_void_p(_ptr(x)), B, c_void_p(_ptr(y)),
+                                          c_void_p(_ptr(ws)), None, self._stream())
+        else:
+            sc = self._buf("infer", 2 * B * max(self.widths[1:-1] or (1,)))
+            s = self.lib.sfft_mlp_forward(ctypes.byref(self.net), c_void_p(_ptr(x)), B, c_void_p(_ptr(y)),
+                                          None, c_void_p(_ptr(sc)), self._stream())
+        self._check(s)
+        return y
+
+    def gradients(self, x, t):
+        """Forward, mean squared error against t and backward; fills self.g.
+        Returns (y, loss as a device float)."""
+        B = x.shape[0]
+        y = self.forward(x, keep=True)
+        dy = self._buf("dy", B)
+        loss = self._buf("loss", 1)
+        self._check(self.lib.sfft_mlp_mse_grad(c_void_p(_ptr(y)), c_void_p(_ptr(t)), B, c_void_p(_ptr(dy)),
+                                               c_void_p(_ptr(loss)), self._stream()))
+        sc = self._buf("bwd", 2 * B * max(self.widths[1:-1] or (1,)))
+        self._check(self.lib.sfft_mlp_backward(ctypes.byref(self.net), c_void_p(_ptr(x)), B,
+                                               c_void_p(_ptr(self._ws["ws"])), c_void_p(_ptr(dy)), self.gw,
+                                               self.gb, c_void_p(_ptr(sc)), self._stream()))
+        return y, loss[:1]
+
+    def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        self.step += 1
+        self._check(self.lib.sfft_mlp_adam(self.count, c_void_p(_ptr(self.p)), c_void_p(_ptr(self.p16)),
+                                           c_void_p(_ptr(self.g)), c_void_p(_ptr(self.m)),
+                                           c_void_p(_ptr(self.v)), lr, beta1, beta2, eps, self.step,
+                                           self._stream()))
+
+    def fit(self, x, t, epochs: int, batch: int = 4096, lr: float = 2e-3, lr_end: float = 2e-5):
+        """Minibatch Adam over the rows of (x, t) in their stored order (the
+        caller shuffles once), with the learning rate decayed geometrically
+        from lr to lr_end. Returns the last epoch's mean loss."""
+        n = x.shape[0]
+        steps = epochs * max(1, n // batch)
+        decay = (lr_end / lr) ** (1.0 / max(1, steps - 1))
+        k, acc = 0, None
+        for _ in range(epochs):
+            acc = self.torch.zeros(1, dtype=self.torch.float32, device=self.dev)
+            nb = 0
+            for s in range(0, n - batch + 1, batch):
+                _, loss = self.gradients(x[s:s + batch], t[s:s + batch])
+                self.adam(lr * decay ** k)
+                acc += loss
+                k += 1
+                nb += 1
+        return float(acc.item()) / max(nb, 1)
+
+
+def sfft_dataset(pricer, problems, qmax: int = 4096, kmin: float = -1.5, kmax: float = 1.5):
+    """Price every instance at the grid strikes with log-moneyness in
+    [kmin, kmax] (at most qmax of them) with the SFFT pricer and return host
+    arrays: raw query rows (count x 8: Heston parameters, r, T,
+    log-moneyness) and targets C / S0."""
+    strikes = [sfft.strike_window(p, kmin, kmax, qmax) for p in problems]
+    c, lk, st, _ = pricer.price_batch(problems, strikes)
+    c, lk = c.cpu().numpy(), lk.cpu().numpy()
+    rows, tgt = [], []
+    off = 0
+    for p, (lb, sd, q), s in zip(problems, strikes, st):
+        if s == 0 and q > 0:
+            k = lk[off:off + q] - math.log(p.S0)
+            base = np.array(list(p.p[:5]) + [p.r, p.T], dtype=np.float64)
+            rows.append(np.concatenate([np.repeat(base[None, :], q, axis=0), k[:, None]], axis=1))
+            tgt.append(c[off:off + q] / p.S0)
+        off += q
+    return np.concatenate(rows), np.concatenate(tgt)
+
+
+class Surrogate:
+    """A trained MLP with its held-out error; prices queries through the
+    network inside the box when that error is at most `accept` * S0, else
+    through the SFFT pricer."""
+
+    def __init__(self, pricer, mlp: MLP, heldout_err: float, accept: float = 1e-3, S0: float = 100.0,
+                 n: int = 16, lo=wl.SURROGATE_LO, hi=wl.SURROGATE_HI):
+        self.pricer, self.mlp = pricer, mlp
+        self.heldout_err = heldout_err
+        self.trusted = heldout_err <= accept * S0
+        self.S0, self.n, self.lo, self.hi = S0, n, lo, hi
+
+    def price(self, raw: np.ndarray):
+        """raw: (B, 8) host rows (Heston parameters, r, T, log-moneyness).
+        Returns (prices, used_network mask)."""
+        torch = self.mlp.torch
+        rd = torch.tensor(np.ascontiguousarray(raw, dtype=np.float64), device=self.mlp.dev)
+        x, ib = self.mlp.normalize(rd, self.lo, self.hi)
+        y = self.mlp.forward(x)
+        out = (y.double() * self.S0).cpu().numpy()
+        use = ib.cpu().numpy().astype(bool) & self.trusted
+        miss = np.nonzero(~use)[0]
+        if len(miss):
+            out[miss] = self.sfft_prices(raw[miss])
+        return out, use
+
+    def sfft_prices(self, raw: np.ndarray) -> np.ndarray:
+        """One SFFT instance per query, priced at the grid strike nearest to
+        its log-moneyness."""
+        probs, strikes = [], []
+        for row in raw:
+            p = wl.Problem(wl.HESTON, tuple(float(v) for v in row[:5]), S0=self.S0, r=float(row[5]),
+                           T=float(row[6]), alpha=1.5, eta=0.25, n=self.n, quad=wl.SIMPSON_CM99)
+            dk = 2.0 * math.pi / ((1 << self.n) * p.eta)
+            k0 = -math.pi / p.eta
+            u = int(round((float(row[7]) - k0) / dk))
+            u = min(max(u, 0), (1 << self.n) - 1)
+            probs.append(p)
+            strikes.append((u, 1, 1))
+        c, _, _, _ = self.pricer.price_batch(probs, strikes, raise_on_error=False)
+        return c.cpu().numpy()
+
+
+def train_surrogate(pricer, n_train_inst: int = 1024, n_test_inst: int = 64, epochs: int = 12,
+                    seed: int = 260728435, widths=(8, 256, 256, 256, 256, 1), lo=wl.SURROGATE_LO,
+                    hi=wl.SURROGATE_HI, n: int = 16, accept: float = 1e-3):
+    """SFFT prices of n_train_inst box instances (about 4000 strikes each, so
+    1024 instances give about 2^22 prices) train the network; n_test_inst
+    further instances give the held-out error. Returns (Surrogate, stats)."""
+    torch = pricer.torch
+    t0 = time.perf_counter()
+    train = wl.heston_surrogate_batch(n_train_inst, seed, n=n, lo=lo, hi=hi)
+    test = wl.heston_surrogate_batch(n_test_inst, seed + 1, n=n, lo=lo, hi=hi)
+    Xr, Y = sfft_dataset(pricer, train, kmin=lo[7], kmax=hi[7])
+    perm = np.random.Generator(np.random.PCG64(seed + 2)).permutation(len(Y))
+    Xr, Y = Xr[perm], Y[perm]
+    t_data = time.perf_counter() - t0
+    mlp = MLP(widths, seed=seed)
+    x, _ = mlp.normalize(torch.tensor(Xr, device=mlp.dev), lo, hi)
+    t = torch.tensor(Y, dtype=torch.float32, device=mlp.dev)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    last = mlp.fit(x, t, epochs)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t1
+    Xh, Yh = sfft_dataset(pricer, test, kmin=lo[7], kmax=hi[7])
+    xh, _ = mlp.normalize(torch.tensor(Xh, device=mlp.dev), lo, hi)
+    yh = mlp.forward(xh).double().cpu().numpy()
+    err = float(np.max(np.abs(yh - Yh))) * test[0].S0
+    sur = Surrogate(pricer, mlp, err, accept=accept, n=n, lo=lo, hi=hi)
+    stats = {"train_prices": int(len(Y)), "heldout_prices": int(len(Yh)), "epochs": epochs,
+             "final_loss": last, "heldout_max_abs_err": err, "trusted": sur.trusted,
+             "data_s": t_data, "fit_s": t_fit}
+    return sur, stats

@@ -125,3 +125,23 @@ def heston_box_batch(count: int, seed: int, n: int = 16, tol: float = 1e-12) -> 
 def strike_set(l_begin: int, stride: int, q: int) -> np.ndarray:
     """Grid indices l_begin + i*stride, i in [0, q)."""
     return l_begin + stride * np.arange(q, dtype=np.int64)
+
+
+# surrogate box: the Heston box of the mixed batch, r, T and log-moneyness
+SURROGATE_NAMES = ("kappa", "theta", "sigma_v", "rho", "v0", "r", "T", "k")
+SURROGATE_LO = tuple(lo for lo, _ in CONFIG3_RANGES[HESTON]) + (0.0, 0.1, -1.5)
+SURROGATE_HI = tuple(hi for _, hi in CONFIG3_RANGES[HESTON]) + (0.05, 3.0, 1.5)
+
+
+def heston_surrogate_batch(count: int, seed: int, n: int = 16, tol: float = 1e-12,
+                           lo=SURROGATE_LO, hi=SURROGATE_HI) -> List[Problem]:
+    """Heston instances with parameters, r and T uniform in [lo, hi] (the
+    first seven coordinates of the surrogate box). Draw order per instance:
+    the five model parameters, r, T."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        v = [float(rng.uniform(lo[i], hi[i])) for i in range(7)]
+        out.append(Problem(HESTON, tuple(v[:5]), S0=100.0, r=v[5], T=v[6], alpha=1.5,
+                           eta=0.25, n=n, tol=tol, quad=SIMPSON_CM99))
+    return out

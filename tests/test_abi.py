@@ -1,6 +1,6 @@
 """C-ABI checks that need no GPU: the library builds and loads, exports every
-function include/sfft.h declares, and its host-only helpers agree with the
-oracle."""
+function the headers in include/ declare, and its host-only helpers agree
+with the oracle."""
 import ctypes
 import math
 import os
@@ -22,9 +22,14 @@ def lib():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "sfft.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sfft_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(sfft_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -39,6 +44,8 @@ def test_struct_layout_matches_header():
     # sfft_problem: 4 int32, 8 doubles, 7 doubles
     assert ctypes.sizeof(sfft.SfftProblem) == 4 * 4 + 8 * 8 + 7 * 8
     assert ctypes.sizeof(sfft.SfftInfo) == 4 * 4 + 8
+    # sfft_mlp: n_layers + 9 widths (int32), then 8 + 8 pointers
+    assert ctypes.sizeof(sfft.SfftMlp) == 10 * 4 + 16 * 8
 
 
 def test_status_strings(lib):
