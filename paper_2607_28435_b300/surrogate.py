@@ -191,7 +191,9 @@ def sfft_dataset(pricer, problems, qmax: int = 4096, kmin: float = -1.5, kmax: f
     arrays: raw query rows (count x 8: Heston parameters, r, T,
     log-moneyness) and targets C / S0."""
     strikes = [sfft.strike_window(p, kmin, kmax, qmax) for p in problems]
-    c, lk, st, _ = pricer.price_batch(problems, strikes)
+    # instances the pricer rejects (e.g. a Heston moment of order alpha + 1
+    # that explodes before T) give no rows
+    c, lk, st, _ = pricer.price_batch(problems, strikes, raise_on_error=False)
     c, lk = c.cpu().numpy(), lk.cpu().numpy()
     rows, tgt = [], []
     off = 0
@@ -279,3 +281,55 @@ def train_surrogate(pricer, n_train_inst: int = 1024, n_test_inst: int = 64, epo
              "final_loss": last, "heldout_max_abs_err": err, "trusted": sur.trusted,
              "data_s": t_data, "fit_s": t_fit}
     return sur, stats
+
+
+def main(argv=None):
+    """Train on the full box and report the fit and the query rates as one
+    JSON line: python -m paper_2607_28435_b300.surrogate [--instances N]
+    [--epochs E]."""
+    import argparse
+    import json
+
+    import torch
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--instances", type=int, default=1024)
+    ap.add_argument("--epochs", type=int, default=12)
+    ap.add_argument("--queries", type=int, default=1 << 20)
+    args = ap.parse_args(argv)
+    pricer = sfft.Pricer(0)
+    try:
+        sur, st = train_surrogate(pricer, n_train_inst=args.instances, epochs=args.epochs)
+        B = args.queries
+        rng = np.random.Generator(np.random.PCG64(7))
+        lo, hi = np.asarray(wl.SURROGATE_LO), np.asarray(wl.SURROGATE_HI)
+        q = lo + (hi - lo) * rng.uniform(size=(B, 8))
+        qd = torch.tensor(q, device=sur.mlp.dev)
+        x, _ = sur.mlp.normalize(qd)
+        sur.mlp.forward(x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        reps = 5
+        for _ in range(reps):
+            x, _ = sur.mlp.normalize(qd)
+            sur.mlp.forward(x)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        w = sur.mlp.widths
+        flops = 2.0 * B * sum(w[i] * w[i + 1] for i in range(len(w) - 1))
+        t0 = time.perf_counter()
+        sur.sfft_prices(q[:4096])
+        sfft_rate = 4096 / (time.perf_counter() - t0)
+        out = {"surrogate": st, "queries": B, "network_queries_per_s": B / (ms * 1e-3),
+               "network_ms": ms, "network_fp32_tflops": flops / (ms * 1e-3) / 1e12,
+               "sfft_one_instance_per_query_per_s": sfft_rate,
+               "gain": B / (ms * 1e-3) / sfft_rate}
+        print(json.dumps(out), flush=True)
+    finally:
+        pricer.close()
+
+
+if __name__ == "__main__":
+    main()
