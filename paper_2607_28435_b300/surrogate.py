@@ -208,16 +208,26 @@ def sfft_dataset(pricer, problems, qmax: int = 4096, kmin: float = -1.5, kmax: f
 
 
 class Surrogate:
-    """A trained MLP with its held-out error; prices queries through the
-    network inside the box when that error is at most `accept` * S0, else
-    through the SFFT pricer."""
+    """A trained MLP and where to trust it. The box's (T, k) plane is cut into
+    cells; a cell is trusted when the held-out maximum error of the prices in
+    it is at most margin * accept * S0. Queries inside the box and in a
+    trusted cell are priced by the network, all others by the SFFT pricer."""
 
-    def __init__(self, pricer, mlp: MLP, heldout_err: float, accept: float = 1e-3, S0: float = 100.0,
-                 n: int = 16, lo=wl.SURROGATE_LO, hi=wl.SURROGATE_HI):
+    def __init__(self, pricer, mlp: MLP, cell_err: np.ndarray, accept: float = 1e-3, margin: float = 0.3,
+                 S0: float = 100.0, n: int = 16, lo=wl.SURROGATE_LO, hi=wl.SURROGATE_HI):
         self.pricer, self.mlp = pricer, mlp
-        self.heldout_err = heldout_err
-        self.trusted = heldout_err <= accept * S0
+        self.cell_err = np.asarray(cell_err, dtype=np.float64)
+        self.trusted_cells = self.cell_err <= margin * accept * S0
+        self.trusted = bool(self.trusted_cells.any())
         self.S0, self.n, self.lo, self.hi = S0, n, lo, hi
+
+    @staticmethod
+    def cells(raw: np.ndarray, lo, hi, shape) -> Tuple[np.ndarray, np.ndarray]:
+        """(T, k) cell of every row: the T and k ranges of the box cut into
+        shape[0] and shape[1] equal parts."""
+        iT = np.floor((raw[:, 6] - lo[6]) / (hi[6] - lo[6]) * shape[0]).astype(np.int64)
+        ik = np.floor((raw[:, 7] - lo[7]) / (hi[7] - lo[7]) * shape[1]).astype(np.int64)
+        return np.clip(iT, 0, shape[0] - 1), np.clip(ik, 0, shape[1] - 1)
 
     def price(self, raw: np.ndarray):
         """raw: (B, 8) host rows (Heston parameters, r, T, log-moneyness).
@@ -227,7 +237,8 @@ class Surrogate:
         x, ib = self.mlp.normalize(rd, self.lo, self.hi)
         y = self.mlp.forward(x)
         out = (y.double() * self.S0).cpu().numpy()
-        use = ib.cpu().numpy().astype(bool) & self.trusted
+        iT, ik = self.cells(raw, self.lo, self.hi, self.trusted_cells.shape)
+        use = ib.cpu().numpy().astype(bool) & self.trusted_cells[iT, ik]
         miss = np.nonzero(~use)[0]
         if len(miss):
             out[miss] = self.sfft_prices(raw[miss])
@@ -250,16 +261,19 @@ class Surrogate:
         return c.cpu().numpy()
 
 
-def train_surrogate(pricer, n_train_inst: int = 1024, n_test_inst: int = 64, epochs: int = 12,
+def train_surrogate(pricer, n_train_inst: int = 1024, n_test_inst: int = 256, epochs: int = 12,
                     seed: int = 260728435, widths=(8, 256, 256, 256, 256, 1), lo=wl.SURROGATE_LO,
-                    hi=wl.SURROGATE_HI, n: int = 16, accept: float = 1e-3):
+                    hi=wl.SURROGATE_HI, n: int = 16, accept: float = 1e-3, cells=(6, 12)):
     """SFFT prices of n_train_inst box instances (about 4000 strikes each, so
-    1024 instances give about 2^22 prices) train the network; n_test_inst
-    further instances give the held-out error. Returns (Surrogate, stats)."""
+    1024 instances give about 2^22 prices) train the network. n_test_inst
+    further instances give the held-out error per (T, k) cell, which decides
+    where the network is trusted; n_test_inst more, drawn independently,
+    check the trusted cells. Returns (Surrogate, stats)."""
     torch = pricer.torch
     t0 = time.perf_counter()
     train = wl.heston_surrogate_batch(n_train_inst, seed, n=n, lo=lo, hi=hi)
     test = wl.heston_surrogate_batch(n_test_inst, seed + 1, n=n, lo=lo, hi=hi)
+    val = wl.heston_surrogate_batch(n_test_inst, seed + 3, n=n, lo=lo, hi=hi)
     Xr, Y = sfft_dataset(pricer, train, kmin=lo[7], kmax=hi[7])
     perm = np.random.Generator(np.random.PCG64(seed + 2)).permutation(len(Y))
     Xr, Y = Xr[perm], Y[perm]
@@ -272,14 +286,30 @@ def train_surrogate(pricer, n_train_inst: int = 1024, n_test_inst: int = 64, epo
     last = mlp.fit(x, t, epochs)
     torch.cuda.synchronize()
     t_fit = time.perf_counter() - t1
-    Xh, Yh = sfft_dataset(pricer, test, kmin=lo[7], kmax=hi[7])
-    xh, _ = mlp.normalize(torch.tensor(Xh, device=mlp.dev), lo, hi)
-    yh = mlp.forward(xh).double().cpu().numpy()
-    err = float(np.max(np.abs(yh - Yh))) * test[0].S0
-    sur = Surrogate(pricer, mlp, err, accept=accept, n=n, lo=lo, hi=hi)
-    stats = {"train_prices": int(len(Y)), "heldout_prices": int(len(Yh)), "epochs": epochs,
-             "final_loss": last, "heldout_max_abs_err": err, "trusted": sur.trusted,
-             "data_s": t_data, "fit_s": t_fit}
+    S0 = train[0].S0
+
+    def errors(problems):
+        Xh, Yh = sfft_dataset(pricer, problems, kmin=lo[7], kmax=hi[7])
+        xh, _ = mlp.normalize(torch.tensor(Xh, device=mlp.dev), lo, hi)
+        yh = mlp.forward(xh).double().cpu().numpy()
+        return Xh, np.abs(yh - Yh) * S0
+
+    Xh, eh = errors(test)
+    iT, ik = Surrogate.cells(Xh, lo, hi, cells)
+    cell_err = np.full(cells, np.inf)
+    for a, b_, e in zip(iT, ik, eh):
+        cell_err[a, b_] = e if not np.isfinite(cell_err[a, b_]) else max(cell_err[a, b_], e)
+    sur = Surrogate(pricer, mlp, cell_err, accept=accept, S0=S0, n=n, lo=lo, hi=hi)
+    Xv, ev = errors(val)
+    vT, vk = Surrogate.cells(Xv, lo, hi, cells)
+    tv = sur.trusted_cells[vT, vk]
+    stats = {"train_prices": int(len(Y)), "heldout_prices": int(len(eh)), "epochs": epochs,
+             "final_loss": last, "heldout_max_abs_err": float(eh.max()),
+             "heldout_rms_err": float(np.sqrt(np.mean(eh ** 2))),
+             "trusted_cells": int(sur.trusted_cells.sum()), "cells": int(np.prod(cells)),
+             "validation_prices": int(len(ev)), "validation_trusted_fraction": float(tv.mean()),
+             "validation_max_abs_err_trusted": float(ev[tv].max()) if tv.any() else None,
+             "accept_abs": accept * S0, "data_s": t_data, "fit_s": t_fit}
     return sur, stats
 
 

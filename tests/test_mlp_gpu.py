@@ -116,9 +116,13 @@ def test_small_fit_and_serving(mods):
         # the fallback's grid mapping: rows that are grid strikes price as in the batch
         assert np.allclose(sur.sfft_prices(Xh[:16]), 100.0 * Yh[:16], rtol=0, atol=1e-8 * 100.0)
         out, used = sur.price(Xh)
-        if sur.trusted:
-            assert used.all()
-            assert np.max(np.abs(out - 100.0 * Yh)) <= 1e-2 * 100.0
+        # the network answers only in trusted cells, within the acceptance
+        # there; every other query is the SFFT price itself
+        iT, ik = sur.cells(Xh, lo, hi, sur.trusted_cells.shape)
+        assert np.array_equal(used, sur.trusted_cells[iT, ik])
+        if used.any():
+            assert np.max(np.abs(out[used] - 100.0 * Yh[used])) <= 1e-2 * 100.0
+        assert np.allclose(out[~used], 100.0 * Yh[~used], rtol=0, atol=1e-8 * 100.0)
         # out of the box: answered by the SFFT pricer at the nearest grid strike
         far = Xh[:3].copy()
         far[:, 7] = 1.0  # log-moneyness outside [-0.4, 0.4]
