@@ -38,6 +38,21 @@ ZIPUP_TRAFFIC = {"bytes": 48452608 + 917167104, "instances": 4096, "src": "b51a6
 KERNEL_SRCS = ("cplx.cuh", "kernels.cuh", "la.cuh", "model.cuh", "tt_kernels.cu")
 
 
+def batch_problems(args, seed=None):
+    """The mixed batch: n uniform in 16..34 at tol 1e-12 by default, or one n
+    (--n) and another tolerance (--tol), e.g. --n 30 --tol 1e-7."""
+    from paper_2607_28435_b300 import workloads as wl
+    lo, hi = (args.n, args.n) if args.n else (16, 34)
+    return wl.config3_batch(args.count, seed=wl.CONFIG3_SEED if seed is None else seed, n_lo=lo, n_hi=hi,
+                            tol=args.tol)
+
+
+def workload_name(args):
+    nr = f"n {args.n}" if args.n else "n 16..34"
+    tol = "" if args.tol == 1e-12 else f", tol {args.tol:g}"
+    return f"batched TT-SFFT, {args.count} instances (Heston/Merton/VG), {nr}{tol}"
+
+
 def kernel_src_hash():
     import hashlib
     h = hashlib.sha256()
@@ -58,6 +73,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--count", type=int, default=4096)
+    ap.add_argument("--n", type=int, default=None,
+                    help="one grid exponent for every instance (default: uniform in 16..34)")
+    ap.add_argument("--tol", type=float, default=1e-12, help="truncation tolerance of every instance")
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -216,7 +234,7 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    problems = wl.config3_batch(args.count, seed=wl.CONFIG3_SEED + rank)
+    problems = batch_problems(args, seed=wl.CONFIG3_SEED + rank)
     strikes = [sfft.strike_window(p) for p in problems]
     total_q = sum(s[2] for s in strikes)
     pricer = sfft.Pricer(local_rank)
@@ -335,7 +353,8 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
     achieved = prof[dom]["flops"] / (dms * 1e-3) / 1e9 if dms > 0 else 0.0
     launches = sum(v["launches"] for v in prof.values())
     traffic = None
-    if dom == "zipup" and args.count == ZIPUP_TRAFFIC["instances"] and kernel_src_hash() == ZIPUP_TRAFFIC["src"]:
+    if (dom == "zipup" and args.count == ZIPUP_TRAFFIC["instances"] and args.n is None and args.tol == 1e-12
+            and kernel_src_hash() == ZIPUP_TRAFFIC["src"]):
         traffic = ZIPUP_TRAFFIC["bytes"]
 
     # dense-FFT baseline on the same batch: one instance per n <= 30 timed,
@@ -366,9 +385,9 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"batched TT-SFFT, {args.count} instances (Heston/Merton/VG), n 16..34",
+        "config": {"workload": workload_name(args),
                    "instances": args.count, "strikes_per_step": total_q, "priced_per_step": q_ok,
-                   "failed_instances": int(len(ok) - sum(ok)), "tol": 1e-12, "eta": 0.25, "alpha": 1.5,
+                   "failed_instances": int(len(ok) - sum(ok)), "tol": args.tol, "eta": 0.25, "alpha": 1.5,
                    "window": "|log K/S0| <= 1.5, <= 4096 strikes", "l2": "flushed (256 MB write) between steps",
                    "max_int_rank": max(ranks_int) if ranks_int else None,
                    "max_out_rank": max(ranks_out) if ranks_out else None},
@@ -481,7 +500,7 @@ def dense_baseline(pricer, problems, strikes, torch, dev):
 def run_reference(args, pool, ncores):
     from paper_2607_28435_b300 import workloads as wl
     from oracle import carr_madan as cm
-    problems = wl.config3_batch(args.count)
+    problems = batch_problems(args)
     strikes = [cm.strike_window(p) for p in problems]
     rates = []
     for i in range(args.warmup + args.steps):
@@ -494,7 +513,7 @@ def run_reference(args, pool, ncores):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": f"batched TT-SFFT, {args.count} instances (Heston/Merton/VG), n 16..34"},
+        "config": {"workload": workload_name(args)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
                          "sample": f"per step, {n_inst} instances in a seeded random order, each timed on "
                                    f"its first max(32, 2^24/support) strikes and scaled to all its strikes "

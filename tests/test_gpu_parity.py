@@ -297,6 +297,21 @@ def test_config3_sample(pricer):
     check_prices(pricer, sel, sample=6, seed=3)
 
 
+def test_config4_accuracy_at_tol_1e7(pricer):
+    # the mixed batch at n = 30 with truncation tolerance 1e-7 (the mixed-
+    # precision configuration's accuracy target, 1e-6 S0 per instance), on
+    # the FP64 path: every instance prices, and sampled strikes of those whose
+    # direct sum runs over at most 2^20 points agree with the oracle
+    probs = wl.config3_batch(48, n_lo=30, n_hi=30, tol=1e-7)
+    strikes = [cm.strike_window(p) for p in probs]
+    _, _, status, info = pricer.price_batch(probs, strikes, raise_on_error=False)
+    assert status == [0] * len(probs), status
+    sel = [p for p in probs if cm.support_limit(p) <= (1 << 20)]
+    assert len(sel) >= 24
+    worst, _, _ = check_prices(pricer, sel, sample=8, seed=4, tol=1e-6)
+    assert worst <= 1e-6
+
+
 def test_reused_batch_matches_lists(pricer):
     # a Batch marshalled once gives the same prices, statuses and ranks as the
     # list form, on two calls in a row
