@@ -347,7 +347,7 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
     # whose launches are all one kernel (a two-tier phase launches the same
     # kernel twice per step; "cross" mixes two kernels), the one with the most
     # time; achieved = its algorithmic flops over its launches' total time
-    tt_phases = ["build", "zipup", "round", "readout", "probe"]
+    tt_phases = ["build", "zipup", "round", "readout"]
     dom = max(tt_phases, key=lambda k: prof[k]["ms"])
     dms = prof[dom]["ms"]
     achieved = prof[dom]["flops"] / (dms * 1e-3) / 1e9 if dms > 0 else 0.0

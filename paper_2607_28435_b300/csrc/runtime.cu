@@ -525,7 +525,10 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   cross_dev = reinterpret_cast<int*>(p);
   if ((s = ensure(ctx, "list_counts", sizeof(int) * 2, &p))) return s;
   list_counts = reinterpret_cast<int*>(p);
-  k_build_lists<<<1, 1024, 0, ctx->stream>>>(m_dev, b.n_arr, cnt, kSvdMaxBits, svd_dev, cross_dev, list_counts);
+  {
+    PhaseScope ps(ctx, PH_PROBE);
+    k_build_lists<<<1, 1024, 0, ctx->stream>>>(m_dev, b.n_arr, cnt, kSvdMaxBits, svd_dev, cross_dev, list_counts);
+  }
   CK(cudaGetLastError());
   // the zip-up, rounding and readout take every instance, largest n first
   std::vector<int> all_list(cnt);

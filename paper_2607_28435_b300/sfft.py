@@ -24,7 +24,7 @@ MAX_N = 48
 NPHASES = 10
 PHASE_NAMES = ["probe", "build", "zipup", "round", "readout", "mpo", "dense_sample", "dense_fft",
                "dense_gather", "cross"]
-PHASE_KERNELS = ["k_support_probe", "k_integrand_ttsvd", "k_zipup", "k_tt_round", "k_readout",
+PHASE_KERNELS = ["k_support_probe+k_build_lists", "k_integrand_ttsvd", "k_zipup", "k_tt_round", "k_readout",
                  "k_mpo_interp+k_tt_round", "k_dense_sample", "k_fft_pass", "k_dense_gather",
                  "k_integrand_cross+k_tt_round"]
 MAX_RANK = 32
