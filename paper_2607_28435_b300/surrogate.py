@@ -316,7 +316,7 @@ def train_surrogate(pricer, n_train_inst: int = 1024, n_test_inst: int = 256, ep
 def main(argv=None):
     """Train on the full box and report the fit and the query rates as one
     JSON line: python -m paper_2607_28435_b300.surrogate [--instances N]
-    [--epochs E]."""
+    [--epochs E] [--cells NT NK]."""
     import argparse
     import json
 
@@ -324,12 +324,14 @@ def main(argv=None):
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--instances", type=int, default=1024)
-    ap.add_argument("--epochs", type=int, default=12)
+    ap.add_argument("--epochs", type=int, default=160)
+    ap.add_argument("--cells", type=int, nargs=2, default=(6, 12), help="(T, k) cells of the trust table")
     ap.add_argument("--queries", type=int, default=1 << 20)
     args = ap.parse_args(argv)
     pricer = sfft.Pricer(0)
     try:
-        sur, st = train_surrogate(pricer, n_train_inst=args.instances, epochs=args.epochs)
+        sur, st = train_surrogate(pricer, n_train_inst=args.instances, epochs=args.epochs,
+                                  cells=tuple(args.cells))
         B = args.queries
         rng = np.random.Generator(np.random.PCG64(7))
         lo, hi = np.asarray(wl.SURROGATE_LO), np.asarray(wl.SURROGATE_HI)
