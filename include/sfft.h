@@ -54,7 +54,12 @@ typedef enum {
   SFFT_ECUDA = 4,    /* a CUDA runtime call failed (text in sfft_last_error) */
   SFFT_ERANK = 5,    /* a TT or MPO rank would exceed the cap */
   SFFT_ENOCONV = 6,  /* integrand builder did not reach the tolerance */
-  SFFT_ETIMEOUT = 7  /* a bounded device-side wait expired */
+  SFFT_ETIMEOUT = 7, /* a bounded device-side wait expired */
+  SFFT_EBOUNDS = 8   /* a price left the no-arbitrage bounds by more than
+                        1e-6 S0 max(1, e^{-alpha k}) (k the log-moneyness):
+                        the discrete sum does not resolve the damped integrand
+                        (near a moment explosion at this alpha); prices are
+                        still written, for inspection */
 } sfft_status;
 
 /* Characteristic-function models of log(S_T/S0). Sec. 2 gives Black-Scholes
@@ -184,8 +189,9 @@ sfft_status sfft_qft_price_batch(sfft_ctx *ctx, const sfft_problem *probs, int32
  * whole pricing step.)
  * sfft_graph_create runs the batch once in a private context, whose
  * workspaces, MPO cache and stream belong to the graph alone and never move,
- * then captures the same call; every instance must price (else the status of
- * the first failure is returned and *out stays NULL). prices and log_strikes
+ * then captures the same call; every instance must price, with status
+ * SFFT_OK or SFFT_EBOUNDS (else the status of the first failure is returned
+ * and *out stays NULL). prices and log_strikes
  * (device, sum(q) doubles each) stay bound to the graph. */
 typedef struct sfft_graph sfft_graph;
 sfft_status sfft_graph_create(sfft_ctx *ctx, const sfft_problem *probs, int32_t count,

@@ -32,6 +32,7 @@ enum { PH_PROBE = 0, PH_BUILD = 1, PH_ZIPUP = 2, PH_ROUND = 3, PH_READOUT = 4, P
 #define SFFT_EINVAL_DEV 1
 #define SFFT_ERANK_DEV 5
 #define SFFT_ENOCONV_DEV 6
+#define SFFT_EBOUNDS_DEV 8
 
 __global__ void k_sample(const InstParams* P, const long long* j, long long count, cd* x);
 __global__ void k_support_probe(const InstParams* P, int count, double probe_tol, int m_min,
@@ -98,7 +99,7 @@ __global__ void k_readout(const int* list, int count, int* counter, const InstPa
                           const cd* B, const long long* b_off,
                           const int* b_ranks_all, int core_stride, const long long* l_begin,
                           const int* tbits, const int* qarr, const long long* out_off,
-                          double* prices, double* logk, const int* status, cd* scratch,
+                          double* prices, double* logk, int* status, cd* scratch,
                           long long scratch_stride);
 
 __global__ void k_dfma_peak(double* out, int iters);

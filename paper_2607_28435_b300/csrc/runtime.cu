@@ -805,6 +805,7 @@ const char* sfft_status_string(sfft_status s) {
     case SFFT_ERANK: return "rank cap reached";
     case SFFT_ENOCONV: return "integrand builder did not converge";
     case SFFT_ETIMEOUT: return "device wait timed out";
+    case SFFT_EBOUNDS: return "prices outside the no-arbitrage bounds (grid too coarse for the damped integrand)";
   }
   return "unknown status";
 }
@@ -1351,8 +1352,11 @@ sfft_status sfft_graph_create(sfft_ctx* ctx, const sfft_problem* probs, int32_t 
   // 1. a plain run sizes every workspace and builds the MPOs
   std::vector<int32_t> st(count);
   s = price_common(g->own, probs, count, l_begin, stride, q, prices, log_strikes, st.data(), nullptr, 0);
+  // SFFT_EBOUNDS means computed, outside the bounds: its prices are written
+  // on every replay and sfft_graph_status reports it
+  if (s == SFFT_EBOUNDS) s = SFFT_OK;
   for (int i = 0; s == SFFT_OK && i < count; ++i)
-    if (st[i] != SFFT_OK) s = (sfft_status)st[i];
+    if (st[i] != SFFT_OK && st[i] != SFFT_EBOUNDS) s = (sfft_status)st[i];
   if (s) {
     set_err(ctx, s, "graph: every instance must price (%s)", g->own->err.c_str());
     sfft_graph_destroy(g);

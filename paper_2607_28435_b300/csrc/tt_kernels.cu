@@ -1005,7 +1005,7 @@ __global__ void k_readout(const int* list, int count, int* counter, const InstPa
                           int core_stride, const long long* l_begin,
                           const int* tbits, const int* qarr,
                           const long long* out_off, double* prices,
-                          double* logk, const int* status,
+                          double* logk, int* status,
                           cd* scratch, long long scratch_stride) {
   __shared__ cd Lv[(1 << READOUT_TREE_BITS) * SFFT_SLOT_RANK_DEV];
   __shared__ cd Lv2[(1 << READOUT_TREE_BITS) * SFFT_SLOT_RANK_DEV];
@@ -1096,6 +1096,12 @@ __global__ void k_readout(const int* list, int count, int* counter, const InstPa
     // 4. combine and price
     const int rmid = rb[sh];
     const long long pbase = (sh < n) ? (lb >> sh) : 0;
+    // a call price lies in [max(S0 - K e^{-rT}, 0), S0]. Outside it by more
+    // than 1e-6 S0 max(1, e^{-alpha k}) the discrete sum has not resolved the
+    // integrand: the factor e^{-alpha k} of the price amplifies the sum's own
+    // rounding at far strikes (Sec. 4), so the band widens with it there.
+    // The bounds are evaluated in FP32, well inside the band.
+    bool out_of_bounds = false;
     for (int i = threadIdx.x; i < q; i += blockDim.x) {
       const long long u = lb + ((long long)i << tbits[inst]);
       const int c = (int)((u >> t) & ((1 << h) - 1));
@@ -1104,9 +1110,14 @@ __global__ void k_readout(const int* list, int count, int* counter, const InstPa
       for (int a = 0; a < rmid; ++a) acc = cfma(Lv[c * SFFT_SLOT_RANK_DEV + a], R0[pi * rmid + a], acc);
       double sgn;
       const double f = price_factor(prm, u, &sgn);
-      pr[i] = prm.S0 * f * sgn * acc.x;
-      lk[i] = log(prm.S0) + prm.k0 + prm.dk * (double)u;
+      const double price = prm.S0 * f * sgn * acc.x;
+      const double km = prm.k0 + prm.dk * (double)u;
+      pr[i] = price;
+      lk[i] = log(prm.S0) + km;
+      const double lower = fmax(prm.S0 * (1.0 - (double)expf((float)km) * prm.disc), 0.0);
+      const double band = 1e-6 * prm.S0 * fmax(1.0, (double)expf((float)(-prm.alpha * km)));
+      out_of_bounds |= !(price >= lower - band && price <= prm.S0 + band);
     }
-    __syncthreads();
+    if (__syncthreads_or(out_of_bounds) && threadIdx.x == 0) status[inst] = SFFT_EBOUNDS_DEV;
   WORK_LOOP_END
 }

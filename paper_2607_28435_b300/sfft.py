@@ -18,8 +18,9 @@ LIB_PATH = os.path.join(HERE, "libsfft.so")
 
 c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
-SFFT_OK, SFFT_EINVAL, SFFT_EMOMENT, SFFT_ENOMEM, SFFT_ECUDA, SFFT_ERANK, SFFT_ENOCONV, SFFT_ETIMEOUT = range(8)
-STATUS_NAMES = ["OK", "EINVAL", "EMOMENT", "ENOMEM", "ECUDA", "ERANK", "ENOCONV", "ETIMEOUT"]
+(SFFT_OK, SFFT_EINVAL, SFFT_EMOMENT, SFFT_ENOMEM, SFFT_ECUDA, SFFT_ERANK, SFFT_ENOCONV, SFFT_ETIMEOUT,
+ SFFT_EBOUNDS) = range(9)
+STATUS_NAMES = ["OK", "EINVAL", "EMOMENT", "ENOMEM", "ECUDA", "ERANK", "ENOCONV", "ETIMEOUT", "EBOUNDS"]
 MAX_N = 48
 NPHASES = 10
 PHASE_NAMES = ["probe", "build", "zipup", "round", "readout", "mpo", "dense_sample", "dense_fft",
@@ -241,7 +242,7 @@ class Graph:
 
 class SfftError(RuntimeError):
     def __init__(self, status: int, msg: str):
-        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
         self.status = status
 
 

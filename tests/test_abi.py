@@ -49,7 +49,7 @@ def test_struct_layout_matches_header():
 
 
 def test_status_strings(lib):
-    for s in range(8):
+    for s in range(9):
         assert lib.sfft_status_string(s)
     assert b"unknown" in lib.sfft_status_string(99)
 

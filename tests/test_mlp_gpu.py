@@ -105,7 +105,7 @@ def test_small_fit_and_serving(mods):
         lo = tuple(mid[:7]) + (-0.4,)
         hi = tuple(v * 1.05 if v > 0 else v * 0.95 for v in mid[:7]) + (0.4,)
         lo, hi = tuple(min(a, b) for a, b in zip(lo, hi)), tuple(max(a, b) for a, b in zip(lo, hi))
-        sur, st = surrogate.train_surrogate(pricer, n_train_inst=64, n_test_inst=8, epochs=20,
+        sur, st = surrogate.train_surrogate(pricer, n_train_inst=64, n_test_inst=8, epochs=20, qmax=4096,
                                             widths=(8, 64, 64, 1), lo=lo, hi=hi, accept=1e-2)
         assert st["final_loss"] < 1e-3
         assert math.isfinite(st["heldout_max_abs_err"])
