@@ -261,20 +261,22 @@ class Surrogate:
         return c.cpu().numpy()
 
 
-def train_surrogate(pricer, n_train_inst: int = 1024, n_test_inst: int = 256, epochs: int = 12,
+def train_surrogate(pricer, n_train_inst: int = 16384, n_test_inst: int = 1024, epochs: int = 12,
                     seed: int = 260728435, widths=(8, 256, 256, 256, 256, 1), lo=wl.SURROGATE_LO,
-                    hi=wl.SURROGATE_HI, n: int = 16, accept: float = 1e-3, cells=(6, 12)):
-    """SFFT prices of n_train_inst box instances (about 4000 strikes each, so
-    1024 instances give about 2^22 prices) train the network. n_test_inst
-    further instances give the held-out error per (T, k) cell, which decides
-    where the network is trusted; n_test_inst more, drawn independently,
-    check the trusted cells. Returns (Surrogate, stats)."""
+                    hi=wl.SURROGATE_HI, n: int = 16, accept: float = 1e-3, cells=(6, 12), qmax: int = 256):
+    """SFFT prices of n_train_inst box instances at qmax strikes each (16384 x
+    256 = 2^22 prices) train the network: many parameter sets with few strikes
+    each, since the fit's error is set by how densely the seven model and
+    market coordinates are sampled, not the strikes. n_test_inst further
+    instances give the held-out error per (T, k) cell, which decides where the
+    network is trusted; n_test_inst more, drawn independently, check the
+    trusted cells. Returns (Surrogate, stats)."""
     torch = pricer.torch
     t0 = time.perf_counter()
     train = wl.heston_surrogate_batch(n_train_inst, seed, n=n, lo=lo, hi=hi)
     test = wl.heston_surrogate_batch(n_test_inst, seed + 1, n=n, lo=lo, hi=hi)
     val = wl.heston_surrogate_batch(n_test_inst, seed + 3, n=n, lo=lo, hi=hi)
-    Xr, Y = sfft_dataset(pricer, train, kmin=lo[7], kmax=hi[7])
+    Xr, Y = sfft_dataset(pricer, train, qmax=qmax, kmin=lo[7], kmax=hi[7])
     perm = np.random.Generator(np.random.PCG64(seed + 2)).permutation(len(Y))
     Xr, Y = Xr[perm], Y[perm]
     t_data = time.perf_counter() - t0
@@ -289,7 +291,7 @@ def train_surrogate(pricer, n_train_inst: int = 1024, n_test_inst: int = 256, ep
     S0 = train[0].S0
 
     def errors(problems):
-        Xh, Yh = sfft_dataset(pricer, problems, kmin=lo[7], kmax=hi[7])
+        Xh, Yh = sfft_dataset(pricer, problems, qmax=qmax, kmin=lo[7], kmax=hi[7])
         xh, _ = mlp.normalize(torch.tensor(Xh, device=mlp.dev), lo, hi)
         yh = mlp.forward(xh).double().cpu().numpy()
         return Xh, np.abs(yh - Yh) * S0
@@ -323,7 +325,8 @@ def main(argv=None):
     import torch
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--instances", type=int, default=1024)
+    ap.add_argument("--instances", type=int, default=16384)
+    ap.add_argument("--qmax", type=int, default=256, help="strikes per training instance")
     ap.add_argument("--epochs", type=int, default=160)
     ap.add_argument("--cells", type=int, nargs=2, default=(6, 12), help="(T, k) cells of the trust table")
     ap.add_argument("--queries", type=int, default=1 << 20)
@@ -331,7 +334,7 @@ def main(argv=None):
     pricer = sfft.Pricer(0)
     try:
         sur, st = train_surrogate(pricer, n_train_inst=args.instances, epochs=args.epochs,
-                                  cells=tuple(args.cells))
+                                  cells=tuple(args.cells), qmax=args.qmax)
         B = args.queries
         rng = np.random.Generator(np.random.PCG64(7))
         lo, hi = np.asarray(wl.SURROGATE_LO), np.asarray(wl.SURROGATE_HI)
