@@ -213,7 +213,7 @@ class Surrogate:
     it is at most margin * accept * S0. Queries inside the box and in a
     trusted cell are priced by the network, all others by the SFFT pricer."""
 
-    def __init__(self, pricer, mlp: MLP, cell_err: np.ndarray, accept: float = 1e-3, margin: float = 0.3,
+    def __init__(self, pricer, mlp: MLP, cell_err: np.ndarray, accept: float = 1e-3, margin: float = 0.5,
                  S0: float = 100.0, n: int = 16, lo=wl.SURROGATE_LO, hi=wl.SURROGATE_HI):
         self.pricer, self.mlp = pricer, mlp
         self.cell_err = np.asarray(cell_err, dtype=np.float64)
@@ -305,13 +305,18 @@ def train_surrogate(pricer, n_train_inst: int = 16384, n_test_inst: int = 1024, 
     Xv, ev = errors(val)
     vT, vk = Surrogate.cells(Xv, lo, hi, cells)
     tv = sur.trusted_cells[vT, vk]
+    # the same fit under other margins: validation share and maximum error
+    by_margin = {}
+    for mg in (0.3, 0.5, 0.7, 1.0):
+        tm = (cell_err <= mg * accept * S0)[vT, vk]
+        by_margin[str(mg)] = [float(tm.mean()), float(ev[tm].max()) if tm.any() else None]
     stats = {"train_prices": int(len(Y)), "heldout_prices": int(len(eh)), "epochs": epochs,
              "final_loss": last, "heldout_max_abs_err": float(eh.max()),
              "heldout_rms_err": float(np.sqrt(np.mean(eh ** 2))),
              "trusted_cells": int(sur.trusted_cells.sum()), "cells": int(np.prod(cells)),
              "validation_prices": int(len(ev)), "validation_trusted_fraction": float(tv.mean()),
              "validation_max_abs_err_trusted": float(ev[tv].max()) if tv.any() else None,
-             "accept_abs": accept * S0, "data_s": t_data, "fit_s": t_fit}
+             "accept_abs": accept * S0, "validation_by_margin": by_margin, "data_s": t_data, "fit_s": t_fit}
     return sur, stats
 
 
