@@ -505,7 +505,7 @@ def run_reference(args, pool, ncores):
     rates = []
     for i in range(args.warmup + args.steps):
         rate, _, n_inst, skipped, wall, timed = oracle_sample(pool, problems, strikes,
-                                                              max(3.0, args.cpu_seconds / 3), ncores)
+                                                              args.cpu_seconds, ncores)
         if i >= args.warmup:
             rates.append(rate)
     value = statistics.mean(rates)
