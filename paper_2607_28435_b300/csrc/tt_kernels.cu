@@ -1100,8 +1100,11 @@ __global__ void k_readout(const int* list, int count, int* counter, const InstPa
     // than 1e-6 S0 max(1, e^{-alpha k}) the discrete sum has not resolved the
     // integrand: the factor e^{-alpha k} of the price amplifies the sum's own
     // rounding at far strikes (Sec. 4), so the band widens with it there.
-    // The bounds are evaluated in FP32, well inside the band.
+    // The test runs in FP32 (a float price is good to ~6e-8 relative, far
+    // inside the band); the wide band is formed only for a price outside the
+    // narrow one.
     bool out_of_bounds = false;
+    const float s0f = (float)prm.S0, discf = (float)prm.disc, band0 = 1e-6f * s0f;
     for (int i = threadIdx.x; i < q; i += blockDim.x) {
       const long long u = lb + ((long long)i << tbits[inst]);
       const int c = (int)((u >> t) & ((1 << h) - 1));
@@ -1114,9 +1117,12 @@ __global__ void k_readout(const int* list, int count, int* counter, const InstPa
       const double km = prm.k0 + prm.dk * (double)u;
       pr[i] = price;
       lk[i] = log(prm.S0) + km;
-      const double lower = fmax(prm.S0 * (1.0 - (double)expf((float)km) * prm.disc), 0.0);
-      const double band = 1e-6 * prm.S0 * fmax(1.0, (double)expf((float)(-prm.alpha * km)));
-      out_of_bounds |= !(price >= lower - band && price <= prm.S0 + band);
+      const float pf = (float)price, kf = (float)km;
+      const float lower = fmaxf(s0f * (1.0f - expf(kf) * discf), 0.0f);
+      if (!(pf >= lower - band0 && pf <= s0f + band0)) {
+        const float band = band0 * fmaxf(1.0f, expf(-(float)prm.alpha * kf));
+        out_of_bounds |= !(pf >= lower - band && pf <= s0f + band);
+      }
     }
     if (__syncthreads_or(out_of_bounds) && threadIdx.x == 0) status[inst] = SFFT_EBOUNDS_DEV;
   WORK_LOOP_END
