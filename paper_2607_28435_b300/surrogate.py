@@ -362,10 +362,18 @@ def main(argv=None):
         t0 = time.perf_counter()
         sur.sfft_prices(q[:4096])
         sfft_rate = 4096 / (time.perf_counter() - t0)
+        # end to end: the network where trusted, one SFFT instance per other query
+        Bs = min(B, 1 << 16)
+        t0 = time.perf_counter()
+        _, used = sur.price(q[:Bs])
+        torch.cuda.synchronize()
+        served = Bs / (time.perf_counter() - t0)
         out = {"surrogate": st, "queries": B, "network_queries_per_s": B / (ms * 1e-3),
                "network_ms": ms, "network_fp32_tflops": flops / (ms * 1e-3) / 1e12,
                "sfft_one_instance_per_query_per_s": sfft_rate,
-               "gain": B / (ms * 1e-3) / sfft_rate}
+               "gain": B / (ms * 1e-3) / sfft_rate,
+               "served": {"queries": Bs, "network_share": float(used.mean()), "queries_per_s": served,
+                          "gain_over_sfft_alone": served / sfft_rate}}
         print(json.dumps(out), flush=True)
     finally:
         pricer.close()
