@@ -123,6 +123,13 @@ def test_small_fit_and_serving(mods):
         if used.any():
             assert np.max(np.abs(out[used] - 100.0 * Yh[used])) <= 1e-2 * 100.0
         assert np.allclose(out[~used], 100.0 * Yh[~used], rtol=0, atol=1e-8 * 100.0)
+        # a chain (one parameter set, many strikes) shares one fallback instance
+        # and prices as the per-query instances do
+        chain = np.repeat(Xh[:1], 40, axis=0)
+        chain[:, 7] = Xh[:40, 7] if np.all(Xh[:40, :7] == Xh[0, :7]) else np.linspace(lo[7], hi[7], 40)
+        single = np.concatenate([sur.sfft_prices(chain[j:j + 1]) for j in range(0, 40, 13)])
+        shared = sur.sfft_prices(chain)[::13]
+        assert np.allclose(shared, single, rtol=0, atol=1e-8 * 100.0)
         # out of the box: answered by the SFFT pricer at the nearest grid strike
         far = Xh[:3].copy()
         far[:, 7] = 1.0  # log-moneyness outside [-0.4, 0.4]
