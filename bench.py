@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the oracle check of a sample of the timed output")
     return ap.parse_args()
 
 
@@ -93,6 +95,77 @@ def _oracle_task(args):
     u = wl.strike_set(lb, st, q)
     cm.prices(prob, u, route="sparse")
     return q, time.perf_counter() - t0
+
+
+def _oracle_prices_task(args):
+    """Oracle prices (direct sum over the integrand support) of one instance
+    at listed grid indices."""
+    from oracle import carr_madan as cm
+    import numpy as np
+    prob, u = args
+    c, _ = cm.prices(prob, np.asarray(u, dtype=np.int64), route="sparse")
+    return c
+
+
+def _support_task(prob):
+    from oracle import carr_madan as cm
+    return int(cm.support_limit(prob))
+
+
+def accuracy_sample(pool, problems, strikes, status, prices, seed=17, per_cell=8, wide=48,
+                    max_support=1 << 24, strikes_per_inst=8):
+    """Check a seeded sample of one timed step's output against the oracle.
+
+    The sample covers every (model, n) cell of the batch with up to
+    `per_cell` instances (3 models x 19 grid exponents), plus `wide`
+    instances whose integrand support exceeds 2^14 points (the ones the
+    cross builder takes), each at `strikes_per_inst` strikes: both ends of
+    its window and random ones. Instances whose direct sum would run over
+    more than `max_support` points are left out and counted. prices: host
+    array of the step's output. Returns the accuracy record of the bench line."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    offs = np.concatenate([[0], np.cumsum([s[2] for s in strikes])])
+    sup = pool.map(_support_task, problems, chunksize=64)
+    ok = [i for i, st in enumerate(status) if st == 0]
+    cells = {}
+    for i in ok:
+        cells.setdefault((problems[i].model, problems[i].n), []).append(i)
+    picks = []
+    too_wide = 0
+    for key in sorted(cells):
+        idx = [i for i in cells[key] if sup[i] <= max_support]
+        too_wide += len(cells[key]) - len(idx)
+        picks += [int(i) for i in rng.permutation(idx)[:per_cell]]
+    wide_all = [i for i in ok if sup[i] > (1 << 14)]
+    wide_ok = [i for i in wide_all if sup[i] <= max_support and i not in set(picks)]
+    picks += [int(i) for i in rng.permutation(wide_ok)[:wide]]
+    tasks, where = [], []
+    for i in picks:
+        lb, st, q = strikes[i]
+        k = np.unique(np.concatenate([[0, q - 1], rng.integers(0, q, max(strikes_per_inst - 2, 0))]))
+        tasks.append((problems[i], (lb + st * k).tolist()))
+        where.append(offs[i] + k)
+    t0 = time.perf_counter()
+    refs = pool.map(_oracle_prices_task, tasks, chunksize=1)
+    wall = time.perf_counter() - t0
+    errs = np.array([float(np.max(np.abs(prices[w] - r))) / problems[i].S0
+                     for i, w, r in zip(picks, where, refs)])
+    models = sorted({problems[i].model for i in picks})
+    return {"max_abs_err_over_S0": float(errs.max()) if len(errs) else None,
+            "median_abs_err_over_S0": float(np.median(errs)) if len(errs) else None,
+            "instances": len(picks), "strikes": int(sum(len(w) for w in where)),
+            "over_1e-8": int((errs > 1e-8).sum()), "over_1e-6": int((errs > 1e-6).sum()),
+            "n_covered": sorted({problems[i].n for i in picks}),
+            "models_covered": models,
+            "wide_support_instances": int(sum(1 for i in picks if sup[i] > (1 << 14))),
+            "wide_support_in_batch": len(wide_all),
+            "left_out_support_over": {"points": max_support, "instances": too_wide},
+            "oracle_seconds": wall,
+            "how": "after the timed steps: a seeded sample of the last timed step's device output, up "
+                   f"to {per_cell} instances per (model, n) cell plus {wide} of the wide-support "
+                   "(cross-built) instances, each at both ends of its window and random strikes, "
+                   "against the oracle's FP64 direct sum over the integrand support"}
 
 
 def _oracle_pieces(problems, strikes, skipped, seed=0):
@@ -282,6 +355,11 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
 
     ok = [s == 0 for s in status]
     q_ok = sum(s[2] for s, o in zip(strikes, ok) if o)
+    # accuracy of the timed output itself (off the clock): the last timed
+    # step's prices against the oracle on a seeded sample of the batch
+    accuracy = None
+    if pool is not None and rank == 0 and not args.no_accuracy:
+        accuracy = accuracy_sample(pool, problems, strikes, list(status), prices.cpu().numpy())
     tot_s, q_all = reduce_over_ranks(sum(step_ms) / 1e3, q_ok, world, dev)
     value = q_all * args.steps / tot_s
 
@@ -364,7 +442,7 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
         dense = dense_baseline(pricer, problems, strikes, torch, dev)
 
     cpu = None
-    if pool is not None and rank == 0:
+    if pool is not None and rank == 0 and not args.no_cpu:
         rate, one_rate, n_inst, skipped, wall, timed = oracle_sample(pool, problems, strikes,
                                                                      args.cpu_seconds, ncores)
         cpu = {"value": rate, "unit": UNIT, "cores": ncores, "kind": "oracle", "one_core_value": one_rate,
@@ -408,6 +486,7 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
         "represented": {"value": rep_pts * args.steps / tot_s if tot_s > 0 else None,
                         "unit": "grid points/s"},
         "per_strike": {"fp64_flop": sum(v["flops"] for v in prof.values()) / args.steps / max(q_ok, 1)},
+        "accuracy": accuracy,
         "graph_replay": graph,
         "cpu_baseline": cpu,
         "dense_fft": dense,
@@ -530,7 +609,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     ncores = len(os.sched_getaffinity(0))
     pool = None
-    if rank == 0 and (args.impl == "reference" or not args.no_cpu):
+    if rank == 0 and (args.impl == "reference" or not args.no_cpu or not args.no_accuracy):
         pool = oracle_pool(ncores)
     if args.impl == "reference":
         if rank == 0:

@@ -86,7 +86,12 @@ typedef struct {
   int32_t model;    /* sfft_model */
   int32_t quad;     /* sfft_quad */
   int32_t n;        /* grid exponent, M = 2^n, 1 <= n <= SFFT_MAX_N */
-  int32_t max_rank; /* cap on TT ranks; 0 -> SFFT_DEFAULT_MAX_RANK */
+  int32_t max_rank; /* cap on the ranks of the integrand TT and of the rounded
+                       output TT (a builder or rounding step that needs more
+                       sets SFFT_ERANK); 0 -> SFFT_DEFAULT_MAX_RANK. The
+                       intermediate ranks of the zip-up contraction, which the
+                       rounding then lowers, are bounded only by the core-slot
+                       capacity SFFT_MAX_RANK */
   double p[8];      /* model parameters, see sfft_model */
   double S0;        /* spot, > 0 */
   double r;         /* risk-free rate */
@@ -97,7 +102,10 @@ typedef struct {
   double k0;        /* must be NaN (default grid start); reserved */
 } sfft_problem;
 
-/* Per-instance diagnostics. */
+/* Per-instance diagnostics. Build and core times are not kept per instance:
+ * a batch's instances run concurrently, so the per-phase device times of a
+ * whole call (integrand build, zip-up, rounding, readout, ...) come from the
+ * profiling API (sfft_profile_enable / sfft_profile_read) instead. */
 typedef struct {
   int32_t status;    /* sfft_status of this instance */
   int32_t int_rank;  /* max rank of the integrand TT */
@@ -125,6 +133,28 @@ sfft_status sfft_destroy(sfft_ctx *ctx);
 /* Make all later device work of this context run on `cuda_stream`
  * (a cudaStream_t; NULL = legacy default stream). */
 sfft_status sfft_set_stream(sfft_ctx *ctx, void *cuda_stream);
+
+/* Hand-off counts of the last sfft_price_batch call on this context (host
+ * array of 4): how many instances the first-tier launches of the TT-SVD
+ * builder, the cross builder, the zip-up and the output rounding passed on to
+ * their full-size second tier. A first-tier launch runs several CTAs per SM on
+ * a small shared-memory carve; an instance whose panels or ranks outgrow that
+ * carve is handed on, before any of its outputs is written, and the second
+ * tier prices it from its unmodified inputs. Synchronises the context's
+ * stream. Zeros before the first call.
+ *
+ * Test hooks (environment variables read by sfft_create; host side only,
+ * nothing faults or stalls the device):
+ *   SFFT_TIER1="build=8,round=6,cross=4,zipq=40,zipw=900" narrows the
+ *     first-tier limits (builder panel columns, rounding rank, cross rank,
+ *     zip-up panel columns, zip-up panel elements factored in shared memory)
+ *     so that hand-offs and the global-memory factorisation paths run;
+ *   SFFT_FAULT="enomem:<workspace>[:<times>]" fails that workspace's
+ *     allocations with SFFT_ENOMEM; "jacobi:<sweeps>" caps the Jacobi sweeps
+ *     of every SVD of a pricing call (non-convergence reports SFFT_ENOCONV);
+ *     "enoconv:<position>" makes the builder result of that position among the
+ *     call's valid instances SFFT_ENOCONV. Items are separated by ';'. */
+sfft_status sfft_tier2_counts(sfft_ctx *ctx, int32_t *counts);
 
 /* Strike selection helper (host only, no device work). For grid indices
  * u in [0, M) with log-moneyness k'_u in [lo_logm, hi_logm], returns the
@@ -261,11 +291,14 @@ sfft_status sfft_tt_apply_qft(sfft_ctx *ctx, int32_t n, const int32_t *in_ranks,
  *   errbuf, errlen       optional host buffer for a readable error message
  * Sizes beyond the limits are rejected with SFFT_EINVAL and a message in
  * errbuf. The first call on a device (the current one) looks up the array's
- * device address and sets the kernel's shared-memory limit; make that first
- * call before any stream capture. Every call shares the one array and leaves
- * its contents behind (the status word is cleared at the start of each call),
- * so calls that overlap on the GPU, on any streams or threads, race. Returns
- * after the stream has completed the call's work. */
+ * device address and sets the kernel's shared-memory limit. Every call shares
+ * the one array and leaves its contents behind (the status word is cleared at
+ * the start of each call), so calls that overlap on the GPU, on any streams or
+ * threads, race. The call blocks: it copies ranks and status between host and
+ * device and synchronises `stream` twice, so it returns only after the stream
+ * has completed its work, and it must not be called while `stream` (or the
+ * legacy stream) is being captured into a CUDA graph. When the output capacity
+ * is too small, SFFT_EINVAL is returned and out_ranks is left untouched. */
 #define SFFT_NOALLOC_MAX_N 48
 #define SFFT_NOALLOC_SCRATCH_BYTES 3473920
 sfft_status sfft_tt_round_noalloc(int32_t n, int32_t d, const int32_t *in_ranks,

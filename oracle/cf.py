@@ -61,9 +61,3 @@ def psi1(model: int, p, r: float, T: float, alpha: float, v):
     num = phi1(model, p, r, T, v - 1j * (alpha + 1.0))
     den = (alpha + 1j * v) * (alpha + 1.0 + 1j * v)
     return np.exp(-r * T) * num / den
-
-
-def moment(model: int, p, r: float, T: float, power: float) -> float:
-    """E[(S_T/S0)^power] = phi1(-i * power) (real), used by the damping
-    condition of Eq. damping_moment_condition with power = alpha + 1."""
-    return float(np.real(phi1(model, p, r, T, np.array([-1j * power]))[0]))

@@ -142,13 +142,6 @@ def qft_bitrev_product_form(n):
     return np.exp(-2j * math.pi * ph) / math.sqrt(M)
 
 
-def mpo_apply_dense(mpo_cores, tt_cores):
-    """Q x for dense reconstructions (small n only)."""
-    Q = mpo_full(mpo_cores)
-    x = tt_full(tt_cores).reshape(-1)
-    return Q @ x
-
-
 def rank1_exp_tt(gamma, n):
     """Rank-one TT of g(lambda) = exp(gamma * x(lambda)), x = sum lambda_l 2^-l
     (Sec. 3.3): core l holds [1, exp(gamma 2^-l)]."""

@@ -94,7 +94,11 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
                         const long long* b_off, int* b_ranks_all, int core_stride_a,
                         int core_stride_w, int core_stride_b, cd* scratch,
                         long long scratch_stride, int* status, int hb, double* acc, int vcap, int* defer,
-                        const int* dcount);
+                        const int* dcount, int qmax1, int wlim);
+// Jacobi sweep limit of the SVDs in the TT kernels (test hook; default 60),
+// enqueued on `stream`. The value is taken from pageable host memory before
+// the call returns; not for use while the stream is being captured.
+cudaError_t sfft_set_jacobi_cap(int sweeps, cudaStream_t stream);
 __global__ void k_readout(const int* list, int count, int* counter, const InstParams* P,
                           const cd* B, const long long* b_off,
                           const int* b_ranks_all, int core_stride, const long long* l_begin,

@@ -557,6 +557,11 @@ static __device__ int stream_qr(const cd* Z, long long q, int p, int ldz, cd* W,
   return nR;
 }
 
+// Jacobi sweep limit of ts_svd (60). A context's fault-injection hook lowers
+// it to make the SVDs report non-convergence (SFFT_ENOCONV) without any
+// device fault; every kernel reads it at each factorisation.
+static __device__ int la_jacobi_cap = 60;
+
 static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, int wcap, cd* V,
                         double* sig, cd* taus, int* sh_flag) {
   const int hb = wcap / p - p;
@@ -571,7 +576,8 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
   __syncthreads();
   TsSvd out;
   out.m = m;
-  out.sweeps = hestenes(V, p, p, m, 60, sh_flag);
+  const int cap = la_jacobi_cap;
+  out.sweeps = hestenes(V, p, p, m, cap, sh_flag);
   {
     // QR of the stacked row blocks, Jacobi sweeps, norms and sort
     double f = 0.0;
@@ -582,7 +588,7 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
       carried = carried + b < p ? carried + b : p;
       rows -= b;
     }
-    out.flops = f + flops_hestenes(p, m, out.sweeps < 0 ? 60 : out.sweeps) + (double)(4 * p * m);
+    out.flops = f + flops_hestenes(p, m, out.sweeps < 0 ? cap : out.sweeps) + (double)(4 * p * m);
   }
   // column norms
   double* nrm = reinterpret_cast<double*>(W);  // W is free now

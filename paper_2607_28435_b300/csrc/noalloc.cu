@@ -170,11 +170,15 @@ extern "C" sfft_status sfft_tt_round_noalloc(int32_t n, int32_t d, const int32_t
   }
   long long need = 0;
   for (int s = 0; s < n; ++s) need += (long long)rk[s] * d * rk[s + 1];
-  for (int s = 0; s <= n; ++s) out_ranks[s] = rk[s];
   if (need > cap) {
-    say(errbuf, errlen, "output capacity too small for the rounded cores");
+    // out_ranks is left as the caller passed it
+    char m[160];
+    snprintf(m, sizeof m, "output capacity %lld complex is below the %lld the rounded cores need",
+             (long long)cap, need);
+    say(errbuf, errlen, m);
     return SFFT_EINVAL;
   }
+  for (int s = 0; s <= n; ++s) out_ranks[s] = rk[s];
   o = 0;
   for (int s = 0; s < n; ++s) {
     const long long sz = (long long)rk[s] * d * rk[s + 1];

@@ -6,6 +6,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -82,6 +83,22 @@ struct sfft_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;
   double prof_ms[SFFT_NPHASE_DEV] = {0};
   long long prof_launches[SFFT_NPHASE_DEV] = {0};
+  // tier-1 limits of the two-tier launches (defaults: the carves' own
+  // limits; the SFFT_TIER1 test hook narrows them to force hand-offs)
+  struct Tier1 {
+    int build_p = 32;    // TT-SVD builder: panel columns (2 r)
+    int round_r = 24;    // output rounding: rank
+    int cross_r = 16;    // cross builder: rank
+    int zip_q = LA_MAXQ; // zip-up: panel columns (s' r')
+    int zip_w = 1 << 30; // zip-up: panel elements factored in shared memory
+  } t1;
+  // fault-injection test hooks (SFFT_FAULT), all on the host side
+  std::string fault_enomem;    // workspace whose allocations fail
+  int fault_enomem_left = 0;   // how many more times (< 0: always)
+  int fault_jacobi = 0;        // > 0: Jacobi sweep limit during pricing calls
+  int fault_enoconv = -1;      // >= 0: that batch position reports SFFT_ENOCONV
+  // hand-off counts of the last TT pricing call's two-tier launches (device)
+  int* defer_heads[4] = {nullptr, nullptr, nullptr, nullptr};
   // while a graph is being captured: host data of every upload is first
   // copied into this pinned arena (a captured copy must read pinned memory
   // that outlives the capture)
@@ -118,6 +135,10 @@ sfft_status set_err(sfft_ctx* ctx, sfft_status s, const char* fmt, ...) {
 
 sfft_status ensure(sfft_ctx* ctx, const char* name, size_t bytes, void** out) {
   DevBuf& b = ctx->bufs[name];
+  if (ctx->fault_enomem_left != 0 && ctx->fault_enomem == name) {
+    if (ctx->fault_enomem_left > 0) --ctx->fault_enomem_left;
+    return set_err(ctx, SFFT_ENOMEM, "allocation of %s (%zu bytes) failed: injected by SFFT_FAULT", name, bytes);
+  }
   if (b.bytes < bytes) {
     if (b.p) {
       cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -559,6 +580,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   // TT-SVD builder: tier 1 panels up to kSmallP columns in 128-thread CTAs,
   // several per SM; tier 2 the full carve for the instances tier 1 handed on
   const size_t bsmem1 = la::ts_svd_smem_bytes(kSmallP, kSmallP) + 256;
+  const int build_p1 = std::min(ctx->t1.build_p, kSmallP);
   const int bgrid1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, bsmem1,
                                                                 kThreadsSmall));
   const int bgrid2 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem));
@@ -593,7 +615,8 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     PhaseScope ps(ctx, PH_CROSS);
     k_integrand_cross<<<xgrid1, kThreadsSmall, xsmem1, ctx->stream>>>(
         b.P, cross_dev, cnt, ctr + 1, cross_scratch, 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2, b.a_ranks,
-        b.status, xhb, acc_ptr(ctx), kCrossSweeps, xp, kCrossSmallR, defer_cross, list_counts + 1);
+        b.status, xhb, acc_ptr(ctx), kCrossSweeps, xp, std::min(ctx->t1.cross_r, kCrossSmallR), defer_cross,
+        list_counts + 1);
   }
   {
     PhaseScope ps(ctx, PH_CROSS);
@@ -616,7 +639,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     PhaseScope ps(ctx, PH_BUILD);
     k_integrand_ttsvd<<<bgrid1, kThreadsSmall, bsmem1, ctx->stream>>>(
         b.P, m_dev, svd_dev, cnt, ctr + 0, build_scratch, sstride, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
-        b.a_ranks, b.status, kSmallP, acc_ptr(ctx), kSmallP, defer_build, list_counts);
+        b.a_ranks, b.status, kSmallP, acc_ptr(ctx), build_p1, defer_build, list_counts);
   }
   {
     PhaseScope ps(ctx, PH_BUILD);
@@ -632,6 +655,12 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   CK(cudaStreamWaitEvent(ctx->stream, ctx->join, 0));
   CK(side_err);
   CK(main_err);
+  if (ctx->fault_enoconv >= 0 && ctx->fault_enoconv < cnt) {
+    // test hook: the builder of this batch position reports non-convergence
+    static const int kEnoconv = SFFT_ENOCONV;
+    CK(cudaMemcpyAsync(b.status + ctx->fault_enoconv, &kEnoconv, sizeof(int), cudaMemcpyHostToDevice,
+                       ctx->stream));
+  }
   if (!apply) return SFFT_OK;
 
   // MPO per instance
@@ -650,6 +679,9 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   if ((s = ensure(ctx, "defer_zip", sizeof(int) * (cnt + 1), &p))) return s;
   defer_zip = reinterpret_cast<int*>(p);
   CK(cudaMemsetAsync(defer_zip, 0, sizeof(int), ctx->stream));
+  ctx->defer_heads[0] = defer_build;
+  ctx->defer_heads[1] = defer_cross;
+  ctx->defer_heads[2] = defer_zip;
   const RoundSmem zs1 = zip_smem(true);
   const RoundSmem zs = zip_smem();
   const int zg1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, zs1.bytes));
@@ -662,7 +694,8 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
         all_dev, cnt, ctr + 3, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
         reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
         SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
-        SFFT_ZIP_SCRATCH, b.status, zs1.hb, acc_ptr(ctx), zs1.vcap, defer_zip, nullptr);
+        SFFT_ZIP_SCRATCH, b.status, zs1.hb, acc_ptr(ctx), zs1.vcap, defer_zip, nullptr, ctx->t1.zip_q,
+        ctx->t1.zip_w);
   }
   CK(cudaGetLastError());
   {
@@ -671,12 +704,13 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
         defer_zip + 1, 0, ctr + 9, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
         reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
         SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
-        SFFT_ZIP_SCRATCH, b.status, zs.hb, acc_ptr(ctx), zs.vcap, nullptr, defer_zip);
+        SFFT_ZIP_SCRATCH, b.status, zs.hb, acc_ptr(ctx), zs.vcap, nullptr, defer_zip, LA_MAXQ, ctx->t1.zip_w);
   }
   CK(cudaGetLastError());
   // tier 1: ranks up to kSmallRoundR in 128-thread CTAs; tier 2: the rest
-  const RoundSmem rs1 = round_smem(2, false, kSmallRoundR);
+  const RoundSmem rs1 = round_smem(2, false, std::min(ctx->t1.round_r, kSmallRoundR));
   const RoundSmem rs2 = round_smem(2, false);
+  ctx->defer_heads[3] = defer_round;
   const int grid1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, rs1.bytes, kThreadsSmall));
   const int grid2 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, rs2.bytes));
   if ((s = ensure(ctx, "round_scratch", sizeof(cd) * (size_t)SFFT_ROUND_SCRATCH * std::max(grid1, grid2), &p)))
@@ -788,6 +822,66 @@ sfft_status finish_status(sfft_ctx* ctx, int count, const std::vector<int>& vali
   return first;
 }
 
+// Test hooks, read from the environment when a context is created. They only
+// narrow limits or fail host calls; nothing faults or stalls the device.
+//   SFFT_TIER1="build=8,round=6,cross=4,zipq=40,zipw=900"  tier-1 limits of the
+//     two-tier launches (any subset), so that tests can force hand-offs
+//   SFFT_FAULT="enomem:<workspace>[:<times>]"  that workspace's allocations
+//     fail with SFFT_ENOMEM (every time, or the next <times> times)
+//   SFFT_FAULT="jacobi:<sweeps>"  the SVDs of pricing calls stop after that
+//     many Jacobi sweeps and report SFFT_ENOCONV when not converged
+//   SFFT_FAULT="enoconv:<position>"  the builder result of that position among
+//     a call's valid instances is replaced by SFFT_ENOCONV
+// Several SFFT_FAULT items are separated by ';'.
+void read_test_hooks(sfft_ctx* ctx) {
+  if (const char* t = getenv("SFFT_TIER1")) {
+    std::string str(t);
+    size_t pos = 0;
+    while (pos < str.size()) {
+      size_t end = str.find(',', pos);
+      if (end == std::string::npos) end = str.size();
+      const std::string item = str.substr(pos, end - pos);
+      const size_t eq = item.find('=');
+      if (eq != std::string::npos) {
+        const std::string key = item.substr(0, eq);
+        const int v = atoi(item.c_str() + eq + 1);
+        if (v > 0) {
+          if (key == "build") ctx->t1.build_p = std::max(2, v);
+          else if (key == "round") ctx->t1.round_r = v;
+          else if (key == "cross") ctx->t1.cross_r = v;
+          else if (key == "zipq") ctx->t1.zip_q = v;
+          else if (key == "zipw") ctx->t1.zip_w = v;
+        }
+      }
+      pos = end + 1;
+    }
+  }
+  if (const char* f = getenv("SFFT_FAULT")) {
+    std::string str(f);
+    size_t pos = 0;
+    while (pos < str.size()) {
+      size_t end = str.find(';', pos);
+      if (end == std::string::npos) end = str.size();
+      const std::string item = str.substr(pos, end - pos);
+      const size_t c1 = item.find(':');
+      if (c1 != std::string::npos) {
+        const std::string kind = item.substr(0, c1);
+        const std::string rest = item.substr(c1 + 1);
+        if (kind == "enomem") {
+          const size_t c2 = rest.find(':');
+          ctx->fault_enomem = rest.substr(0, c2);
+          ctx->fault_enomem_left = (c2 == std::string::npos) ? -1 : std::max(0, atoi(rest.c_str() + c2 + 1));
+        } else if (kind == "jacobi") {
+          ctx->fault_jacobi = std::max(1, atoi(rest.c_str()));
+        } else if (kind == "enoconv") {
+          ctx->fault_enoconv = atoi(rest.c_str());
+        }
+      }
+      pos = end + 1;
+    }
+  }
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -829,6 +923,7 @@ sfft_status sfft_create(sfft_ctx** out, int device) {
     return SFFT_ECUDA;
   }
   ctx->num_sms = prop.multiProcessorCount;
+  read_test_hooks(ctx);
   sfft_status s = set_smem_attrs(ctx);
   if (!s && (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
              cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -866,6 +961,18 @@ sfft_status sfft_destroy(sfft_ctx* ctx) {
 sfft_status sfft_set_stream(sfft_ctx* ctx, void* stream) {
   if (!ctx) return SFFT_EINVAL;
   ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+  return SFFT_OK;
+}
+
+sfft_status sfft_tier2_counts(sfft_ctx* ctx, int32_t* counts) {
+  if (!ctx || !counts) return SFFT_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  for (int k = 0; k < 4; ++k) {
+    counts[k] = 0;
+    if (ctx->defer_heads[k])
+      CK(cudaMemcpyAsync(counts + k, ctx->defer_heads[k], sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
   return SFFT_OK;
 }
 
@@ -1029,7 +1136,7 @@ sfft_status sfft_tt_apply_qft(sfft_ctx* ctx, int32_t n, const int32_t* in_ranks,
       nullptr, 1, nullptr, nd, td, md, A, od, reinterpret_cast<int*>(ra), reinterpret_cast<const cd*>(ctx->mpo_pool.p), wd,
       reinterpret_cast<int*>(rw), B, od, reinterpret_cast<int*>(rb), SFFT_CORE_STRIDE_D2,
       SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(scr), SFFT_ZIP_SCRATCH, sd, zs.hb,
-      nullptr, zs.vcap, nullptr, nullptr);
+      nullptr, zs.vcap, nullptr, nullptr, LA_MAXQ, 1 << 30);
   CK(cudaGetLastError());
   const RoundSmem rs = round_smem(2, false);
   k_tt_round<<<1, kThreads, rs.bytes, ctx->stream>>>(nullptr, 1, nullptr, nd, 2, 0, td, md, B, od,
@@ -1193,7 +1300,10 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
     if ((s = get_mpo(ctx, prm[k].n, prm[k].tol, &mp[k]))) return s;
   }
   Batch b;
-  if ((s = run_tt_path(ctx, prm, b, &mp, true))) return s;
+  if (ctx->fault_jacobi > 0) CK(sfft_set_jacobi_cap(ctx->fault_jacobi, ctx->stream));
+  s = run_tt_path(ctx, prm, b, &mp, true);
+  if (ctx->fault_jacobi > 0) CK(sfft_set_jacobi_cap(60, ctx->stream));
+  if (s) return s;
   long long* lb_d;
   long long* off_d;
   int *tb_d, *q_d;

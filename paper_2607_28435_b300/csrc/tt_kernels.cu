@@ -806,14 +806,20 @@ __global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, in
                         const long long* b_off, int* b_ranks_all,
                         int core_stride_a, int core_stride_w, int core_stride_b,
                         cd* scratch, long long scratch_stride,
-                        int* status, int hb, double* acc, int vcap, int* defer, const int* dcount) {
+                        int* status, int hb, double* acc, int vcap, int* defer, const int* dcount,
+                        int qmax1, int wlim) {
   // shared memory: W ((LA_MAXP + hb) x LA_MAXP) for the panel T and, in its
   // spent columns, the explicit Q; V (vcap elements) for the streaming
   // fallback of panels larger than W. A launch without V (vcap <= 1) hands
   // the instances that need it to the full-size launch (defer).
+  // qmax1: most panel columns a launch with defer set keeps (<= LA_MAXQ);
+  // wlim: most panel elements factored directly in shared memory (<= the
+  // carve's W); both are the carve's own limits unless a test narrows them
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb, vcap);
   const int wcap = (LA_MAXP + hb) * LA_MAXP;
+  const int wdir = min(wlim, wcap);
+  const int qfit = min(qmax1, LA_MAXQ);
   const bool has_v = vcap > 1;
   __shared__ int zperm[LA_MAXQ];
   __shared__ double zcn[LA_MAXQ];
@@ -854,7 +860,7 @@ __global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, in
       {
         // a launch without V handles panels of up to LA_MAXQ columns (in W,
         // or in global scratch when larger); the rest go on (uniform over the CTA)
-        const bool fits = s1 * rA1 <= LA_MAXQ;
+        const bool fits = s1 * rA1 <= qfit;
         if (defer && !fits && s < n - 1) {
           defer_instance(defer, inst);
           deferred = true;
@@ -892,7 +898,7 @@ __global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, in
       const int q = s1 * rA1, p = 2 * rc;
       // T = Z^H (p x q, column-major) goes straight to shared memory when it
       // fits: Z's row-major buffer and T's column-major one share the index
-      const bool direct = q <= LA_MAXQ && p * q <= wcap;
+      const bool direct = q <= LA_MAXQ && p * q <= wdir;
       // without V, a panel larger than W is factored in place in the CTA's
       // global scratch instead (same steps, L2-resident)
       const bool gdirect = !direct && !has_v && q <= LA_MAXQ;
@@ -1126,4 +1132,11 @@ __global__ void k_readout(const int* list, int count, int* counter, const InstPa
     }
     if (__syncthreads_or(out_of_bounds) && threadIdx.x == 0) status[inst] = SFFT_EBOUNDS_DEV;
   WORK_LOOP_END
+}
+
+// Jacobi sweep limit of every SVD the kernels of this file run (a test hook of
+// the host runtime; 60 by default). Stream-ordered, so a call can set it for
+// its own launches and restore it after them.
+cudaError_t sfft_set_jacobi_cap(int sweeps, cudaStream_t stream) {
+  return cudaMemcpyToSymbolAsync(la_jacobi_cap, &sweeps, sizeof(int), 0, cudaMemcpyHostToDevice, stream);
 }

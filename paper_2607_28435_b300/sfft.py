@@ -68,6 +68,7 @@ EXPORTS = {
     "sfft_create": (c_int32, [ctypes.POINTER(c_void_p), c_int32]),
     "sfft_destroy": (c_int32, [c_void_p]),
     "sfft_set_stream": (c_int32, [c_void_p, c_void_p]),
+    "sfft_tier2_counts": (c_int32, [c_void_p, ctypes.POINTER(c_int32)]),
     "sfft_strike_window": (c_int32, [ctypes.POINTER(SfftProblem), c_double, c_double, c_int32,
                                      ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
                                      ctypes.POINTER(c_int32)]),
@@ -334,6 +335,14 @@ class Pricer:
 
     def last_error(self) -> str:
         return self.lib.sfft_last_error(self.h).decode()
+
+    def tier2_counts(self):
+        """Instances the last pricing call's first-tier launches handed to their
+        second tier: dict with keys build, cross, zipup, round."""
+        c = (c_int32 * 4)()
+        self._stream()
+        self._check(self.lib.sfft_tier2_counts(self.h, c))
+        return dict(build=c[0], cross=c[1], zipup=c[2], round=c[3])
 
     # -- pricing ------------------------------------------------------------
     def _price(self, fn, problems, strikes, prices=None, log_strikes=None, raise_on_error=True):

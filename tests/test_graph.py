@@ -100,3 +100,36 @@ def test_create_refuses_failing_instance(pricer):
     bad = probs[0].replace(T=-1.0)
     with pytest.raises(sfft.SfftError):
         sfft.Graph(pricer, probs + [bad], strikes + [strikes[0]])
+
+
+def test_replays_match_the_oracle(pricer):
+    # replays before and after an update, checked against the CPU oracle's
+    # FP64 discrete sum at sampled strikes (1e-8 S0), not only against a
+    # direct call
+    from paper_2607_28435_b300 import sfft
+    probs, strikes = _batch(24, 16)
+    g = sfft.Graph(pricer, probs, strikes)
+    rng = np.random.default_rng(16)
+    try:
+        upd = [p.replace(S0=90.0, T=p.T * 0.8, r=0.03) for p in probs]
+        for stmt in (probs, upd):
+            if stmt is upd:
+                g.update(upd)
+            g.prices.fill_(np.nan)
+            g.launch()
+            st, _ = g.status()
+            c = g.prices.cpu().numpy()
+            k = g.log_strikes.cpu().numpy()
+            off, checked = 0, 0
+            for p, (lb, sd, q), s in zip(stmt, strikes, st):
+                if s == 0 and cm.support_limit(p) <= (1 << 20):
+                    u = wl.strike_set(lb, sd, q)
+                    pick = np.unique(np.concatenate([[0, q - 1], rng.integers(0, q, 6)]))
+                    ref, kref = cm.prices(p, u[pick], route="sparse")
+                    assert np.max(np.abs(c[off + pick] - ref)) <= 1e-8 * p.S0, p
+                    assert np.max(np.abs(k[off + pick] - kref)) < 1e-12
+                    checked += 1
+                off += q
+            assert checked >= 16, checked
+    finally:
+        g.close()

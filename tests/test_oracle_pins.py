@@ -171,6 +171,88 @@ def test_put_call_parity_through_negative_damping():
         assert np.max(np.abs(lhs - rhs)) <= 1e-8 * pc.S0, model
 
 
+def test_bs_put_matches_integral_of_the_payoff():
+    # the put of the closed-form module against e^{-rT} E[max(K - S_T, 0)]
+    # under the lognormal law of S_T, integrated numerically
+    S0, r, sig, T = 100.0, 0.05, 0.25, 0.8
+    mu = math.log(S0) + (r - 0.5 * sig * sig) * T
+    sd = sig * math.sqrt(T)
+    for K in (60.0, 95.0, 100.0, 130.0):
+        def dens(s):
+            return math.exp(-0.5 * ((math.log(s) - mu) / sd) ** 2) / (s * sd * math.sqrt(2 * math.pi))
+        val, _ = integrate.quad(lambda s: (K - s) * dens(s), 1e-12, K, epsabs=1e-13, epsrel=1e-13,
+                                limit=400)
+        ref = math.exp(-r * T) * val
+        assert abs(float(cfm.bs_put(S0, K, r, sig, T)) - ref) < 1e-10 * S0, K
+
+
+def test_put_prices_through_negative_damping_match_bs_put():
+    # the oracle's discrete sum with alpha < -1 prices puts; for GBM they are
+    # the closed-form puts up to the discretisation error of config 1
+    p = wl.Problem(cf.GBM, (0.2,), S0=100.0, r=0.05, T=1.0, alpha=-2.5, eta=0.25, n=12)
+    lb, st, q = cm.strike_window(p, qmax=128)
+    u = wl.strike_set(lb, st, q)
+    c, lk = cm.prices(p, u)
+    K = np.exp(lk)
+    sel = (K >= 50.0) & (K <= 150.0)
+    ref = cfm.bs_put(100.0, K[sel], 0.05, 0.2, 1.0)
+    assert np.max(np.abs(c[sel] - ref)) <= 1e-8 * p.S0
+
+
+def _support_cases():
+    """Seeded draws of every model for the support-limit pin: eight per model
+    from the mixed batch's boxes, plus the Heston and VG draws of that batch
+    whose integrands decay slowest (largest support limit at n = 20)."""
+    batch = wl.config3_batch(4096)
+    rng = np.random.default_rng(20)
+    out = [wl.Problem(cf.GBM, (s,), S0=100.0, r=0.025, T=T, alpha=1.5, eta=0.25, n=16)
+           for s, T in ((0.1, 0.1), (0.2, 1.0), (0.4, 3.0), (0.15, 0.3))]
+    for model in (cf.HESTON, cf.MERTON, cf.VG):
+        idx = [i for i, p in enumerate(batch) if p.model == model]
+        out += [batch[i] for i in rng.choice(idx, 8, replace=False)]
+    # slowest decay among the first 600 Heston / VG draws whose support fits n = 20
+    for model in (cf.HESTON, cf.VG):
+        cands = [p.replace(n=20) for p in batch[:1800] if p.model == model]
+        sup = [(cm.support_limit(p), k) for k, p in enumerate(cands)]
+        sup = [t for t in sup if t[0] < (1 << 20)]
+        sup.sort(reverse=True)
+        out += [cands[k] for _, k in sup[:2]]
+    return out
+
+
+def test_support_limit_against_full_grid_sum():
+    # the direct sum stops at support_limit(p); the sum over the whole grid
+    # (own radix-2 FFT over all M points, J = M) must give the same prices
+    # to 1e-11 S0 at every model, so no term that moves a price is dropped
+    worst = 0.0
+    for p0 in _support_cases():
+        for n in (16, 18, 20):
+            p = p0.replace(n=n)
+            J = cm.support_limit(p)
+            lb, st, q = cm.strike_window(p)
+            u = wl.strike_set(lb, st, q)[::max(1, q // 48)]
+            c_sup, _ = cm.prices(p, u, route="sparse", J=J)
+            c_all, _ = cm.prices(p, u, route="fft")
+            e = float(np.max(np.abs(c_sup - c_all))) / p.S0
+            worst = max(worst, e)
+            assert e <= 1e-11, (p.model, p.p, p.T, n, J, e)
+    assert worst > 0.0
+
+
+def test_support_limit_heston_branch_is_not_too_early():
+    # Heston has no closed tail bound: the cut is the first dyadic block whose
+    # samples are all negligible. The tail it drops, summed on the whole grid
+    # beyond J, must be negligible too (and the block below J must not be)
+    batch = wl.config3_batch(600)
+    for p0 in [p for p in batch if p.model == cf.HESTON][:40]:
+        p = p0.replace(n=20)
+        J = cm.support_limit(p)
+        if J >= (1 << 20):
+            continue
+        tail = np.sum(np.abs(cm.integrand(p, np.arange(J, 1 << 20, dtype=np.int64))))
+        assert tail * math.exp(1.5 * 1.5) / math.pi * p.S0 <= 1e-11 * p.S0, (p.p, p.T, J, tail)
+
+
 def test_merton_matches_poisson_series():
     s, lam, mu, dj = PARAMS[cf.MERTON]
     p = wl.Problem(cf.MERTON, (s, lam, mu, dj), S0=100.0, r=0.05, T=0.8, alpha=1.5,
