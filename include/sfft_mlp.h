@@ -34,9 +34,26 @@ extern "C" {
 
 #define SFFT_MLP_MAX_LAYERS 8
 
+/* Arithmetic of the products (sfft_mlp.mode):
+ *   SFFT_MLP_TENSOR_CORES: fifth-generation tensor cores (tcgen05.mma,
+ *     bfloat16 operands, float32 accumulation in tensor memory). The inputs
+ *     enter as the bfloat16 pair hi + lo (hi = bf16(x), lo = bf16(x - hi),
+ *     about 16 significant bits); every hidden activation h_l is rounded to
+ *     the nearest bfloat16 (ties to even) before the next product, and the
+ *     workspace keeps those rounded values, so the backward pass
+ *     differentiates the network as evaluated (the rounding passes gradients
+ *     through unchanged). Needs n_layers >= 2, w_0 <= 8, hidden widths that
+ *     are multiples of 16 in [16, 256], w_L = 1, and 16-byte aligned W_l of
+ *     the layers after the first and workspace (else SFFT_EINVAL).
+ *   SFFT_MLP_CUDA_CORES: float32 CUDA-core products with float32
+ *     activations, any widths. */
+#define SFFT_MLP_TENSOR_CORES 0
+#define SFFT_MLP_CUDA_CORES 1
+
 typedef struct sfft_mlp {
   int32_t n_layers;                          /* L, 1..SFFT_MLP_MAX_LAYERS */
   int32_t width[SFFT_MLP_MAX_LAYERS + 1];    /* w_0 .. w_L, each 1..1024; w_L = 1 */
+  int32_t mode;                              /* SFFT_MLP_TENSOR_CORES or SFFT_MLP_CUDA_CORES */
   const uint16_t *w[SFFT_MLP_MAX_LAYERS];    /* W_l as bfloat16 bits */
   const float *b[SFFT_MLP_MAX_LAYERS];       /* b_l */
 } sfft_mlp;
@@ -52,13 +69,19 @@ int64_t sfft_mlp_workspace_floats(const sfft_mlp *net, int64_t batch);
 sfft_status sfft_mlp_normalize(const double *raw, int64_t batch, int32_t n_in, const double *lo,
                                const double *hi, float *x, int32_t *in_box, void *stream);
 
-/* Forward pass: y (batch floats) = network(x). Either ws holds
+/* Forward pass: y (batch floats) = network(x), in the arithmetic net->mode
+ * names. Either ws holds
  * sfft_mlp_workspace_floats(net, batch) floats, which keep z_l and h_l of
  * every layer for sfft_mlp_backward, or ws is NULL and ws_scratch holds
  * 2 * batch * max(w_1 .. w_{L-1}) floats used as two ping-pong activation
  * buffers (inference). */
 sfft_status sfft_mlp_forward(const sfft_mlp *net, const float *x, int64_t batch, float *y, float *ws,
                              float *ws_scratch, void *stream);
+
+/* Number of tensor-core forward launches whose bounded waits on the tensor
+ * cores expired since the library was loaded (their outputs are not valid);
+ * 0 in a healthy run. Synchronises the device. */
+int32_t sfft_mlp_tc_timeouts(void);
 
 /* Mean squared error of y against t (batch floats each): dy = 2 (y - t) /
  * batch, and *loss (device float, may be NULL) = mean (y - t)^2. */

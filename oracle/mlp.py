@@ -11,6 +11,13 @@ normal CDF Phi(z) = (1 + erf(z / sqrt 2)) / 2, so GELU'(z) = Phi(z) + z phi(z).
 Loss: mean over the batch of (y - t)^2. Gradients by the chain rule, layer by
 layer from the output (reverse-mode differentiation of the above).
 
+Tensor-core arithmetic (act_bf16=True): the products take bfloat16 operands,
+so the network as evaluated there feeds the inputs as the pair hi + lo (hi the
+nearest bfloat16 of the float32 input, lo the nearest bfloat16 of the float32
+remainder) and rounds every hidden activation h_l to the nearest bfloat16
+before the next product. The backward pass differentiates that network with
+the rounding passed through unchanged (its derivative taken as 1).
+
 Parity: pinned by central finite differences of the loss (every weight and
 bias of a small network) and by closed-form GELU values; see
 tests/test_mlp_oracle.py.
@@ -39,42 +46,62 @@ def gelu_grad(z):
     return phi_cdf(z) + z * INV_SQRT_2PI * np.exp(-0.5 * z * z)
 
 
-def forward(weights, biases, x):
+def bf16_pair(x):
+    """hi + lo for float32 inputs x: hi = bfloat16(x), lo = bfloat16(x - hi),
+    the difference taken in float32 (where it is exact)."""
+    xf = np.asarray(x, dtype=np.float32)
+    hi = bf16_round(xf)
+    lo = bf16_round(xf - hi.astype(np.float32))
+    return hi + lo
+
+
+def forward(weights, biases, x, act_bf16=False):
     """x: (B, width[0]). weights[l]: (width[l+1], width[l]); biases[l]:
     (width[l+1],). Returns (y of shape (B,), the pre-activations z_l and the
-    layer inputs h_{l-1}, both per layer)."""
-    h = np.asarray(x, dtype=np.float64)
+    layer inputs h_{l-1}, both per layer). act_bf16: the tensor-core
+    arithmetic described above."""
+    h = bf16_pair(x) if act_bf16 else np.asarray(x, dtype=np.float64)
     zs, hs = [], []
     L = len(weights)
     for l in range(L):
         hs.append(h)
         z = h @ np.asarray(weights[l], dtype=np.float64).T + np.asarray(biases[l], dtype=np.float64)
         zs.append(z)
-        h = gelu(z) if l < L - 1 else z
+        if l < L - 1:
+            h = bf16_round(gelu(z)) if act_bf16 else gelu(z)
+        else:
+            h = z
     return h[:, 0], zs, hs
 
 
-def loss(weights, biases, x, t):
-    y, _, _ = forward(weights, biases, x)
+def loss(weights, biases, x, t, act_bf16=False):
+    y, _, _ = forward(weights, biases, x, act_bf16)
     return float(np.mean((y - np.asarray(t, dtype=np.float64)) ** 2))
 
 
-def backward(weights, biases, x, t):
-    """Gradients of the mean squared error: (dW per layer, db per layer,
-    dL/dy per sample)."""
-    y, zs, hs = forward(weights, biases, x)
-    B = y.shape[0]
-    dy = 2.0 * (y - np.asarray(t, dtype=np.float64)) / B
-    dz = dy[:, None]
+def backward_from(weights, zs, hs, dy):
+    """The chain rule from the output down, given the forward pass's
+    pre-activations zs, layer inputs hs and dL/dy: (dW, db) per layer."""
+    dz = np.asarray(dy, dtype=np.float64)[:, None]
     L = len(weights)
     dW = [None] * L
     db = [None] * L
     for l in range(L - 1, -1, -1):
-        dW[l] = dz.T @ hs[l]
+        dW[l] = dz.T @ np.asarray(hs[l], dtype=np.float64)
         db[l] = dz.sum(axis=0)
         if l > 0:
             dh = dz @ np.asarray(weights[l], dtype=np.float64)
             dz = dh * gelu_grad(zs[l - 1])
+    return dW, db
+
+
+def backward(weights, biases, x, t, act_bf16=False):
+    """Gradients of the mean squared error: (dW per layer, db per layer,
+    dL/dy per sample)."""
+    y, zs, hs = forward(weights, biases, x, act_bf16)
+    B = y.shape[0]
+    dy = 2.0 * (y - np.asarray(t, dtype=np.float64)) / B
+    dW, db = backward_from(weights, zs, hs, dy)
     return dW, db, dy
 
 

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsfft.so")
-SOURCES = ["runtime.cu", "tt_kernels.cu", "dense_fft.cu", "calib.cu", "noalloc.cu", "mlp.cu"]
+SOURCES = ["runtime.cu", "tt_kernels.cu", "dense_fft.cu", "calib.cu", "noalloc.cu", "mlp.cu", "mlp_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -24,7 +24,7 @@ def nvcc() -> str:
 def build(verbose: bool = False, extra=()) -> str:
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
-    deps.append(os.path.join(ROOT, "include", "sfft.h"))
+    deps += [os.path.join(ROOT, "include", h) for h in ("sfft.h", "sfft_mlp.h")]
     if os.path.exists(LIB) and not extra:
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in deps):

@@ -197,6 +197,7 @@ __global__ void k_mlp_adam(long long count, float* p, uint16_t* pb, const float*
 
 bool net_ok(const sfft_mlp* net) {
   if (!net || net->n_layers < 1 || net->n_layers > SFFT_MLP_MAX_LAYERS) return false;
+  if (net->mode != SFFT_MLP_TENSOR_CORES && net->mode != SFFT_MLP_CUDA_CORES) return false;
   for (int l = 0; l <= net->n_layers; ++l)
     if (net->width[l] < 1 || net->width[l] > 1024) return false;
   if (net->width[net->n_layers] != 1) return false;
@@ -228,7 +229,15 @@ sfft_status launch_status() { return cudaGetLastError() == cudaSuccess ? SFFT_OK
 
 }  // namespace
 
+// tensor-core forward pass (mlp_tc.cu)
+bool sfft_mlp_tc_shape_ok(const sfft_mlp* net);
+sfft_status sfft_mlp_forward_tc(const sfft_mlp* net, const float* x, int64_t batch, float* y, float* ws,
+                                cudaStream_t s);
+int sfft_mlp_tc_timeouts_read();
+
 extern "C" {
+
+int32_t sfft_mlp_tc_timeouts(void) { return sfft_mlp_tc_timeouts_read(); }
 
 int64_t sfft_mlp_workspace_floats(const sfft_mlp* net, int64_t batch) {
   if (!net_ok(net) || batch < 0) return -1;
@@ -250,6 +259,10 @@ sfft_status sfft_mlp_forward(const sfft_mlp* net, const float* x, int64_t batch,
     return SFFT_EINVAL;
   if (batch == 0) return SFFT_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (net->mode == SFFT_MLP_TENSOR_CORES) {
+    if (!sfft_mlp_tc_shape_ok(net)) return SFFT_EINVAL;
+    return sfft_mlp_forward_tc(net, x, batch, y, ws, s);
+  }
   const int L = net->n_layers;
   const long long maxw = max_hidden(net);
   const float* h = x;

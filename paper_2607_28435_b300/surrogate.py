@@ -33,7 +33,8 @@ class MLP:
     row-major w_l x w_{l-1}), its bfloat16 image for the products, the
     gradient buffer of the same layout and Adam's two moment buffers."""
 
-    def __init__(self, widths: Sequence[int] = (8, 256, 256, 256, 256, 1), seed: int = 0, device: int = 0):
+    def __init__(self, widths: Sequence[int] = (8, 256, 256, 256, 256, 1), seed: int = 0, device: int = 0,
+                 tensor_cores=None):
         import torch
         self.torch = torch
         self.lib = sfft.load_library()
@@ -63,7 +64,15 @@ class MLP:
         self.v = torch.zeros_like(self.p)
         self.step = 0
         self.refresh_bf16()
+        # products on the tensor cores (bfloat16 activations) when the shape
+        # allows it and the caller did not ask otherwise, else CUDA cores
+        if tensor_cores is None:
+            tensor_cores = self.tc_shape_ok(self.widths)
+        if tensor_cores and not self.tc_shape_ok(self.widths):
+            raise ValueError("tensor-core products need w_0 <= 8 and hidden widths in 16..256, multiples of 16")
+        self.tensor_cores = bool(tensor_cores)
         self.net = sfft.SfftMlp()
+        self.net.mode = sfft.MLP_TENSOR_CORES if self.tensor_cores else sfft.MLP_CUDA_CORES
         self.net.n_layers = self.L
         for l in range(self.L + 1):
             self.net.width[l] = self.widths[l]
@@ -73,6 +82,12 @@ class MLP:
         self.gw = (c_void_p * self.L)(*[_ptr(self.g) + 4 * o for o in self.w_off])
         self.gb = (c_void_p * self.L)(*[_ptr(self.g) + 4 * o for o in self.b_off])
         self._ws = {}
+
+    @staticmethod
+    def tc_shape_ok(widths) -> bool:
+        """Shapes the tensor-core forward pass takes (include/sfft_mlp.h)."""
+        return (len(widths) >= 3 and 1 <= widths[0] <= 8 and widths[-1] == 1
+                and all(16 <= w <= 256 and w % 16 == 0 for w in widths[1:-1]))
 
     # -- helpers ------------------------------------------------------------
     def _stream(self):

@@ -26,8 +26,10 @@ def mods():
     return sfft, surrogate
 
 
-def _random_mlp(surrogate, widths, seed):
-    m = surrogate.MLP(widths, seed=seed)
+def _random_mlp(surrogate, widths, seed, tensor_cores=False):
+    # CUDA-core products (float32 activations) unless asked otherwise: the
+    # tensor-core arithmetic has its own tests (test_mlp_tc.py)
+    m = surrogate.MLP(widths, seed=seed, tensor_cores=tensor_cores)
     rng = np.random.default_rng(seed)
     p = rng.standard_normal(m.count).astype(np.float32) * 0.4
     m.p.copy_(torch.from_numpy(p))
@@ -83,7 +85,7 @@ def test_adam_step_and_bf16_image_match_oracle(mods):
 
 def test_normalize_and_box_flags(mods):
     _, surrogate = mods
-    m = surrogate.MLP((8, 4, 1), seed=1)
+    m = surrogate.MLP((8, 4, 1), seed=1, tensor_cores=False)
     lo, hi = np.array(wl.SURROGATE_LO), np.array(wl.SURROGATE_HI)
     rng = np.random.default_rng(7)
     raw = lo + (hi - lo) * rng.uniform(-0.2, 1.2, size=(257, 8))

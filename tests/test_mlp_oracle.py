@@ -81,3 +81,38 @@ def test_bf16_rounding_cases():
                     dtype=np.float32)
     want = [1.0, 1.0, 1.0 + 2.0 ** -6, -2.5, 3.140625, 1.0 + 2.0 ** -7]
     assert list(mlp.bf16_round(vals)) == want
+
+
+def test_bf16_pair_encoding():
+    # hi is the nearest bfloat16, lo the nearest bfloat16 of the float32
+    # remainder: values a bfloat16 holds have lo = 0; 1 + 2^-10 splits into
+    # 1 and 2^-10 exactly; in general hi + lo is within 2^-16 relative of x
+    x = np.array([1.0, -2.5, 1.0 + 2.0 ** -10, 0.1, -0.7, 3e-3], dtype=np.float32)
+    pair = mlp.bf16_pair(x)
+    assert pair[0] == 1.0 and pair[1] == -2.5
+    assert pair[2] == 1.0 + 2.0 ** -10
+    assert np.all(np.abs(pair - x.astype(np.float64)) <= 2.0 ** -16 * np.abs(x))
+    hi = mlp.bf16_round(x)
+    assert np.all(np.abs(pair - hi) <= 2.0 ** -8 * np.abs(x))
+
+
+def test_bf16_network_rounds_hidden_activations_and_tracks_exact_gradients():
+    W, b = _net((5, 12, 9, 1), 8)
+    rng = np.random.default_rng(9)
+    x = rng.uniform(-1, 1, size=(11, 5)).astype(np.float32)
+    t = rng.standard_normal(11)
+    y, zs, hs = mlp.forward(W, b, x, act_bf16=True)
+    # every hidden activation fed to a product is a bfloat16 value: GELU(z) rounded
+    for l in (1, 2):
+        h = hs[l]
+        assert np.array_equal(h, mlp.bf16_round(h))
+        assert np.all(np.abs(h - mlp.gelu(zs[l - 1])) <= 2.0 ** -8 * np.abs(mlp.gelu(zs[l - 1])) + 1e-300)
+    # the output is linear in the last activations
+    assert np.allclose(y, hs[2] @ W[2][0] + b[2][0], rtol=0, atol=1e-13)
+    # with the rounding passed through, the gradients differ from the exact
+    # float64 network's only by the bfloat16 steps (a few parts in 10^3),
+    # not by a dropped or transposed term
+    dW, db, _ = mlp.backward(W, b, x, t, act_bf16=True)
+    dW0, db0, _ = mlp.backward(W, b, x.astype(np.float64), t)
+    for a, c in zip(dW + db, dW0 + db0):
+        assert np.max(np.abs(a - c)) <= 2e-2 * np.max(np.abs(c)) + 1e-12
