@@ -42,9 +42,12 @@ extern "C" {
  *     the nearest bfloat16 (ties to even) before the next product, and the
  *     workspace keeps those rounded values, so the backward pass
  *     differentiates the network as evaluated (the rounding passes gradients
- *     through unchanged). Needs n_layers >= 2, w_0 <= 8, hidden widths that
- *     are multiples of 16 in [16, 256], w_L = 1, and 16-byte aligned W_l of
- *     the layers after the first and workspace (else SFFT_EINVAL).
+ *     through unchanged). GELU is evaluated there with Hastings' rational
+ *     approximation of erf (Abramowitz & Stegun 7.1.26, absolute error at
+ *     most 1.5e-7), far inside the bfloat16 rounding that follows. Needs n_layers >= 2, w_0 <= 8, hidden widths that
+ *     are multiples of 16 in [16, 256], w_L = 1, and a 16-byte aligned
+ *     workspace and packed weights (net->tc_weights, from sfft_mlp_pack)
+ *     (else SFFT_EINVAL).
  *   SFFT_MLP_CUDA_CORES: float32 CUDA-core products with float32
  *     activations, any widths. */
 #define SFFT_MLP_TENSOR_CORES 0
@@ -56,7 +59,22 @@ typedef struct sfft_mlp {
   int32_t mode;                              /* SFFT_MLP_TENSOR_CORES or SFFT_MLP_CUDA_CORES */
   const uint16_t *w[SFFT_MLP_MAX_LAYERS];    /* W_l as bfloat16 bits */
   const float *b[SFFT_MLP_MAX_LAYERS];       /* b_l */
+  const void *tc_weights;                    /* SFFT_MLP_TENSOR_CORES: the weights in the
+                                                tensor cores' operand layout, written by
+                                                sfft_mlp_pack (16-byte aligned); refresh
+                                                it after every change of the W_l */
 } sfft_mlp;
+
+/* Bytes of the packed weight image of a network the tensor-core path takes
+ * (-1 for any other shape). */
+int64_t sfft_mlp_pack_bytes(const sfft_mlp *net);
+
+/* Write the packed weight image of net's bfloat16 W_l into `packed` (device,
+ * sfft_mlp_pack_bytes(net) bytes, 16-byte aligned): layer 1 as [W_1 | W_1]
+ * (the weights of the hi and lo input halves), every later layer as K-chunks
+ * of 32 in the K-major operand layout of the tensor cores, the output layer's
+ * single row padded with zero rows to 16. */
+sfft_status sfft_mlp_pack(const sfft_mlp *net, void *packed, void *stream);
 
 /* Floats of the workspace that sfft_mlp_forward fills for a later
  * sfft_mlp_backward: z_l and h_l of every layer, batch rows each. */

@@ -234,8 +234,20 @@ bool sfft_mlp_tc_shape_ok(const sfft_mlp* net);
 sfft_status sfft_mlp_forward_tc(const sfft_mlp* net, const float* x, int64_t batch, float* y, float* ws,
                                 cudaStream_t s);
 int sfft_mlp_tc_timeouts_read();
+long long sfft_mlp_tc_packed_bytes(const sfft_mlp* net);
+sfft_status sfft_mlp_tc_pack(const sfft_mlp* net, void* out, cudaStream_t s);
 
 extern "C" {
+
+int64_t sfft_mlp_pack_bytes(const sfft_mlp* net) {
+  if (!net_ok(net) || !sfft_mlp_tc_shape_ok(net)) return -1;
+  return sfft_mlp_tc_packed_bytes(net);
+}
+
+sfft_status sfft_mlp_pack(const sfft_mlp* net, void* packed, void* stream) {
+  if (!net_ok(net) || !sfft_mlp_tc_shape_ok(net) || !packed) return SFFT_EINVAL;
+  return sfft_mlp_tc_pack(net, packed, reinterpret_cast<cudaStream_t>(stream));
+}
 
 int32_t sfft_mlp_tc_timeouts(void) { return sfft_mlp_tc_timeouts_read(); }
 

@@ -50,7 +50,7 @@ MLP_MAX_LAYERS = 8
 class SfftMlp(ctypes.Structure):
     """sfft_mlp of include/sfft_mlp.h: widths and device pointers per layer."""
     _fields_ = [("n_layers", c_int32), ("width", c_int32 * (MLP_MAX_LAYERS + 1)), ("mode", c_int32),
-                ("w", c_void_p * MLP_MAX_LAYERS), ("b", c_void_p * MLP_MAX_LAYERS)]
+                ("w", c_void_p * MLP_MAX_LAYERS), ("b", c_void_p * MLP_MAX_LAYERS), ("tc_weights", c_void_p)]
 
 
 MLP_TENSOR_CORES, MLP_CUDA_CORES = 0, 1
@@ -67,6 +67,8 @@ EXPORTS = {
     "sfft_mlp_backward": (c_int32, [_P_MLP, c_void_p, c_int64, c_void_p, c_void_p,
                                     ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_void_p, c_void_p]),
     "sfft_mlp_tc_timeouts": (c_int32, []),
+    "sfft_mlp_pack_bytes": (c_int64, [_P_MLP]),
+    "sfft_mlp_pack": (c_int32, [_P_MLP, c_void_p, c_void_p]),
     "sfft_mlp_adam": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_float,
                                 ctypes.c_float, ctypes.c_float, ctypes.c_float, c_int64, c_void_p]),
     "sfft_create": (c_int32, [ctypes.POINTER(c_void_p), c_int32]),

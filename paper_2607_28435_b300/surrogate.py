@@ -79,6 +79,14 @@ class MLP:
         for l in range(self.L):
             self.net.w[l] = _ptr(self.p16) + 2 * self.w_off[l]
             self.net.b[l] = _ptr(self.p) + 4 * self.b_off[l]
+        self.packed = None
+        if self.tensor_cores:
+            # the weights in the tensor cores' operand layout, rewritten after
+            # every update of the bfloat16 image
+            nb = int(self.lib.sfft_mlp_pack_bytes(ctypes.byref(self.net)))
+            self.packed = torch.empty(max(nb, 16), dtype=torch.uint8, device=self.dev)
+            self.net.tc_weights = _ptr(self.packed)
+            self._pack()
         self.gw = (c_void_p * self.L)(*[_ptr(self.g) + 4 * o for o in self.w_off])
         self.gb = (c_void_p * self.L)(*[_ptr(self.g) + 4 * o for o in self.b_off])
         self._ws = {}
@@ -104,6 +112,11 @@ class MLP:
             self._ws[name] = b
         return b
 
+    def _pack(self):
+        if self.packed is not None:
+            self._check(self.lib.sfft_mlp_pack(ctypes.byref(self.net), c_void_p(_ptr(self.packed)),
+                                               self._stream()))
+
     def refresh_bf16(self):
         """p16 <- bfloat16(p): an Adam step with learning rate 0 and zero
         gradients leaves p unchanged and writes its bfloat16 image."""
@@ -114,6 +127,8 @@ class MLP:
             self._check(self.lib.sfft_mlp_adam(self.count, c_void_p(_ptr(self.p)), c_void_p(_ptr(self.p16)),
                                                c_void_p(_ptr(gz)), c_void_p(_ptr(mz)), c_void_p(_ptr(vz)),
                                                0.0, 0.9, 0.999, 1.0, 1, self._stream()))
+            if getattr(self, "net", None) is not None:
+                self._pack()
 
     def weights(self) -> Tuple[List[np.ndarray], List[np.ndarray]]:
         """Host copies (float64) of the bfloat16 weights the products use and
@@ -179,6 +194,7 @@ class MLP:
                                            c_void_p(_ptr(self.g)), c_void_p(_ptr(self.m)),
                                            c_void_p(_ptr(self.v)), lr, beta1, beta2, eps, self.step,
                                            self._stream()))
+        self._pack()
 
     def fit(self, x, t, epochs: int, batch: int = 4096, lr: float = 2e-3, lr_end: float = 2e-5):
         """Minibatch Adam over the rows of (x, t) in their stored order (the

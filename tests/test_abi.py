@@ -44,9 +44,11 @@ def test_struct_layout_matches_header():
     # sfft_problem: 4 int32, 8 doubles, 7 doubles
     assert ctypes.sizeof(sfft.SfftProblem) == 4 * 4 + 8 * 8 + 7 * 8
     assert ctypes.sizeof(sfft.SfftInfo) == 4 * 4 + 8
-    # sfft_mlp: n_layers + 9 widths + mode (int32), 4 bytes of padding, then 8 + 8 pointers
-    assert ctypes.sizeof(sfft.SfftMlp) == 11 * 4 + 4 + 16 * 8
+    # sfft_mlp: n_layers + 9 widths + mode (int32), 4 bytes of padding, then
+    # 8 + 8 pointers and the packed-weight pointer
+    assert ctypes.sizeof(sfft.SfftMlp) == 11 * 4 + 4 + 17 * 8
     assert sfft.SfftMlp.w.offset == 48
+    assert sfft.SfftMlp.tc_weights.offset == 48 + 16 * 8
 
 
 def test_status_strings(lib):

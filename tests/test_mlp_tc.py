@@ -8,7 +8,9 @@ Tolerances, from the arithmetic:
     h: float32 accumulation of K products, bounded by 2 K 2^-24 times the sum
     of the magnitudes of the terms (K <= 256);
   * a hidden activation: exactly a bfloat16 value, within the rounding of
-    GELU(z) to bfloat16 (half a step, 2^-8 relative) plus the float32 GELU's own error;
+    GELU(z) to bfloat16 (half a step, 2^-8 relative) plus the error of the
+    kernel's GELU (Hastings' erf approximation, at most 1.5e-7 in erf, so
+    below 1e-7 |z| in GELU, and float32 rounding);
   * end to end, against the reference's own bfloat16 chain: rounding
     decisions taken on float32 and float64 GELU values can differ where the
     two straddle a bfloat16 midpoint, each such flip moving one activation
@@ -87,7 +89,7 @@ def test_layerwise_parity(mods, widths, B):
         hb = hg.astype(np.float32).view(np.uint32)
         assert np.all(hb & 0xFFFF == 0)
         g = ref.gelu(zg)
-        assert np.all(np.abs(hg - g) <= 2.0 ** -8 * np.abs(g) + 1e-7), l
+        assert np.all(np.abs(hg - g) <= 2.0 ** -8 * np.abs(g) + 2e-7 * (1.0 + np.abs(zg))), l
         h_in = hg
     yr = h_in @ W[-1][0] + b[-1][0]
     mag = np.abs(h_in) @ np.abs(W[-1][0]) + abs(b[-1][0])
