@@ -262,7 +262,10 @@ class Surrogate:
 
     def price(self, raw: np.ndarray):
         """raw: (B, 8) host rows (Heston parameters, r, T, log-moneyness).
-        Returns (prices, used_network mask)."""
+        Returns (prices, used_network mask, status): status is 0 for a
+        network answer and the SFFT status of the query's fallback instance
+        otherwise (for example SFFT_EMOMENT, whose price is NaN, or
+        SFFT_EBOUNDS, whose price left the no-arbitrage bounds)."""
         torch = self.mlp.torch
         rd = torch.tensor(np.ascontiguousarray(raw, dtype=np.float64), device=self.mlp.dev)
         x, ib = self.mlp.normalize(rd, self.lo, self.hi)
@@ -270,17 +273,19 @@ class Surrogate:
         out = (y.double() * self.S0).cpu().numpy()
         iT, ik = self.cells(raw, self.lo, self.hi, self.trusted_cells.shape)
         use = ib.cpu().numpy().astype(bool) & self.trusted_cells[iT, ik]
+        status = np.zeros(len(raw), dtype=np.int32)
         miss = np.nonzero(~use)[0]
         if len(miss):
-            out[miss] = self.sfft_prices(raw[miss])
-        return out, use
+            out[miss], status[miss] = self.sfft_prices(raw[miss])
+        return out, use, status
 
-    def sfft_prices(self, raw: np.ndarray, max_span: int = sfft.MAX_STRIKES) -> np.ndarray:
+    def sfft_prices(self, raw: np.ndarray, max_span: int = sfft.MAX_STRIKES):
         """SFFT prices at the grid strike nearest to each query's
-        log-moneyness. Queries with the same seven model and market
-        coordinates (an option chain) share one instance, priced over the
-        contiguous grid range their strikes span when that is at most
-        max_span points; every other query is an instance of its own."""
+        log-moneyness, and each query's status (its instance's sfft status).
+        Queries with the same seven model and market coordinates (an option
+        chain) share one instance, priced over the contiguous grid range their
+        strikes span when that is at most max_span points; every other query
+        is an instance of its own."""
         M = 1 << self.n
         eta = 0.25
         dk = 2.0 * math.pi / (M * eta)
@@ -304,31 +309,45 @@ class Surrogate:
                     probs.append(p)
                     strikes.append((int(u), 1, 1))
                     picks.append(([i], np.zeros(1, dtype=np.int64)))
-        c, _, _, _ = self.pricer.price_batch(probs, strikes, raise_on_error=False)
+        c, _, st, _ = self.pricer.price_batch(probs, strikes, raise_on_error=False)
         c = c.cpu().numpy()
         out = np.empty(len(raw))
+        status = np.empty(len(raw), dtype=np.int32)
         off = 0
-        for (idx, rel), (_, _, q) in zip(picks, strikes):
+        for (idx, rel), (_, _, q), si in zip(picks, strikes, st):
             out[idx] = c[off + rel]
+            status[idx] = si
             off += q
-        return out
+        return out, status
+
+
+MARGINS = (0.3, 0.4, 0.5, 0.7, 1.0)
 
 
 def train_surrogate(pricer, n_train_inst: int = 16384, n_test_inst: int = 1024, epochs: int = 12,
                     seed: int = 260728435, widths=(8, 256, 256, 256, 256, 1), lo=wl.SURROGATE_LO,
-                    hi=wl.SURROGATE_HI, n: int = 16, accept: float = 1e-3, cells=(6, 12), qmax: int = 256):
+                    hi=wl.SURROGATE_HI, n: int = 16, accept: float = 1e-3, cells=(6, 12), qmax: int = 256,
+                    margin=None, batch: int = 4096, lr: float = 2e-3):
     """SFFT prices of n_train_inst box instances at qmax strikes each (16384 x
     256 = 2^22 prices) train the network: many parameter sets with few strikes
     each, since the fit's error is set by how densely the seven model and
-    market coordinates are sampled, not the strikes. n_test_inst further
-    instances give the held-out error per (T, k) cell, which decides where the
-    network is trusted; n_test_inst more, drawn independently, check the
-    trusted cells. Returns (Surrogate, stats)."""
+    market coordinates are sampled, not the strikes. Three further sets of
+    n_test_inst instances, each drawn independently, then serve one purpose
+    each:
+      * held-out: the maximum error per (T, k) cell; a cell is trusted when it
+        is at most margin * accept * S0;
+      * validation: picks the margin (when margin is None), the largest of
+        MARGINS whose trusted cells keep the validation maximum within
+        accept * S0;
+      * confirmation: untouched by either choice, it gives the reported share
+        of queries the network answers and their maximum error.
+    Returns (Surrogate, stats)."""
     torch = pricer.torch
     t0 = time.perf_counter()
     train = wl.heston_surrogate_batch(n_train_inst, seed, n=n, lo=lo, hi=hi)
     test = wl.heston_surrogate_batch(n_test_inst, seed + 1, n=n, lo=lo, hi=hi)
     val = wl.heston_surrogate_batch(n_test_inst, seed + 3, n=n, lo=lo, hi=hi)
+    conf = wl.heston_surrogate_batch(n_test_inst, seed + 4, n=n, lo=lo, hi=hi)
     Xr, Y = sfft_dataset(pricer, train, qmax=qmax, kmin=lo[7], kmax=hi[7])
     perm = np.random.Generator(np.random.PCG64(seed + 2)).permutation(len(Y))
     Xr, Y = Xr[perm], Y[perm]
@@ -338,7 +357,7 @@ def train_surrogate(pricer, n_train_inst: int = 16384, n_test_inst: int = 1024, 
     t = torch.tensor(Y, dtype=torch.float32, device=mlp.dev)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    last = mlp.fit(x, t, epochs)
+    last = mlp.fit(x, t, epochs, batch=batch, lr=lr)
     torch.cuda.synchronize()
     t_fit = time.perf_counter() - t1
     S0 = train[0].S0
@@ -354,22 +373,30 @@ def train_surrogate(pricer, n_train_inst: int = 16384, n_test_inst: int = 1024, 
     cell_err = np.full(cells, np.inf)
     for a, b_, e in zip(iT, ik, eh):
         cell_err[a, b_] = e if not np.isfinite(cell_err[a, b_]) else max(cell_err[a, b_], e)
-    sur = Surrogate(pricer, mlp, cell_err, accept=accept, S0=S0, n=n, lo=lo, hi=hi)
     Xv, ev = errors(val)
     vT, vk = Surrogate.cells(Xv, lo, hi, cells)
-    tv = sur.trusted_cells[vT, vk]
-    # the same fit under other margins: validation share and maximum error
+    # every margin on the validation set: share answered and maximum error
     by_margin = {}
-    for mg in (0.3, 0.4, 0.5, 0.7, 1.0):
+    for mg in MARGINS:
         tm = (cell_err <= mg * accept * S0)[vT, vk]
         by_margin[str(mg)] = [float(tm.mean()), float(ev[tm].max()) if tm.any() else None]
+    if margin is None:
+        ok = [mg for mg in MARGINS if by_margin[str(mg)][1] is None or by_margin[str(mg)][1] <= accept * S0]
+        margin = max(ok) if ok else min(MARGINS)
+    sur = Surrogate(pricer, mlp, cell_err, accept=accept, margin=margin, S0=S0, n=n, lo=lo, hi=hi)
+    # the confirmation set, independent of the held-out and validation sets
+    Xc, ec = errors(conf)
+    cT, ck = Surrogate.cells(Xc, lo, hi, cells)
+    tc_ = sur.trusted_cells[cT, ck]
     stats = {"train_prices": int(len(Y)), "heldout_prices": int(len(eh)), "epochs": epochs,
              "final_loss": last, "heldout_max_abs_err": float(eh.max()),
              "heldout_rms_err": float(np.sqrt(np.mean(eh ** 2))),
              "trusted_cells": int(sur.trusted_cells.sum()), "cells": int(np.prod(cells)),
-             "validation_prices": int(len(ev)), "validation_trusted_fraction": float(tv.mean()),
-             "validation_max_abs_err_trusted": float(ev[tv].max()) if tv.any() else None,
-             "accept_abs": accept * S0, "validation_by_margin": by_margin, "data_s": t_data, "fit_s": t_fit}
+             "margin": margin, "validation_by_margin": by_margin,
+             "confirm_prices": int(len(ec)), "confirm_trusted_fraction": float(tc_.mean()),
+             "confirm_max_abs_err_trusted": float(ec[tc_].max()) if tc_.any() else None,
+             "confirm_max_abs_err_all": float(ec.max()),
+             "accept_abs": accept * S0, "tensor_cores": mlp.tensor_cores, "data_s": t_data, "fit_s": t_fit}
     return sur, stats
 
 
@@ -388,6 +415,7 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=320)
     ap.add_argument("--cells", type=int, nargs=2, default=(6, 12), help="(T, k) cells of the trust table")
     ap.add_argument("--queries", type=int, default=1 << 20)
+    ap.add_argument("--out", default=None, help="also write the JSON record to this file")
     args = ap.parse_args(argv)
     pricer = sfft.Pricer(0)
     try:
@@ -418,7 +446,7 @@ def main(argv=None):
         # end to end: the network where trusted, one SFFT instance per other query
         Bs = min(B, 1 << 16)
         t0 = time.perf_counter()
-        _, used = sur.price(q[:Bs])
+        _, used, _ = sur.price(q[:Bs])
         torch.cuda.synchronize()
         served = Bs / (time.perf_counter() - t0)
         # option chains: 256 parameter sets x 256 strikes; SFFT alone prices
@@ -432,11 +460,12 @@ def main(argv=None):
         sur.sfft_prices(ch)
         chain_sfft = len(ch) / (time.perf_counter() - t0)
         t0 = time.perf_counter()
-        _, used_ch = sur.price(ch)
+        _, used_ch, _ = sur.price(ch)
         torch.cuda.synchronize()
         chain_served = len(ch) / (time.perf_counter() - t0)
         out = {"surrogate": st, "queries": B, "network_queries_per_s": B / (ms * 1e-3),
-               "network_ms": ms, "network_fp32_tflops": flops / (ms * 1e-3) / 1e12,
+               "network_ms": ms, "network_tflops": flops / (ms * 1e-3) / 1e12,
+               "network_arithmetic": "tcgen05 bf16 (tensor cores)" if sur.mlp.tensor_cores else "fp32 CUDA cores",
                "sfft_one_instance_per_query_per_s": sfft_rate,
                "gain": B / (ms * 1e-3) / sfft_rate,
                "served": {"queries": Bs, "network_share": float(used.mean()), "queries_per_s": served,
@@ -445,6 +474,10 @@ def main(argv=None):
                                  "queries_per_s": chain_served, "sfft_alone_queries_per_s": chain_sfft,
                                  "gain_over_sfft_alone": chain_served / chain_sfft}}
         print(json.dumps(out), flush=True)
+        if args.out:
+            with open(args.out, "w") as f:
+                json.dump(out, f, indent=1)
+                f.write("\n")
     finally:
         pricer.close()
 

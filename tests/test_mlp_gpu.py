@@ -116,8 +116,10 @@ def test_small_fit_and_serving(mods):
         Xh, Yh = surrogate.sfft_dataset(pricer, test, kmin=lo[7], kmax=hi[7])
         Xh, Yh = Xh[:2048], Yh[:2048]
         # the fallback's grid mapping: rows that are grid strikes price as in the batch
-        assert np.allclose(sur.sfft_prices(Xh[:16]), 100.0 * Yh[:16], rtol=0, atol=1e-8 * 100.0)
-        out, used = sur.price(Xh)
+        fp, fst = sur.sfft_prices(Xh[:16])
+        assert np.allclose(fp, 100.0 * Yh[:16], rtol=0, atol=1e-8 * 100.0) and not fst.any()
+        out, used, qst = sur.price(Xh)
+        assert not qst.any()
         # the network answers only in trusted cells, within the acceptance
         # there; every other query is the SFFT price itself
         iT, ik = sur.cells(Xh, lo, hi, sur.trusted_cells.shape)
@@ -129,15 +131,15 @@ def test_small_fit_and_serving(mods):
         # and prices as the per-query instances do
         chain = np.repeat(Xh[:1], 40, axis=0)
         chain[:, 7] = Xh[:40, 7] if np.all(Xh[:40, :7] == Xh[0, :7]) else np.linspace(lo[7], hi[7], 40)
-        single = np.concatenate([sur.sfft_prices(chain[j:j + 1]) for j in range(0, 40, 13)])
-        shared = sur.sfft_prices(chain)[::13]
+        single = np.concatenate([sur.sfft_prices(chain[j:j + 1])[0] for j in range(0, 40, 13)])
+        shared = sur.sfft_prices(chain)[0][::13]
         assert np.allclose(shared, single, rtol=0, atol=1e-8 * 100.0)
         # out of the box: answered by the SFFT pricer at the nearest grid strike
         far = Xh[:3].copy()
         far[:, 7] = 1.0  # log-moneyness outside [-0.4, 0.4]
-        out_far, used_far = sur.price(far)
+        out_far, used_far, _ = sur.price(far)
         assert not used_far.any()
-        assert np.allclose(out_far, sur.sfft_prices(far), rtol=0, atol=1e-9 * 100.0)
+        assert np.allclose(out_far, sur.sfft_prices(far)[0], rtol=0, atol=1e-9 * 100.0)
         # throughput: the network against one SFFT instance per query
         B = 1 << 16
         rng = np.random.default_rng(8)
@@ -154,5 +156,63 @@ def test_small_fit_and_serving(mods):
         sur.sfft_prices(q[:512])
         sfft_rate = 512 / (time.perf_counter() - t0)
         assert net_rate > 20 * sfft_rate, (net_rate, sfft_rate)
+    finally:
+        pricer.close()
+
+
+def test_fallback_statuses_reach_the_caller(mods):
+    # a query next to a Heston moment explosion of order alpha + 1 (its
+    # discrete sum leaves the no-arbitrage bounds, SFFT_EBOUNDS) and one whose
+    # moment explodes before T (SFFT_EMOMENT, NaN price) come back flagged,
+    # as does every query of a chain that shares such an instance; ordinary
+    # queries come back 0
+    sfft, surrogate = mods
+    pricer = sfft.Pricer(0)
+    try:
+        net = surrogate.MLP((8, 16, 1), seed=2)
+        sur = surrogate.Surrogate(pricer, net, np.full((6, 12), np.inf))  # trusts no cell
+        bad = wl.heston_surrogate_batch(16384, 260728435)[8441]
+        rows = [list(bad.p) + [bad.r, bad.T, k] for k in (-0.2, 0.0, 0.3)]
+        rows.append(list(bad.p[:2]) + [0.99, 0.0, bad.p[4], 0.0, 2.99, 0.1])   # explodes before T
+        rows.append(list(wl.HESTON_CFG2) + [0.025, 1.0, 0.1])                 # ordinary
+        out, used, st = sur.price(np.array(rows))
+        assert not used.any()
+        assert list(st[:3]) == [sfft.SFFT_EBOUNDS] * 3, st
+        assert st[3] == sfft.SFFT_EMOMENT and np.isnan(out[3])
+        assert st[4] == 0 and np.isfinite(out[4])
+    finally:
+        pricer.close()
+
+
+def test_surrogate_meets_the_acceptance_on_a_reduced_box(mods):
+    # the learned part's acceptance, 1e-3 S0 in the maximum norm, on a reduced
+    # Heston box (0.15 of every parameter range around the box centre,
+    # |log-moneyness| <= 0.4): a fit of about 15 s on the tensor-core path;
+    # trust is decided on the held-out set, the margin on the validation set,
+    # and the figures asserted come from a third, independent set
+    sfft, surrogate = mods
+    pricer = sfft.Pricer(0)
+    try:
+        mid = [0.5 * (a + b) for a, b in zip(wl.SURROGATE_LO, wl.SURROGATE_HI)]
+        span = [b - a for a, b in zip(wl.SURROGATE_LO, wl.SURROGATE_HI)]
+        lo = tuple(m - 0.075 * s for m, s in zip(mid[:7], span[:7])) + (-0.4,)
+        hi = tuple(m + 0.075 * s for m, s in zip(mid[:7], span[:7])) + (0.4,)
+        t0 = time.perf_counter()
+        sur, st = surrogate.train_surrogate(pricer, n_train_inst=4096, n_test_inst=512, epochs=300,
+                                            widths=(8, 256, 256, 256, 1), lo=lo, hi=hi, qmax=256, cells=(4, 6),
+                                            seed=11, lr=3e-3)
+        assert time.perf_counter() - t0 < 90
+        assert st["tensor_cores"]
+        assert st["confirm_trusted_fraction"] >= 0.5, st
+        assert st["confirm_max_abs_err_trusted"] <= 1e-3 * 100.0, st
+        # served queries from fresh instances: network answers within the
+        # acceptance, the rest priced by SFFT itself
+        fresh = wl.heston_surrogate_batch(16, 12345, lo=lo, hi=hi)
+        Xq, Yq = surrogate.sfft_dataset(pricer, fresh, qmax=64, kmin=lo[7], kmax=hi[7])
+        out, used, qst = sur.price(Xq)
+        assert not qst.any()
+        if used.any():
+            assert np.max(np.abs(out[used] - 100.0 * Yq[used])) <= 1e-3 * 100.0
+        assert np.allclose(out[~used], 100.0 * Yq[~used], rtol=0, atol=1e-8 * 100.0)
     finally:
         pricer.close()
