@@ -50,7 +50,9 @@ def batch_problems(args, seed=None):
 def workload_name(args):
     nr = f"n {args.n}" if args.n else "n 16..34"
     tol = "" if args.tol == 1e-12 else f", tol {args.tol:g}"
-    return f"batched TT-SFFT, {args.count} instances (Heston/Merton/VG), {nr}{tol}"
+    mixed = (", MPO contraction in complex FP32 on tcgen05 (QR/SVD FP64)"
+             if getattr(args, "precision", "fp64") == "mixed" else "")
+    return f"batched TT-SFFT, {args.count} instances (Heston/Merton/VG), {nr}{tol}{mixed}"
 
 
 def kernel_src_hash():
@@ -81,6 +83,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the oracle check of a sample of the timed output")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="mixed: the zip-up's MPO contraction in complex FP32 on the tensor cores")
     return ap.parse_args()
 
 
@@ -311,6 +315,8 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
     strikes = [sfft.strike_window(p) for p in problems]
     total_q = sum(s[2] for s in strikes)
     pricer = sfft.Pricer(local_rank)
+    mixed = args.precision == "mixed"
+    pricer.set_precision(mixed)
     fp64_peak = pricer.calibrate_fp64()
     prices = torch.empty(total_q, dtype=torch.float64, device=dev)
     logk = torch.empty(total_q, dtype=torch.float64, device=dev)
@@ -360,6 +366,12 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
     accuracy = None
     if pool is not None and rank == 0 and not args.no_accuracy:
         accuracy = accuracy_sample(pool, problems, strikes, list(status), prices.cpu().numpy())
+    # mixed precision: every strike of every instance against the FP64 path
+    # (itself checked against the oracle), and the FP64 path's phase times
+    mixed_rec = None
+    if mixed and rank == 0:
+        mixed_rec = mixed_vs_fp64(local_rank, batch, prices, list(status), strikes, problems, prof, args, torch,
+                                  np)
     tot_s, q_all = reduce_over_ranks(sum(step_ms) / 1e3, q_ok, world, dev)
     value = q_all * args.steps / tot_s
 
@@ -462,7 +474,8 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+bf16x3 tensor-core contraction (fp32 accumulate)" if mixed else "f64", "data": "synthetic",
         "config": {"workload": workload_name(args),
                    "instances": args.count, "strikes_per_step": total_q, "priced_per_step": q_ok,
                    "failed_instances": int(len(ok) - sum(ok)), "tol": args.tol, "eta": 0.25, "alpha": 1.5,
@@ -487,12 +500,51 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
                         "unit": "grid points/s"},
         "per_strike": {"fp64_flop": sum(v["flops"] for v in prof.values()) / args.steps / max(q_ok, 1)},
         "accuracy": accuracy,
+        "mixed_precision": mixed_rec,
         "graph_replay": graph,
         "cpu_baseline": cpu,
         "dense_fft": dense,
     }
     pricer.close()
     return line
+
+
+def mixed_vs_fp64(device, batch, prices, status, strikes, problems, prof, args, torch, np):
+    """Price the same batch on the FP64 path (a second context, off the
+    clock) and compare every strike of every instance; time the FP64 path's
+    steps with the profiler for its phase times."""
+    from paper_2607_28435_b300 import sfft
+    ref = sfft.Pricer(device)
+    try:
+        p64 = torch.empty_like(prices)
+        k64 = torch.empty_like(prices)
+        ref.price_batch(batch, None, p64, k64, raise_on_error=False)  # warm: MPOs built
+        ref.profile(True)
+        ref.profile_read(reset=True)
+        reps = 3
+        for _ in range(reps):
+            ref.price_batch(batch, None, p64, k64, raise_on_error=False)
+        torch.cuda.synchronize()
+        pr64 = ref.profile_read(reset=True)
+        ref.profile(False)
+    finally:
+        ref.close()
+    a, b = prices.cpu().numpy(), p64.cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum([s[2] for s in strikes])])
+    per = np.array([np.max(np.abs(a[offs[i]:offs[i + 1]] - b[offs[i]:offs[i + 1]])) / problems[i].S0
+                    if status[i] == 0 and offs[i + 1] > offs[i] else 0.0 for i in range(len(problems))])
+    okm = np.array([s == 0 for s in status])
+    pz = prof["zipup"]
+    return {"instances": int(okm.sum()), "strikes": int(sum(s[2] for s, o in zip(strikes, okm) if o)),
+            "max_abs_err_vs_fp64_over_S0": float(per.max()), "median_per_instance": float(np.median(per[okm])),
+            "p99_per_instance": float(np.percentile(per[okm], 99)),
+            "instances_over_1e-6": int((per > 1e-6).sum()),
+            "zipup_ms_per_step": pz["ms"] / args.steps, "zipup_ms_per_step_fp64": pr64["zipup"]["ms"] / reps,
+            "ms_per_step_fp64_profiled": sum(v["ms"] for v in pr64.values()) / reps,
+            "tensor_core_sites_per_step": pz["evals"] / args.steps,
+            "sites_per_step": float(sum(p.n for p, o in zip(problems, okm) if o)),
+            "how": "every strike of every priced instance of the last timed step against the same batch on the "
+                   "FP64 path (second context, off the clock); the FP64 path's times from 3 profiled steps"}
 
 
 def reduce_over_ranks(seconds: float, strikes: int, world: int, device):

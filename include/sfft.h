@@ -134,6 +134,25 @@ sfft_status sfft_destroy(sfft_ctx *ctx);
  * (a cudaStream_t; NULL = legacy default stream). */
 sfft_status sfft_set_stream(sfft_ctx *ctx, void *cuda_stream);
 
+/* Arithmetic of the MPO x TT contraction of this context's pricing calls
+ * (sfft_price_batch, captured batches):
+ *   SFFT_PRECISION_FP64  (default) every step in FP64 on the CUDA cores;
+ *   SFFT_PRECISION_MIXED the zip-up's MPO contraction of each site (Sec. 3.2,
+ *     Eq. complexity_TTO), the complex product of the carried partial result
+ *     with the operator core, runs on the fifth-generation tensor cores in
+ *     complex FP32: one real GEMM in the 4M form [Re X | Im X] against
+ *     [[Re W, Im W], [-Im W, Re W]], each FP32 operand split into three
+ *     bfloat16 pieces (the six products of combined order <= 2, FP32
+ *     accumulation), so its inputs keep FP32 precision.
+ *     The QR and SVD steps, the carry contraction and the readout stay FP64.
+ *     Sites whose panel exceeds one 128-row tile, and the instances the
+ *     first-tier zip-up hands to its second tier, run in FP64. The prices
+ *     then differ from the FP64 path by roughly the FP32 rounding of the
+ *     contraction (checked to 1e-6 S0 at tolerance 1e-7). */
+#define SFFT_PRECISION_FP64 0
+#define SFFT_PRECISION_MIXED 1
+sfft_status sfft_set_precision(sfft_ctx *ctx, int32_t precision);
+
 /* Hand-off counts of the last sfft_price_batch call on this context (host
  * array of 4): how many instances the first-tier launches of the TT-SVD
  * builder, the cross builder, the zip-up and the output rounding passed on to
@@ -321,7 +340,9 @@ sfft_status sfft_profile_enable(sfft_ctx *ctx, int32_t on);
 
 /* Read the accumulated per-phase totals since the last reset (host arrays of
  * SFFT_NPHASES entries each, any may be NULL): device milliseconds, launches,
- * algorithmic FP64 flops (complex multiply-add = 8), integrand evaluations.
+ * algorithmic FP64 flops (complex multiply-add = 8), integrand evaluations
+ * (for the zip-up phase: the number of sites whose MPO contraction ran on
+ * the tensor cores, see sfft_set_precision).
  * Synchronises the context's stream. reset != 0 clears the totals. */
 sfft_status sfft_profile_read(sfft_ctx *ctx, double *ms, double *flops, double *evals,
                               int64_t *launches, int32_t reset);

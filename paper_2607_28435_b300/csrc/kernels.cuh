@@ -32,6 +32,7 @@ enum { PH_PROBE = 0, PH_BUILD = 1, PH_ZIPUP = 2, PH_ROUND = 3, PH_READOUT = 4, P
 #define SFFT_EINVAL_DEV 1
 #define SFFT_ERANK_DEV 5
 #define SFFT_ENOCONV_DEV 6
+#define SFFT_ETIMEOUT_DEV 7
 #define SFFT_EBOUNDS_DEV 8
 
 __global__ void k_sample(const InstParams* P, const long long* j, long long count, cd* x);
@@ -95,6 +96,17 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
                         int core_stride_w, int core_stride_b, cd* scratch,
                         long long scratch_stride, int* status, int hb, double* acc, int vcap, int* defer,
                         const int* dcount, int qmax1, int wlim);
+// The same with the MPO contraction of each site on the tensor cores (tcgen05,
+// FP32 operands as three bfloat16 pieces, FP32 accumulation) wherever one
+// 128-row tile holds it; the QR steps stay FP64.
+__global__ void k_zipup_tc(const int* list, int count, int* counter, const int* n_arr,
+                           const double* tol_arr, const int* maxrank_arr,
+                           const cd* A, const long long* a_off, const int* a_ranks_all,
+                           const cd* Wmpo, const long long* w_off, const int* w_ranks_all, cd* B,
+                           const long long* b_off, int* b_ranks_all, int core_stride_a,
+                           int core_stride_w, int core_stride_b, cd* scratch,
+                           long long scratch_stride, int* status, int hb, double* acc, int vcap, int* defer,
+                           const int* dcount, int qmax1, int wlim);
 // Jacobi sweep limit of the SVDs in the TT kernels (test hook; default 60),
 // enqueued on `stream`. The value is taken from pageable host memory before
 // the call returns; not for use while the stream is being captured.

@@ -92,6 +92,8 @@ struct sfft_ctx {
     int zip_q = LA_MAXQ; // zip-up: panel columns (s' r')
     int zip_w = 1 << 30; // zip-up: panel elements factored in shared memory
   } t1;
+  // arithmetic of the zip-up's MPO contraction (SFFT_PRECISION_*)
+  int precision = SFFT_PRECISION_FP64;
   // fault-injection test hooks (SFFT_FAULT), all on the host side
   std::string fault_enomem;    // workspace whose allocations fail
   int fault_enomem_left = 0;   // how many more times (< 0: always)
@@ -317,6 +319,7 @@ sfft_status set_smem_attrs(sfft_ctx* ctx) {
   CK(cudaFuncSetAttribute(k_tt_round, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)round_smem(4).bytes));
   CK(cudaFuncSetAttribute(k_zipup, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_zipup_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   CK(cudaFuncSetAttribute(k_fft_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
   return SFFT_OK;
 }
@@ -684,13 +687,17 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   ctx->defer_heads[2] = defer_zip;
   const RoundSmem zs1 = zip_smem(true);
   const RoundSmem zs = zip_smem();
-  const int zg1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, zs1.bytes));
+  // mixed precision: tier 1 runs each site's MPO contraction on the tensor
+  // cores; tier 2 (rare, the full carve) stays FP64
+  const bool mixed = ctx->precision == SFFT_PRECISION_MIXED;
+  const void* zip1 = mixed ? (const void*)k_zipup_tc : (const void*)k_zipup;
+  const int zg1 = std::min(cnt, ctx->num_sms * blocks_per_sm(zip1, zs1.bytes));
   const int zg2 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, zs.bytes));
   if ((s = ensure(ctx, "zip_scratch", sizeof(cd) * (size_t)SFFT_ZIP_SCRATCH * std::max(zg1, zg2), &p)))
     return s;
   {
     PhaseScope ps(ctx, PH_ZIPUP);
-    k_zipup<<<zg1, kThreads, zs1.bytes, ctx->stream>>>(
+    (mixed ? k_zipup_tc : k_zipup)<<<zg1, kThreads, zs1.bytes, ctx->stream>>>(
         all_dev, cnt, ctr + 3, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
         reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
         SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
@@ -961,6 +968,12 @@ sfft_status sfft_destroy(sfft_ctx* ctx) {
 sfft_status sfft_set_stream(sfft_ctx* ctx, void* stream) {
   if (!ctx) return SFFT_EINVAL;
   ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+  return SFFT_OK;
+}
+
+sfft_status sfft_set_precision(sfft_ctx* ctx, int32_t precision) {
+  if (!ctx || (precision != SFFT_PRECISION_FP64 && precision != SFFT_PRECISION_MIXED)) return SFFT_EINVAL;
+  ctx->precision = precision;
   return SFFT_OK;
 }
 
@@ -1459,6 +1472,9 @@ sfft_status sfft_graph_create(sfft_ctx* ctx, const sfft_problem* probs, int32_t 
     delete g;
     return set_err(ctx, s, "graph: context creation failed");
   }
+  // the private context prices as the caller's does
+  g->own->precision = ctx->precision;
+  g->own->t1 = ctx->t1;
   // 1. a plain run sizes every workspace and builds the MPOs
   std::vector<int32_t> st(count);
   s = price_common(g->own, probs, count, l_begin, stride, q, prices, log_strikes, st.data(), nullptr, 0);

@@ -13,7 +13,10 @@
 // site sweeps are sequential, the dense algebra inside a site is spread over
 // the CTA. Large per-site panels live in a per-CTA global scratch slice, which
 // stays resident in L2.
+#include <cuda_bf16.h>
+
 #include "kernels.cuh"
+#include "tc.cuh"
 
 using namespace la;
 
@@ -789,6 +792,168 @@ __global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count,
 }
 
 // ---------------------------------------------------------------------------
+// Mixed precision: the zip-up's MPO contraction on the tensor cores
+// ---------------------------------------------------------------------------
+// The panel Z[(a', b'), (c, mu)] = sum_{a, lam} Dt[c][a][lam][b'] conj(W[a][2 mu + lam][a'])
+// is the complex product X Y^T with X[(c, b'), (a, lam)] = Dt[c][a][lam][b']
+// (M = r_c r' rows, K = 2 s columns) and Y[(mu, a'), (a, lam)] =
+// conj(W[a][2 mu + lam][a']) (N = 2 s' rows). In real arithmetic it is the
+// single GEMM D' = A' B'^T with
+//   A' = [Re X | Im X]                        (M x 2K)
+//   B' = [[Re W, Im W], [-Im W, Re W]]        (2N x 2K: rows (mu, a'), then again)
+// so that D'[m, n] = Re Z' and D'[m, N + n] = Im Z' (the 4M form), run as
+// tcgen05.mma kind::f16 on one 128-row tile with FP32 accumulation in tensor
+// memory. Every operand value v is split into three bfloat16 pieces
+// v0 = bf16(v), v1 = bf16(v - v0), v2 = bf16(v - v0 - v1), which hold v to
+// about 2^-25 (FP32 precision), and the six products v_i w_j with i + j <= 2
+// are formed. For each K step of 16 the leading product v0 w0 and the five
+// smaller ones go to two separate accumulators; the step's two partial
+// panels are then added in FP64 into a panel in the CTA's global scratch
+// (L2-resident), so no FP32 sum runs over more than one K step. Long FP32
+// accumulations, compounded over the n sites of the zip-up chain, would
+// otherwise set the price error. The operand tiles live in the shared-memory
+// block W, which the panel may overwrite once the last MMAs have completed.
+struct ZipTc {
+  uint32_t tmem;
+  uint64_t* mbar;
+  uint32_t phase;
+};
+
+// the three bfloat16 pieces of v (split from the FP64 value), as bit patterns
+__device__ __forceinline__ void bf16_split3(double v, uint16_t* b) {
+  const __nv_bfloat16 h0 = __double2bfloat16(v);
+  const double r1 = v - (double)__bfloat162float(h0);
+  const __nv_bfloat16 h1 = __double2bfloat16(r1);
+  const double r2 = r1 - (double)__bfloat162float(h1);
+  const __nv_bfloat16 h2 = __double2bfloat16(r2);
+  b[0] = __bfloat16_as_ushort(h0);
+  b[1] = __bfloat16_as_ushort(h1);
+  b[2] = __bfloat16_as_ushort(h2);
+}
+
+// Operand bytes the contraction needs for M rows, K = 2 s complex columns and
+// N1 = 2 s' complex outputs (0 when one tile cannot hold it: 128 rows, two
+// accumulators of at most 64 columns in the CTA's 128 tensor-memory columns).
+__device__ __forceinline__ int zip_tc_bytes(int M, int K, int N1) {
+  const int kp = (2 * K + 15) & ~15, np = (2 * N1 + 15) & ~15;
+  if (M > 128 || np > 64 || np < 16) return 0;
+  return 3 * (128 + np) * kp * 2;
+}
+
+// Forms the panel in Zg (global scratch, FP64: Zg[idx] = Z, idx = (a' r' +
+// b') p + (c 2 + mu)) and then stores it where the FP64 loop would: the
+// conjugate into sm_panel when given, else into Zg itself (conjugated when
+// conj_out). Returns false when a bounded wait for the MMAs expired.
+__device__ bool zip_panel_tc(const cd* Dt, const cd* Ws, int rc, int s0, int s1, int rA1, unsigned char* opnd,
+                             ZipTc& tz, cd* Zg, cd* sm_panel, int q, int p, bool conj_out) {
+  const int M = rc * rA1, K = 2 * s0, N1 = 2 * s1;
+  const int kp = (2 * K + 15) & ~15, np = (2 * N1 + 15) & ~15;
+  const int kb = 2 * kp;  // bytes of an operand row
+  unsigned char* A[3] = {opnd, opnd + 128 * kb, opnd + 2 * 128 * kb};
+  unsigned char* Bp[3] = {opnd + 3 * 128 * kb, opnd + 3 * 128 * kb + np * kb, opnd + 3 * 128 * kb + 2 * np * kb};
+  // A' rows m = (c, b'), columns (re | im) of (a, lam)
+  for (int e = threadIdx.x; e < 128 * kp; e += blockDim.x) {
+    const int m = e / kp, k = e - m * kp;
+    double v = 0.0;
+    if (m < M && k < 2 * K) {
+      const int c = m / rA1, bp = m - c * rA1;
+      const int kk = k < K ? k : k - K;
+      const int a = kk >> 1, lam = kk & 1;
+      const cd d = Dt[(((size_t)c * s0 + a) * 2 + lam) * rA1 + bp];
+      v = k < K ? d.x : d.y;
+    }
+    uint16_t b[3];
+    bf16_split3(v, b);
+    const uint32_t off = tc::kmajor_off(m, 2 * k, kb);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) *reinterpret_cast<uint16_t*>(A[i] + off) = b[i];
+  }
+  // B' rows n = (mu, a') for the real part, N1 + n for the imaginary part
+  for (int e = threadIdx.x; e < np * kp; e += blockDim.x) {
+    const int n = e / kp, k = e - n * kp;
+    double v = 0.0;
+    if (n < 2 * N1 && k < 2 * K) {
+      const bool imag_row = n >= N1;
+      const int nn = imag_row ? n - N1 : n;
+      const int mu = nn / s1, ap = nn - mu * s1;
+      const bool second = k >= K;
+      const int kk = second ? k - K : k;
+      const int a = kk >> 1, lam = kk & 1;
+      const cd w = Ws[(size_t)a * 4 * s1 + (2 * mu + lam) * s1 + ap];
+      v = imag_row ? (second ? w.x : -w.y) : (second ? w.y : w.x);
+    }
+    uint16_t b[3];
+    bf16_split3(v, b);
+    const uint32_t off = tc::kmajor_off(n, 2 * k, kb);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) *reinterpret_cast<uint16_t*>(Bp[i] + off) = b[i];
+  }
+  tc::fence_proxy_async();
+  const uint32_t idesc = tc::idesc_bf16(128, np);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ngrp = (int)(blockDim.x >> 5) / 4;
+  const int m = 32 * (w & 3) + lane;
+  const int c = m / rA1, bp = m - c * rA1;
+  for (int ks = 0; ks < kp / 16; ++ks) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc::fence_after_sync();
+      const uint32_t o = (uint32_t)ks * 256u;  // 16 bf16 = 32 bytes = two core columns
+      // accumulator 0: v0 w0; accumulator 1 (columns np..): the five smaller products
+      tc::mma_bf16(tz.tmem, tc::kmajor_desc(tc::smem_u32(A[0]) + o, kb), tc::kmajor_desc(tc::smem_u32(Bp[0]) + o, kb),
+                   idesc, 0u);
+      const int pi[5] = {1, 0, 2, 1, 0}, pj[5] = {1, 2, 0, 0, 1};
+      for (int t = 0; t < 5; ++t)
+        tc::mma_bf16(tz.tmem + (uint32_t)np, tc::kmajor_desc(tc::smem_u32(A[pi[t]]) + o, kb),
+                     tc::kmajor_desc(tc::smem_u32(Bp[pj[t]]) + o, kb), idesc, t ? 1u : 0u);
+      tc::commit(tz.mbar);
+    }
+    const bool ok = __syncthreads_and(tc::mbar_wait(tz.mbar, tz.phase, 1LL << 22));
+    tz.phase ^= 1u;
+    if (!ok) return false;
+    tc::fence_after_sync();
+    // this K step's partial panel, added in FP64: warp w reads lanes
+    // 32 (w % 4) .. + 31 (rows m); the warps past the first four take the
+    // other 16-column blocks
+    if (w < 4 * ngrp) {
+      for (int cb = 16 * (w >> 2); cb < np; cb += 16 * ngrp) {
+        float v0[16], v1[16];
+        const uint32_t ta = tz.tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)cb;
+        tc::tmem_ld16(ta, v0);
+        tc::tmem_ld16(ta + (uint32_t)np, v1);
+        if (m < M) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int n = cb + i;
+            if (n < 2 * N1) {
+              const bool imag = n >= N1;
+              const int nn = imag ? n - N1 : n;
+              const int mu = nn / s1, ap = nn - mu * s1;
+              const size_t idx = (size_t)(ap * rA1 + bp) * p + (c * 2 + mu);
+              double* t = reinterpret_cast<double*>(Zg + idx) + (imag ? 1 : 0);
+              const double part = (double)v0[i] + (double)v1[i];
+              *t = ks ? *t + part : part;
+            }
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  // where the FP64 loop leaves the panel
+  for (int idx = threadIdx.x; idx < q * p; idx += blockDim.x) {
+    if (sm_panel)
+      sm_panel[idx] = cconj(Zg[idx]);
+    else if (conj_out)
+      Zg[idx] = cconj(Zg[idx]);
+  }
+  __syncthreads();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
 // K4: zip-up MPO x TT contraction (Stoudenmire & White 2010), left to right.
 // ---------------------------------------------------------------------------
 // Carry C (r' x s r) from the previous site is stored as CH = C^H. At site s:
@@ -798,7 +963,8 @@ __global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count,
 // vectors V of Z are the left singular vectors of T: V becomes the output core
 // B_s[c][mu][c''] and Z V = T^H V the next carry CH. Singular values below
 // ztol * ||T|| are dropped; the final rounding sweep sets the ranks.
-__global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, int* counter, const int* n_arr, const double* tol_arr,
+template <bool TC>
+__device__ __forceinline__ void zipup_body(const int* list, int count, int* counter, const int* n_arr, const double* tol_arr,
                         const int* maxrank_arr, const cd* A,
                         const long long* a_off, const int* a_ranks_all,
                         const cd* Wmpo, const long long* w_off,
@@ -814,7 +980,9 @@ __global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, in
   // the instances that need it to the full-size launch (defer).
   // qmax1: most panel columns a launch with defer set keeps (<= LA_MAXQ);
   // wlim: most panel elements factored directly in shared memory (<= the
-  // carve's W); both are the carve's own limits unless a test narrows them
+  // carve's W); both are the carve's own limits unless a test narrows them.
+  // TC: the MPO contraction of each site on the tensor cores (zip_panel_tc)
+  // wherever one tile holds it, in FP64 on the CUDA cores elsewhere.
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, LA_MAXP, hb, vcap);
   const int wcap = (LA_MAXP + hb) * LA_MAXP;
@@ -825,6 +993,24 @@ __global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, in
   __shared__ double zcn[LA_MAXQ];
   const int count_ = dcount ? *dcount : count;
   double fl = 0.0;
+  double tc_sites = 0.0;  // sites whose MPO contraction ran on the tensor cores
+  ZipTc tz;
+  __shared__ uint64_t tc_mbar;
+  __shared__ uint32_t tc_slot;
+  bool tc_fail = false;
+  if constexpr (TC) {
+    if (threadIdx.x == 0) {
+      tc::mbar_init(&tc_mbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&tc_slot, 128);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    tz.tmem = tc_slot;
+    tz.mbar = &tc_mbar;
+    tz.phase = 0u;
+  }
   WORK_LOOP_BEGIN(list, count_, counter)
     const int n = n_arr[inst];
     const double ztol = tol_arr[inst] / sqrt((double)max(n - 1, 1));
@@ -903,7 +1089,20 @@ __global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, in
       // global scratch instead (same steps, L2-resident)
       const bool gdirect = !direct && !has_v && q <= LA_MAXQ;
       cd* Tp = direct ? sm.W : Z;
-      for (int idx = threadIdx.x; idx < q * p; idx += blockDim.x) {
+      bool on_tc = false;
+      if constexpr (TC) {
+        const int need = zip_tc_bytes(rc * rA1, 2 * s0, 2 * s1);
+        if (!tc_fail && need > 0 && need <= (int)(sizeof(cd) * wcap)) {
+          on_tc = true;
+          tc_sites += 1.0;
+          if (!zip_panel_tc(Dt, Ws, rc, s0, s1, rA1, reinterpret_cast<unsigned char*>(sm.W), tz, Z,
+                            direct ? sm.W : nullptr, q, p, gdirect)) {
+            tc_fail = true;
+            st = SFFT_ETIMEOUT_DEV;
+          }
+        }
+      }
+      for (int idx = threadIdx.x; idx < (on_tc ? 0 : q * p); idx += blockDim.x) {
         const int row = idx / p, col = idx - row * p;
         const int ap = row / rA1, bp = row - ap * rA1;
         const int c = col >> 1, mu = col & 1;
@@ -995,8 +1194,35 @@ __global__ void __launch_bounds__(256, 3) k_zipup(const int* list, int count, in
     if (threadIdx.x == 0) status[inst] = max(status[inst], st);
     __syncthreads();
   WORK_LOOP_END
-  if (acc && threadIdx.x == 0) atomicAdd(acc + PH_ZIPUP, fl);
+  if (acc && threadIdx.x == 0) {
+    atomicAdd(acc + PH_ZIPUP, fl);
+    if (tc_sites > 0.0) atomicAdd(acc + SFFT_NPHASE_DEV + PH_ZIPUP, tc_sites);
+  }
+  if constexpr (TC) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+      tc::fence_after_sync();
+      tc::tmem_free(tz.tmem, 128);
+    }
+  }
 }
+
+#define ZIPUP_PARAMS                                                                                  \
+  const int *list, int count, int *counter, const int *n_arr, const double *tol_arr,                 \
+      const int *maxrank_arr, const cd *A, const long long *a_off, const int *a_ranks_all,           \
+      const cd *Wmpo, const long long *w_off, const int *w_ranks_all, cd *B, const long long *b_off, \
+      int *b_ranks_all, int core_stride_a, int core_stride_w, int core_stride_b, cd *scratch,        \
+      long long scratch_stride, int *status, int hb, double *acc, int vcap, int *defer,              \
+      const int *dcount, int qmax1, int wlim
+#define ZIPUP_ARGS                                                                                  \
+  list, count, counter, n_arr, tol_arr, maxrank_arr, A, a_off, a_ranks_all, Wmpo, w_off, w_ranks_all, \
+      B, b_off, b_ranks_all, core_stride_a, core_stride_w, core_stride_b, scratch, scratch_stride,    \
+      status, hb, acc, vcap, defer, dcount, qmax1, wlim
+
+__global__ void __launch_bounds__(256, 3) k_zipup(ZIPUP_PARAMS) { zipup_body<false>(ZIPUP_ARGS); }
+__global__ void __launch_bounds__(256, 3) k_zipup_tc(ZIPUP_PARAMS) { zipup_body<true>(ZIPUP_ARGS); }
+
 
 // ---------------------------------------------------------------------------
 // K6: readout in bit-reversed site order (Sec. 3.3, Eq. discretization_dft)

@@ -28,6 +28,7 @@ PHASE_NAMES = ["probe", "build", "zipup", "round", "readout", "mpo", "dense_samp
 PHASE_KERNELS = ["k_support_probe+k_build_lists", "k_integrand_ttsvd", "k_zipup", "k_tt_round", "k_readout",
                  "k_mpo_interp+k_tt_round", "k_dense_sample", "k_fft_pass", "k_dense_gather",
                  "k_integrand_cross+k_tt_round"]
+PRECISION_FP64, PRECISION_MIXED = 0, 1
 MAX_RANK = 32
 MAX_STRIKES = 65536
 DENSE_MAX_N = 32
@@ -75,6 +76,7 @@ EXPORTS = {
     "sfft_destroy": (c_int32, [c_void_p]),
     "sfft_set_stream": (c_int32, [c_void_p, c_void_p]),
     "sfft_tier2_counts": (c_int32, [c_void_p, ctypes.POINTER(c_int32)]),
+    "sfft_set_precision": (c_int32, [c_void_p, c_int32]),
     "sfft_strike_window": (c_int32, [ctypes.POINTER(SfftProblem), c_double, c_double, c_int32,
                                      ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
                                      ctypes.POINTER(c_int32)]),
@@ -341,6 +343,11 @@ class Pricer:
 
     def last_error(self) -> str:
         return self.lib.sfft_last_error(self.h).decode()
+
+    def set_precision(self, mixed: bool):
+        """FP64 everywhere (False, the default) or the MPO contraction in
+        complex FP32 on the tensor cores (True); see sfft_set_precision."""
+        self._check(self.lib.sfft_set_precision(self.h, PRECISION_MIXED if mixed else PRECISION_FP64))
 
     def tier2_counts(self):
         """Instances the last pricing call's first-tier launches handed to their
