@@ -690,8 +690,12 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   // mixed precision: tier 1 runs each site's MPO contraction on the tensor
   // cores; tier 2 (rare, the full carve) stays FP64
   const bool mixed = ctx->precision == SFFT_PRECISION_MIXED;
-  const void* zip1 = mixed ? (const void*)k_zipup_tc : (const void*)k_zipup;
-  const int zg1 = std::min(cnt, ctx->num_sms * blocks_per_sm(zip1, zs1.bytes));
+  // The occupancy calculator reports one CTA per SM for any kernel that
+  // allocates tensor memory; the hardware co-schedules as many as their
+  // allocations fit (128 of the SM's 512 columns each here), so the tensor-
+  // core zip-up takes the FP64 kernel's occupancy, capped at four per SM.
+  const int zbps = blocks_per_sm((const void*)k_zipup, zs1.bytes);
+  const int zg1 = std::min(cnt, ctx->num_sms * (mixed ? std::min(zbps, 4) : zbps));
   const int zg2 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, zs.bytes));
   if ((s = ensure(ctx, "zip_scratch", sizeof(cd) * (size_t)SFFT_ZIP_SCRATCH * std::max(zg1, zg2), &p)))
     return s;

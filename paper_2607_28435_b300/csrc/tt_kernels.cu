@@ -851,11 +851,13 @@ __device__ bool zip_panel_tc(const cd* Dt, const cd* Ws, int rc, int s0, int s1,
   const int kb = 2 * kp;  // bytes of an operand row
   unsigned char* A[3] = {opnd, opnd + 128 * kb, opnd + 2 * 128 * kb};
   unsigned char* Bp[3] = {opnd + 3 * 128 * kb, opnd + 3 * 128 * kb + np * kb, opnd + 3 * 128 * kb + 2 * np * kb};
-  // A' rows m = (c, b'), columns (re | im) of (a, lam)
-  for (int e = threadIdx.x; e < 128 * kp; e += blockDim.x) {
+  // A' rows m = (c, b'), columns (re | im) of (a, lam). Rows from M on feed
+  // only output rows that are never read, so they are not staged (whatever
+  // they hold); the K padding of the staged rows is zero.
+  for (int e = threadIdx.x; e < M * kp; e += blockDim.x) {
     const int m = e / kp, k = e - m * kp;
     double v = 0.0;
-    if (m < M && k < 2 * K) {
+    if (k < 2 * K) {
       const int c = m / rA1, bp = m - c * rA1;
       const int kk = k < K ? k : k - K;
       const int a = kk >> 1, lam = kk & 1;
@@ -868,11 +870,13 @@ __device__ bool zip_panel_tc(const cd* Dt, const cd* Ws, int rc, int s0, int s1,
 #pragma unroll
     for (int i = 0; i < 3; ++i) *reinterpret_cast<uint16_t*>(A[i] + off) = b[i];
   }
-  // B' rows n = (mu, a') for the real part, N1 + n for the imaginary part
-  for (int e = threadIdx.x; e < np * kp; e += blockDim.x) {
+  // B' rows n = (mu, a') for the real part, N1 + n for the imaginary part;
+  // the padding rows from 2 N1 on feed only columns that are never read, and
+  // the K padding is zero on both operands
+  for (int e = threadIdx.x; e < 2 * N1 * kp; e += blockDim.x) {
     const int n = e / kp, k = e - n * kp;
     double v = 0.0;
-    if (n < 2 * N1 && k < 2 * K) {
+    if (k < 2 * K) {
       const bool imag_row = n >= N1;
       const int nn = imag_row ? n - N1 : n;
       const int mu = nn / s1, ap = nn - mu * s1;
