@@ -416,7 +416,29 @@ def main(argv=None):
     ap.add_argument("--cells", type=int, nargs=2, default=(6, 12), help="(T, k) cells of the trust table")
     ap.add_argument("--queries", type=int, default=1 << 20)
     ap.add_argument("--out", default=None, help="also write the JSON record to this file")
+    ap.add_argument("--forward-only", type=int, default=0, metavar="PASSES",
+                    help="no training: time PASSES forward passes of --queries rows through a randomly "
+                         "initialised network of the surrogate's shape and print one JSON line")
     args = ap.parse_args(argv)
+    if args.forward_only:
+        mlp = MLP(seed=1)
+        B = args.queries
+        x = torch.rand(B, mlp.widths[0], device=mlp.dev) * 2 - 1
+        mlp.forward(x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.forward_only):
+            mlp.forward(x)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.forward_only
+        w = mlp.widths
+        flops = 2.0 * B * sum(w[i] * w[i + 1] for i in range(len(w) - 1))
+        print(json.dumps({"queries": B, "passes": args.forward_only, "ms": ms, "tflops": flops / ms / 1e9,
+                          "tensor_cores": mlp.tensor_cores,
+                          "timeouts": int(mlp.lib.sfft_mlp_tc_timeouts())}), flush=True)
+        return
     pricer = sfft.Pricer(0)
     try:
         sur, st = train_surrogate(pricer, n_train_inst=args.instances, epochs=args.epochs,
