@@ -153,6 +153,50 @@ sfft_status sfft_set_stream(sfft_ctx *ctx, void *cuda_stream);
 #define SFFT_PRECISION_MIXED 1
 sfft_status sfft_set_precision(sfft_ctx *ctx, int32_t precision);
 
+/* ---- tuning of the first-tier launches ----
+ * The first tier of the two-tier kernels runs several CTAs per SM on a small
+ * shared-memory carve; how small pays depends on the batch. A tuning is the
+ * carve of three of them: the TT-SVD builder's panel width (build_p <= 32
+ * columns), the output rounding's rank (round_r <= 24) and the zip-up's CTAs
+ * per SM (zip_ctas, 0 = as many as fit). The defaults are 32, 24 and 0.
+ * sfft_autotune times the batch under the defaults and, by coordinate
+ * descent, under zip_ctas 2, build_p 24 and 16, round_r 20 and 16 (each
+ * configuration the best of `reps` calls, CUDA events on the context's
+ * stream, the outputs written like sfft_price_batch), and caches the fastest
+ * under the batch's signature; later pricing calls of this context (and
+ * graphs created from it) with the same signature use it. The signature is
+ * the device (compute capability, SM count) and the batch's size and its
+ * distribution over grid exponents, models, tolerance decade and grid rule,
+ * each count quantised to its binary order of magnitude (sfft_tune_key gives
+ * the batch part). The cache is exported as text lines "<signature> build_p
+ * round_r zip_ctas" and imported back, so that a given cache fixes the choice
+ * without re-timing. Under the SFFT_TIER1 test hook tuning is refused
+ * (SFFT_EINVAL) and the hook's limits apply. */
+typedef struct {
+  int32_t build_p;  /* TT-SVD builder, first tier: panel columns (2..32) */
+  int32_t round_r;  /* output rounding, first tier: rank (1..24) */
+  int32_t zip_ctas; /* zip-up, first tier: CTAs per SM (0 = as many as fit) */
+} sfft_tune;
+sfft_status sfft_autotune(sfft_ctx *ctx, const sfft_problem *probs, int32_t count, const int64_t *l_begin,
+                          const int64_t *stride, const int32_t *q, double *prices, double *log_strikes,
+                          int32_t reps, sfft_tune *chosen, double *ms_chosen, double *ms_default);
+/* The configuration a batch would use on this context; *found (may be NULL)
+ * says whether it came from the cache (else the defaults). Host only. */
+sfft_status sfft_tune_lookup(sfft_ctx *ctx, const sfft_problem *probs, int32_t count, sfft_tune *cfg,
+                             int32_t *found);
+/* The configurations the last sfft_autotune timed, in order, with their
+ * times (ms, best of its reps): cfgs and ms hold cap entries, *n receives
+ * how many there were. */
+sfft_status sfft_tune_trials(const sfft_ctx *ctx, sfft_tune *cfgs, double *ms, int32_t cap, int32_t *n);
+/* The batch part of the signature as text (host only, no context). */
+sfft_status sfft_tune_key(const sfft_problem *probs, int32_t count, char *buf, int32_t cap);
+/* The cache as text into buf (capacity cap, NUL-terminated); *len receives
+ * the length (buf may be NULL to ask for it). */
+sfft_status sfft_tune_export(const sfft_ctx *ctx, char *buf, int64_t cap, int64_t *len);
+/* Adds the lines of `text` to the cache (SFFT_EINVAL on a malformed line,
+ * nothing added then). */
+sfft_status sfft_tune_import(sfft_ctx *ctx, const char *text);
+
 /* Hand-off counts of the last sfft_price_batch call on this context (host
  * array of 4): how many instances the first-tier launches of the TT-SVD
  * builder, the cross builder, the zip-up and the output rounding passed on to

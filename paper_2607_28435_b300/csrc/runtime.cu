@@ -91,7 +91,16 @@ struct sfft_ctx {
     int cross_r = 16;    // cross builder: rank
     int zip_q = LA_MAXQ; // zip-up: panel columns (s' r')
     int zip_w = 1 << 30; // zip-up: panel elements factored in shared memory
+    int zip_ctas = 0;    // zip-up: CTAs per SM (0: as many as fit)
   } t1;
+  bool t1_hooked = false;  // SFFT_TIER1 set: its limits win over any tuning
+  // tuned first-tier configurations by batch signature (sfft_autotune), the
+  // one in force for the current call, and a forced one while tuning
+  std::map<std::string, Tier1> tune;
+  Tier1 cur;
+  bool forcing = false;
+  Tier1 force;
+  std::vector<std::pair<Tier1, double>> trials;  // the last tuning's configurations and times
   // arithmetic of the zip-up's MPO contraction (SFFT_PRECISION_*)
   int precision = SFFT_PRECISION_FP64;
   // fault-injection test hooks (SFFT_FAULT), all on the host side
@@ -582,8 +591,8 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   CK(cudaMemsetAsync(defer_cross, 0, sizeof(int), ctx->stream));
   // TT-SVD builder: tier 1 panels up to kSmallP columns in 128-thread CTAs,
   // several per SM; tier 2 the full carve for the instances tier 1 handed on
-  const size_t bsmem1 = la::ts_svd_smem_bytes(kSmallP, kSmallP) + 256;
-  const int build_p1 = std::min(ctx->t1.build_p, kSmallP);
+  const int build_p1 = std::min(ctx->cur.build_p, kSmallP);
+  const size_t bsmem1 = la::ts_svd_smem_bytes(build_p1, build_p1) + 256;
   const int bgrid1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, bsmem1,
                                                                 kThreadsSmall));
   const int bgrid2 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_integrand_ttsvd, smem));
@@ -618,7 +627,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     PhaseScope ps(ctx, PH_CROSS);
     k_integrand_cross<<<xgrid1, kThreadsSmall, xsmem1, ctx->stream>>>(
         b.P, cross_dev, cnt, ctr + 1, cross_scratch, 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2, b.a_ranks,
-        b.status, xhb, acc_ptr(ctx), kCrossSweeps, xp, std::min(ctx->t1.cross_r, kCrossSmallR), defer_cross,
+        b.status, xhb, acc_ptr(ctx), kCrossSweeps, xp, std::min(ctx->cur.cross_r, kCrossSmallR), defer_cross,
         list_counts + 1);
   }
   {
@@ -642,7 +651,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     PhaseScope ps(ctx, PH_BUILD);
     k_integrand_ttsvd<<<bgrid1, kThreadsSmall, bsmem1, ctx->stream>>>(
         b.P, m_dev, svd_dev, cnt, ctr + 0, build_scratch, sstride, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
-        b.a_ranks, b.status, kSmallP, acc_ptr(ctx), build_p1, defer_build, list_counts);
+        b.a_ranks, b.status, build_p1, acc_ptr(ctx), build_p1, defer_build, list_counts);
   }
   {
     PhaseScope ps(ctx, PH_BUILD);
@@ -694,8 +703,10 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   // allocates tensor memory; the hardware co-schedules as many as their
   // allocations fit (128 of the SM's 512 columns each here), so the tensor-
   // core zip-up takes the FP64 kernel's occupancy, capped at four per SM.
-  const int zbps = blocks_per_sm((const void*)k_zipup, zs1.bytes);
-  const int zg1 = std::min(cnt, ctx->num_sms * (mixed ? std::min(zbps, 4) : zbps));
+  int zbps = blocks_per_sm((const void*)k_zipup, zs1.bytes);
+  if (mixed) zbps = std::min(zbps, 4);
+  if (ctx->cur.zip_ctas > 0) zbps = std::min(zbps, ctx->cur.zip_ctas);
+  const int zg1 = std::min(cnt, ctx->num_sms * zbps);
   const int zg2 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_zipup, zs.bytes));
   if ((s = ensure(ctx, "zip_scratch", sizeof(cd) * (size_t)SFFT_ZIP_SCRATCH * std::max(zg1, zg2), &p)))
     return s;
@@ -705,8 +716,8 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
         all_dev, cnt, ctr + 3, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
         reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
         SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
-        SFFT_ZIP_SCRATCH, b.status, zs1.hb, acc_ptr(ctx), zs1.vcap, defer_zip, nullptr, ctx->t1.zip_q,
-        ctx->t1.zip_w);
+        SFFT_ZIP_SCRATCH, b.status, zs1.hb, acc_ptr(ctx), zs1.vcap, defer_zip, nullptr, ctx->cur.zip_q,
+        ctx->cur.zip_w);
   }
   CK(cudaGetLastError());
   {
@@ -715,11 +726,11 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
         defer_zip + 1, 0, ctr + 9, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
         reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
         SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
-        SFFT_ZIP_SCRATCH, b.status, zs.hb, acc_ptr(ctx), zs.vcap, nullptr, defer_zip, LA_MAXQ, ctx->t1.zip_w);
+        SFFT_ZIP_SCRATCH, b.status, zs.hb, acc_ptr(ctx), zs.vcap, nullptr, defer_zip, LA_MAXQ, ctx->cur.zip_w);
   }
   CK(cudaGetLastError());
   // tier 1: ranks up to kSmallRoundR in 128-thread CTAs; tier 2: the rest
-  const RoundSmem rs1 = round_smem(2, false, std::min(ctx->t1.round_r, kSmallRoundR));
+  const RoundSmem rs1 = round_smem(2, false, std::min(ctx->cur.round_r, kSmallRoundR));
   const RoundSmem rs2 = round_smem(2, false);
   ctx->defer_heads[3] = defer_round;
   const int grid1 = std::min(cnt, ctx->num_sms * blocks_per_sm((const void*)k_tt_round, rs1.bytes, kThreadsSmall));
@@ -833,6 +844,58 @@ sfft_status finish_status(sfft_ctx* ctx, int count, const std::vector<int>& vali
   return first;
 }
 
+// Signature of a batch for the tuning cache: its size and the distribution of
+// what sets the kernels' work (grid exponents, models, tolerance, grid rule),
+// each count quantised to its binary order of magnitude, so that batches
+// drawn from the same workload share a signature. Host-side only.
+std::string batch_signature(const sfft_problem* probs, int count) {
+  int nb[6] = {0, 0, 0, 0, 0, 0}, mb[4] = {0, 0, 0, 0}, quads = 0;
+  std::vector<double> tols;
+  for (int i = 0; i < count; ++i) {
+    const int n = probs[i].n;
+    const int b = n <= 15 ? 0 : n <= 20 ? 1 : n <= 25 ? 2 : n <= 30 ? 3 : n <= 35 ? 4 : 5;
+    nb[b]++;
+    if (probs[i].model >= 0 && probs[i].model < 4) mb[probs[i].model]++;
+    quads |= 1 << (probs[i].quad & 1);
+    tols.push_back(probs[i].tol);
+  }
+  auto lg = [](int c) { int k = 0; while ((1 << k) <= c) ++k; return k; };  // 0 for 0, else floor(log2 c) + 1
+  double tol_med = 1e-12;
+  if (!tols.empty()) {
+    std::nth_element(tols.begin(), tols.begin() + tols.size() / 2, tols.end());
+    tol_med = tols[tols.size() / 2];
+  }
+  char buf[160];
+  snprintf(buf, sizeof buf, "count=%d;n=%d,%d,%d,%d,%d,%d;model=%d,%d,%d,%d;tol=%d;quad=%d", lg(count), lg(nb[0]),
+           lg(nb[1]), lg(nb[2]), lg(nb[3]), lg(nb[4]), lg(nb[5]), lg(mb[0]), lg(mb[1]), lg(mb[2]), lg(mb[3]),
+           (int)lround(log10(tol_med > 0 ? tol_med : 1e-12)), quads);
+  return buf;
+}
+
+std::string device_signature(const sfft_ctx* ctx) {
+  cudaDeviceProp prop;
+  char buf[96];
+  if (cudaGetDeviceProperties(&prop, ctx->device) == cudaSuccess)
+    snprintf(buf, sizeof buf, "sm%d%d x%d", prop.major, prop.minor, prop.multiProcessorCount);
+  else
+    snprintf(buf, sizeof buf, "sm? x%d", ctx->num_sms);
+  return buf;
+}
+
+// The first-tier configuration of a call: the test hook's limits when set,
+// else the forced one (while tuning), else the tuned one for the batch's
+// signature, else the defaults.
+void choose_tier1(sfft_ctx* ctx, const sfft_problem* probs, int count) {
+  if (ctx->t1_hooked) {
+    ctx->cur = ctx->t1;
+  } else if (ctx->forcing) {
+    ctx->cur = ctx->force;
+  } else {
+    auto it = ctx->tune.find(device_signature(ctx) + "|" + batch_signature(probs, count));
+    ctx->cur = (it != ctx->tune.end()) ? it->second : sfft_ctx::Tier1();
+  }
+}
+
 // Test hooks, read from the environment when a context is created. They only
 // narrow limits or fail host calls; nothing faults or stalls the device.
 //   SFFT_TIER1="build=8,round=6,cross=4,zipq=40,zipw=900"  tier-1 limits of the
@@ -846,6 +909,7 @@ sfft_status finish_status(sfft_ctx* ctx, int count, const std::vector<int>& vali
 // Several SFFT_FAULT items are separated by ';'.
 void read_test_hooks(sfft_ctx* ctx) {
   if (const char* t = getenv("SFFT_TIER1")) {
+    ctx->t1_hooked = true;
     std::string str(t);
     size_t pos = 0;
     while (pos < str.size()) {
@@ -975,6 +1039,160 @@ sfft_status sfft_set_stream(sfft_ctx* ctx, void* stream) {
   return SFFT_OK;
 }
 
+struct GraphCapture;
+static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_t count,
+                                const int64_t* l_begin, const int64_t* stride, const int32_t* q,
+                                double* prices, double* log_strikes, int32_t* inst_status,
+                                sfft_info* info, int mode, GraphCapture* gc = nullptr);
+
+
+sfft_status sfft_tune_key(const sfft_problem* probs, int32_t count, char* buf, int32_t cap) {
+  if (!probs || count < 1 || !buf || cap < 1) return SFFT_EINVAL;
+  const std::string k = batch_signature(probs, count);
+  if ((int)k.size() + 1 > cap) return SFFT_EINVAL;
+  memcpy(buf, k.c_str(), k.size() + 1);
+  return SFFT_OK;
+}
+
+static void to_tune(const sfft_ctx::Tier1& t, sfft_tune* out) {
+  out->build_p = t.build_p;
+  out->round_r = t.round_r;
+  out->zip_ctas = t.zip_ctas;
+}
+
+sfft_status sfft_tune_lookup(sfft_ctx* ctx, const sfft_problem* probs, int32_t count, sfft_tune* cfg,
+                             int32_t* found) {
+  if (!ctx || !probs || count < 1 || !cfg) return SFFT_EINVAL;
+  auto it = ctx->tune.find(device_signature(ctx) + "|" + batch_signature(probs, count));
+  if (found) *found = it != ctx->tune.end();
+  to_tune(it != ctx->tune.end() ? it->second : sfft_ctx::Tier1(), cfg);
+  return SFFT_OK;
+}
+
+sfft_status sfft_tune_trials(const sfft_ctx* ctx, sfft_tune* cfgs, double* ms, int32_t cap, int32_t* n) {
+  if (!ctx || cap < 0 || (cap > 0 && (!cfgs || !ms))) return SFFT_EINVAL;
+  const int m = std::min<int>(cap, (int)ctx->trials.size());
+  for (int i = 0; i < m; ++i) {
+    to_tune(ctx->trials[i].first, cfgs + i);
+    ms[i] = ctx->trials[i].second;
+  }
+  if (n) *n = (int32_t)ctx->trials.size();
+  return SFFT_OK;
+}
+
+sfft_status sfft_tune_export(const sfft_ctx* ctx, char* buf, int64_t cap, int64_t* len) {
+  if (!ctx) return SFFT_EINVAL;
+  std::string out;
+  for (const auto& kv : ctx->tune) {
+    char line[64];
+    snprintf(line, sizeof line, " %d %d %d\n", kv.second.build_p, kv.second.round_r, kv.second.zip_ctas);
+    out += kv.first + line;
+  }
+  if (len) *len = (int64_t)out.size();
+  if (!buf) return SFFT_OK;
+  if ((int64_t)out.size() + 1 > cap) return SFFT_EINVAL;
+  memcpy(buf, out.c_str(), out.size() + 1);
+  return SFFT_OK;
+}
+
+sfft_status sfft_tune_import(sfft_ctx* ctx, const char* text) {
+  if (!ctx || !text) return SFFT_EINVAL;
+  const std::string all(text);
+  size_t pos = 0;
+  std::map<std::string, sfft_ctx::Tier1> add;
+  while (pos < all.size()) {
+    size_t end = all.find('\n', pos);
+    if (end == std::string::npos) end = all.size();
+    const std::string line = all.substr(pos, end - pos);
+    pos = end + 1;
+    if (line.empty()) continue;
+    // "<device>|<batch> build_p round_r zip_ctas": the key holds spaces, the
+    // three numbers are the last three fields
+    size_t c3 = line.rfind(' ');
+    size_t c2 = c3 == std::string::npos ? c3 : line.rfind(' ', c3 - 1);
+    size_t c1 = c2 == std::string::npos ? c2 : line.rfind(' ', c2 - 1);
+    if (c1 == std::string::npos || c1 == 0) return set_err(ctx, SFFT_EINVAL, "tune line: %s", line.c_str());
+    sfft_ctx::Tier1 t;
+    t.build_p = atoi(line.c_str() + c1 + 1);
+    t.round_r = atoi(line.c_str() + c2 + 1);
+    t.zip_ctas = atoi(line.c_str() + c3 + 1);
+    if (t.build_p < 2 || t.build_p > 32 || t.round_r < 1 || t.round_r > 32 || t.zip_ctas < 0 || t.zip_ctas > 8)
+      return set_err(ctx, SFFT_EINVAL, "tune values out of range: %s", line.c_str());
+    add[line.substr(0, c1)] = t;
+  }
+  for (auto& kv : add) ctx->tune[kv.first] = kv.second;
+  return SFFT_OK;
+}
+
+sfft_status sfft_autotune(sfft_ctx* ctx, const sfft_problem* probs, int32_t count, const int64_t* l_begin,
+                          const int64_t* stride, const int32_t* q, double* prices, double* log_strikes,
+                          int32_t reps, sfft_tune* chosen, double* ms_chosen, double* ms_default) {
+  if (!ctx || !probs || count < 1 || reps < 1) return set_err(ctx, SFFT_EINVAL, "bad arguments");
+  if (ctx->t1_hooked) return set_err(ctx, SFFT_EINVAL, "first-tier limits are fixed by SFFT_TIER1");
+  if (ctx->prof) return set_err(ctx, SFFT_EINVAL, "turn profiling off before tuning");
+  CK(cudaSetDevice(ctx->device));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  std::vector<int32_t> st(count);
+  auto run = [&](const sfft_ctx::Tier1& t, double* ms) -> sfft_status {
+    ctx->forcing = true;
+    ctx->force = t;
+    double best = 1e300;
+    sfft_status r = SFFT_OK;
+    for (int k = 0; k < reps && r == SFFT_OK; ++k) {
+      cudaEventRecord(e0, ctx->stream);
+      r = price_common(ctx, probs, count, l_begin, stride, q, prices, log_strikes, st.data(), nullptr, 0);
+      cudaEventRecord(e1, ctx->stream);
+      cudaEventSynchronize(e1);
+      float f = 0.f;
+      cudaEventElapsedTime(&f, e0, e1);
+      best = std::min(best, (double)f);
+    }
+    ctx->forcing = false;
+    // a failing instance (EBOUNDS, EMOMENT, ...) does not stop the tuning
+    if (r != SFFT_OK && r != SFFT_ECUDA && r != SFFT_ENOMEM && r != SFFT_EINVAL) r = SFFT_OK;
+    *ms = best;
+    if (r == SFFT_OK) ctx->trials.push_back({t, best});
+    return r;
+  };
+  ctx->trials.clear();
+  sfft_ctx::Tier1 def, best = def;
+  double t_def = 0.0, t_best = 0.0, t = 0.0;
+  sfft_status s = run(def, &t_def);  // the first run also builds the batch's operators
+  ctx->trials.clear();
+  if (s == SFFT_OK) s = run(def, &t_def);
+  t_best = t_def;
+  // coordinate descent over the first-tier carves: zip-up CTAs per SM, the
+  // builder's panel width, the output rounding's rank
+  const int zips[] = {2};
+  const int builds[] = {24, 16};
+  const int rounds[] = {20, 16};
+  for (int z : zips) {
+    sfft_ctx::Tier1 c = best;
+    c.zip_ctas = z;
+    if (s == SFFT_OK && (s = run(c, &t)) == SFFT_OK && t < t_best) { best = c; t_best = t; }
+  }
+  for (int bp : builds) {
+    sfft_ctx::Tier1 c = best;
+    c.build_p = bp;
+    if (s == SFFT_OK && (s = run(c, &t)) == SFFT_OK && t < t_best) { best = c; t_best = t; }
+  }
+  for (int rr : rounds) {
+    sfft_ctx::Tier1 c = best;
+    c.round_r = rr;
+    if (s == SFFT_OK && (s = run(c, &t)) == SFFT_OK && t < t_best) { best = c; t_best = t; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != SFFT_OK) return s;
+  ctx->tune[device_signature(ctx) + "|" + batch_signature(probs, count)] = best;
+  if (chosen) to_tune(best, chosen);
+  if (ms_chosen) *ms_chosen = t_best;
+  if (ms_default) *ms_default = t_def;
+  return SFFT_OK;
+}
+
 sfft_status sfft_set_precision(sfft_ctx* ctx, int32_t precision) {
   if (!ctx || (precision != SFFT_PRECISION_FP64 && precision != SFFT_PRECISION_MIXED)) return SFFT_EINVAL;
   ctx->precision = precision;
@@ -1062,6 +1280,7 @@ sfft_status sfft_integrand_tt(sfft_ctx* ctx, const sfft_problem* prob, int32_t* 
   sfft_status s = plan(ctx, *prob, &prm[0]);
   if (s) return s;
   Batch b;
+  ctx->cur = ctx->t1_hooked ? ctx->t1 : sfft_ctx::Tier1();
   if ((s = run_tt_path(ctx, prm, b, nullptr, false))) return s;
   int st = 0;
   CK(cudaMemcpyAsync(&st, b.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1178,7 +1397,7 @@ struct GraphCapture {
 static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_t count,
                                 const int64_t* l_begin, const int64_t* stride, const int32_t* q,
                                 double* prices, double* log_strikes, int32_t* inst_status,
-                                sfft_info* info, int mode, GraphCapture* gc = nullptr) {
+                                sfft_info* info, int mode, GraphCapture* gc) {
   // mode 0: TT-SFFT; 1: dense-FFT baseline; 2: QFT route by statevector emulation
   const bool dense = mode != 0;
   if (!ctx || count < 0 || (count > 0 && (!probs || !l_begin || !stride || !q)))
@@ -1317,6 +1536,7 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
     if ((s = get_mpo(ctx, prm[k].n, prm[k].tol, &mp[k]))) return s;
   }
   Batch b;
+  choose_tier1(ctx, probs, count);
   if (ctx->fault_jacobi > 0) CK(sfft_set_jacobi_cap(ctx->fault_jacobi, ctx->stream));
   s = run_tt_path(ctx, prm, b, &mp, true);
   if (ctx->fault_jacobi > 0) CK(sfft_set_jacobi_cap(60, ctx->stream));
@@ -1479,6 +1699,8 @@ sfft_status sfft_graph_create(sfft_ctx* ctx, const sfft_problem* probs, int32_t 
   // the private context prices as the caller's does
   g->own->precision = ctx->precision;
   g->own->t1 = ctx->t1;
+  g->own->t1_hooked = ctx->t1_hooked;
+  g->own->tune = ctx->tune;
   // 1. a plain run sizes every workspace and builds the MPOs
   std::vector<int32_t> st(count);
   s = price_common(g->own, probs, count, l_begin, stride, q, prices, log_strikes, st.data(), nullptr, 0);

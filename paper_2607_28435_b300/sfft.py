@@ -48,6 +48,13 @@ class SfftInfo(ctypes.Structure):
 MLP_MAX_LAYERS = 8
 
 
+class SfftTune(ctypes.Structure):
+    _fields_ = [("build_p", c_int32), ("round_r", c_int32), ("zip_ctas", c_int32)]
+
+    def as_dict(self):
+        return dict(build_p=self.build_p, round_r=self.round_r, zip_ctas=self.zip_ctas)
+
+
 class SfftMlp(ctypes.Structure):
     """sfft_mlp of include/sfft_mlp.h: widths and device pointers per layer."""
     _fields_ = [("n_layers", c_int32), ("width", c_int32 * (MLP_MAX_LAYERS + 1)), ("mode", c_int32),
@@ -77,6 +84,16 @@ EXPORTS = {
     "sfft_set_stream": (c_int32, [c_void_p, c_void_p]),
     "sfft_tier2_counts": (c_int32, [c_void_p, ctypes.POINTER(c_int32)]),
     "sfft_set_precision": (c_int32, [c_void_p, c_int32]),
+    "sfft_autotune": (c_int32, [c_void_p, ctypes.POINTER(SfftProblem), c_int32, ctypes.POINTER(c_int64),
+                                ctypes.POINTER(c_int64), ctypes.POINTER(c_int32), c_void_p, c_void_p, c_int32,
+                                ctypes.POINTER(SfftTune), ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
+    "sfft_tune_lookup": (c_int32, [c_void_p, ctypes.POINTER(SfftProblem), c_int32, ctypes.POINTER(SfftTune),
+                                   ctypes.POINTER(c_int32)]),
+    "sfft_tune_key": (c_int32, [ctypes.POINTER(SfftProblem), c_int32, ctypes.c_char_p, c_int32]),
+    "sfft_tune_export": (c_int32, [c_void_p, ctypes.c_char_p, c_int64, ctypes.POINTER(c_int64)]),
+    "sfft_tune_import": (c_int32, [c_void_p, ctypes.c_char_p]),
+    "sfft_tune_trials": (c_int32, [c_void_p, ctypes.POINTER(SfftTune), ctypes.POINTER(c_double), c_int32,
+                                   ctypes.POINTER(c_int32)]),
     "sfft_strike_window": (c_int32, [ctypes.POINTER(SfftProblem), c_double, c_double, c_int32,
                                      ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
                                      ctypes.POINTER(c_int32)]),
@@ -282,6 +299,17 @@ def strike_window(prob, lo: float = -1.5, hi: float = 1.5, qmax: int = 4096) -> 
     return lb.value, st.value, q.value
 
 
+def tune_key(problems) -> str:
+    """The batch part of the tuning signature (host only)."""
+    lib = load_library()
+    arr = (SfftProblem * max(len(problems), 1))(*[to_c_problem(p) for p in problems])
+    buf = ctypes.create_string_buffer(256)
+    s = lib.sfft_tune_key(arr, len(problems), buf, 256)
+    if s != SFFT_OK:
+        raise SfftError(s, "sfft_tune_key")
+    return buf.value.decode()
+
+
 def _ptr(t) -> int:
     return t.data_ptr() if t is not None else 0
 
@@ -343,6 +371,45 @@ class Pricer:
 
     def last_error(self) -> str:
         return self.lib.sfft_last_error(self.h).decode()
+
+    def autotune(self, problems, strikes=None, reps: int = 2):
+        """Time the batch under the candidate first-tier carves (sfft_autotune);
+        returns (chosen configuration dict, ms chosen, ms default)."""
+        torch = self.torch
+        b = problems if isinstance(problems, Batch) else Batch(problems, strikes)
+        dev = torch.device("cuda", self.device)
+        pr = torch.empty(max(b.total, 1), dtype=torch.float64, device=dev)
+        lk = torch.empty_like(pr)
+        cfg, t1, t0 = SfftTune(), c_double(), c_double()
+        self._stream()
+        self._check(self.lib.sfft_autotune(self.h, b.problems, b.count, b.l_begin, b.stride, b.q,
+                                           c_void_p(_ptr(pr)), c_void_p(_ptr(lk)), reps, ctypes.byref(cfg),
+                                           ctypes.byref(t1), ctypes.byref(t0)))
+        return cfg.as_dict(), t1.value, t0.value
+
+    def tune_trials(self):
+        """[(configuration dict, ms)] of the last autotune, in the order timed."""
+        cfgs = (SfftTune * 16)()
+        ms = (c_double * 16)()
+        n = c_int32()
+        self._check(self.lib.sfft_tune_trials(self.h, cfgs, ms, 16, ctypes.byref(n)))
+        return [(cfgs[i].as_dict(), ms[i]) for i in range(min(n.value, 16))]
+
+    def tune_lookup(self, problems):
+        arr = (SfftProblem * max(len(problems), 1))(*[to_c_problem(p) for p in problems])
+        cfg, found = SfftTune(), c_int32()
+        self._check(self.lib.sfft_tune_lookup(self.h, arr, len(problems), ctypes.byref(cfg), ctypes.byref(found)))
+        return cfg.as_dict(), bool(found.value)
+
+    def tune_export(self) -> str:
+        n = c_int64()
+        self._check(self.lib.sfft_tune_export(self.h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value + 1)
+        self._check(self.lib.sfft_tune_export(self.h, buf, n.value + 1, ctypes.byref(n)))
+        return buf.value.decode()
+
+    def tune_import(self, text: str):
+        self._check(self.lib.sfft_tune_import(self.h, text.encode()))
 
     def set_precision(self, mixed: bool):
         """FP64 everywhere (False, the default) or the MPO contraction in

@@ -66,3 +66,18 @@ def test_trust_cells_cover_the_box():
     iT, ik = Surrogate.cells(raw, lo, hi, (6, 12))
     assert list(iT) == [0, 5, 3, 0, 0]
     assert list(ik) == [0, 11, 0, 11, 5]
+
+
+def test_tuning_signature_buckets_batches_of_one_workload():
+    # the tuning cache's batch signature (host only): the same workload drawn
+    # with another seed shares it; another grid exponent, tolerance or size
+    # does not
+    from paper_2607_28435_b300 import sfft
+    a = wl.config3_batch(4096)
+    b = wl.config3_batch(4096, seed=wl.CONFIG3_SEED + 1)
+    k = sfft.tune_key(a)
+    assert k == sfft.tune_key(a) == sfft.tune_key(b)
+    assert k != sfft.tune_key(wl.config3_batch(4096, n_lo=30, n_hi=30))
+    assert k != sfft.tune_key(wl.config3_batch(4096, tol=1e-7))
+    assert k != sfft.tune_key(a[:256])
+    assert "tol=-12" in k and "count=13" in k
