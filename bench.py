@@ -469,7 +469,7 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
     # the batch time assembled from the per-n times
     dense = None
     if not args.no_dense and rank == 0:
-        dense = dense_baseline(pricer, problems, strikes, torch, dev)
+        dense = dense_baseline(pricer, problems, strikes, torch, dev, fp64_peak)
 
     cpu = None
     if pool is not None and rank == 0 and not args.no_cpu:
@@ -587,13 +587,21 @@ def ctypes_sizeof_problem():
     return ctypes.sizeof(sfft.SfftProblem)
 
 
-def dense_baseline(pricer, problems, strikes, torch, dev):
+def dense_baseline(pricer, problems, strikes, torch, dev, fp64_peak):
+    """The dense-FFT Carr-Madan baseline on the same batch: one instance per
+    n <= 32 (SFFT_DENSE_MAX_N) timed with CUDA events, the batch time
+    assembled as sum_n count_n t_n (n = 33, 34 scaled from n = 32 as
+    M log M). At the largest n its phases are timed separately: the first
+    FFT pass with the sampling of the integrand fused in, the other FFT
+    passes, the gather."""
     by_n = {}
     for p, s in zip(problems, strikes):
         by_n.setdefault(p.n, []).append((p, s))
     t_n = {}
+    phases = {}
+    top_n = max(n for n in by_n if n <= 32)
     for n in sorted(by_n):
-        if n > 30:
+        if n > 32:
             continue
         p, s = by_n[n][0]
         pr = torch.empty(max(s[2], 1), dtype=torch.float64, device=dev)
@@ -606,12 +614,23 @@ def dense_baseline(pricer, problems, strikes, torch, dev):
         e1.record()
         torch.cuda.synchronize()
         t_n[n] = e0.elapsed_time(e1) / 1e3
+        if n in (30, top_n):
+            pricer.profile(True)
+            pricer.profile_read(reset=True)
+            pricer.dense_price_batch([p], [s], pr, lk)
+            torch.cuda.synchronize()
+            ph = pricer.profile_read(reset=True)
+            pricer.profile(False)
+            phases[n] = {k: ph[k]["ms"] for k in ("dense_sample", "dense_fft", "dense_gather")}
     if not t_n:
         return None
     # external reference point: cuFFT's complex-to-complex transform of the
-    # same length (torch.fft on the device), FFT only, beside our sample+FFT+gather
+    # same length (torch.fft on the device), FFT only, for n <= 30 (larger
+    # lengths need two 32-64 GiB arrays beside the baseline's own)
     cufft = {}
     for n in sorted(t_n):
+        if n > 30:
+            continue
         xr = torch.zeros(1 << n, dtype=torch.complex128, device=dev)
         torch.fft.fft(xr)
         torch.cuda.synchronize()
@@ -623,10 +642,6 @@ def dense_baseline(pricer, problems, strikes, torch, dev):
         cufft[str(n)] = e0.elapsed_time(e1) / 1e3
         del xr
     top = max(t_n)
-    # HBM traffic of our dense route at the largest measured n: the sample
-    # writes 16 M bytes, each of the ceil(n/8) passes reads and writes 16 M
-    m_top = 1 << top
-    hbm_bytes = 16.0 * m_top * (1 + 2 * ((top + 7) // 8))
     est = 0.0
     extrapolated = []
     for n, items in by_n.items():
@@ -636,14 +651,29 @@ def dense_baseline(pricer, problems, strikes, torch, dev):
             est += len(items) * t_n[top] * 2.0 ** (n - top) * n / top
             extrapolated.append(n)
     q = sum(s[2] for s in strikes)
-    return {"value": q / est, "unit": UNIT, "batch_seconds": est, "measured_n": sorted(t_n),
-            "seconds_per_n": {str(k): v for k, v in sorted(t_n.items())},
-            "extrapolated_n": sorted(extrapolated),
-            "hbm_gbs_at_top_n": hbm_bytes / t_n[top] / 1e9,
-            "cufft_z2z_seconds_per_n": cufft,
-            "how": "one instance per n timed (CUDA events); batch time = sum_n count_n t_n; "
-                   "n > 30 scaled as M log M from n = 30; cuFFT (torch.fft) of the same "
-                   "lengths as an external reference"}
+    out = {"value": q / est, "unit": UNIT, "batch_seconds": est, "measured_n": sorted(t_n),
+           "seconds_per_n": {str(k): v for k, v in sorted(t_n.items())},
+           "extrapolated_n": sorted(extrapolated),
+           "cufft_z2z_seconds_per_n": cufft,
+           "how": "one instance per n timed (CUDA events); batch time = sum_n count_n t_n; n > 32 scaled as "
+                  "M log M from n = 32; phases at n = 30 and the largest n from the profiler; cuFFT (torch.fft) of the "
+                  "same lengths up to n = 30 as an external reference"}
+    for n, ph in sorted(phases.items()):
+        m, npass = 1 << n, (n + 7) // 8
+        fft_ms = ph["dense_fft"]
+        rec = dict(ph)
+        if fft_ms:
+            # the passes after the first read and write 16 M bytes each and
+            # do their share of the radix-2 work 5 M log2 M
+            rec["fft_passes_hbm_gbs"] = 32.0 * m * (npass - 1) / (fft_ms * 1e-3) / 1e9
+            if fp64_peak:
+                rec["fft_passes_fp64_frac"] = 5.0 * m * n * (npass - 1) / npass / (fft_ms * 1e-3) / 1e9 / fp64_peak
+        if str(n) in cufft:
+            # all passes of our FFT (the first scaled from the others per pass) against cuFFT's Z2Z
+            rec["fft_all_passes_est_ms"] = fft_ms * npass / (npass - 1) if npass > 1 else None
+            rec["cufft_z2z_ms"] = cufft[str(n)] * 1e3
+        out.setdefault("phases_ms", {})[str(n)] = rec
+    return out
 
 
 # --------------------------------------------------------------------------- reference arm

@@ -373,8 +373,9 @@ sfft_status sfft_tt_round_noalloc(int32_t n, int32_t d, const int32_t *in_ranks,
 
 /* Phases timed by the profiler (index into the arrays of sfft_profile_read):
  * 0 support probe and work lists, 1 integrand TT build, 2 zip-up MPO x TT, 3 rounding,
- * 4 readout, 5 MPO build, 6 dense sampling, 7 dense FFT passes,
- * 8 dense gather, 9 integrand TT by cross interpolation (and its rounding);
+ * 4 readout, 5 MPO build, 6 dense sampling (the dense route samples inside
+ * its first FFT pass, so this phase is that pass), 7 the other dense FFT
+ * passes, 8 dense gather, 9 integrand TT by cross interpolation (and its rounding);
  * phase 1 then counts the TT-SVD builder alone. */
 #define SFFT_NPHASES 10
 

@@ -1,7 +1,8 @@
 // Dense-FFT Carr-Madan baseline (the FFT route of Sec. 4.1): every integrand
-// value x_j, j < M = 2^n, is sampled into device memory, an in-place M-point
-// FFT runs as a sequence of radix-2^R decimation-in-frequency passes, and the
-// requested strikes are gathered and priced (Eq. discretization_dft).
+// value x_j, j < M = 2^n, is evaluated inside the first pass of an in-place
+// M-point FFT that runs as a sequence of radix-2^R decimation-in-frequency
+// passes through shared memory, and the requested strikes are gathered and
+// priced (Eq. discretization_dft).
 //
 // Pass with sub-transform length L = 2^R * Lp: for every sub-transform b and
 // offset s < Lp the 2^R elements x[bL + s + r Lp] are transformed,
@@ -24,45 +25,86 @@ __device__ __forceinline__ cd unit_root(long long t, long long L) {
   return mkc(cs, -sn);
 }
 
-__global__ void k_fft_pass(cd* x, long long M, long long Lp, int R, int cols) {
+// With `sample` set (the first pass), the pass evaluates the integrand at its
+// indices instead of reading x: sampling is fused into the first pass, and
+// the array is written once, transformed. The twiddles exp(-2 pi i s k / L)
+// of a block come from two small tables per column, w^(16 kh) and w^kl with
+// k = 16 kh + kl and w = exp(-2 pi i s / L), each entry formed exactly from
+// its reduced integer argument, so a twiddle costs one complex product.
+__global__ void k_fft_pass(cd* x, long long M, long long Lp, int R, int cols, InstParams P, int sample) {
   extern __shared__ double4 smem_raw[];
   cd* sm = reinterpret_cast<cd*>(smem_raw);
   const int Rn = 1 << R;
   cd* tw = sm + (size_t)Rn * cols;
+  cd* t_lo = tw + Rn;            // [c][kl], 16 per column
+  cd* t_hi = t_lo + 16 * cols;   // [c][kh], 16 per column
   for (int i = threadIdx.x; i < Rn; i += blockDim.x) tw[i] = unit_root(i, Rn);
   const long long L = Lp * Rn;
   const long long per_sub = Lp / cols;
+  const int lc = __ffs(cols) - 1;  // cols is a power of two
   const long long nblk = (M / L) * per_sub;
   for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
     const long long b = blk / per_sub;
     const long long s0 = (blk - b * per_sub) * cols;
     const long long base = b * L + s0;
     __syncthreads();
+    for (int e = threadIdx.x; e < 32 * cols; e += blockDim.x) {
+      const int c = e >> 5, j = e & 15;
+      const long long s = s0 + c;
+      if ((e & 31) < 16)
+        t_lo[c * 16 + j] = unit_root((s * j) & (L - 1), L);
+      else
+        t_hi[c * 16 + j] = unit_root((s * 16 * j) & (L - 1), L);
+    }
     for (int e = threadIdx.x; e < Rn * cols; e += blockDim.x) {
-      const int r = e / cols, c = e - r * cols;
-      sm[e] = x[base + (long long)r * Lp + c];
+      const int r = e >> lc, c = e & (cols - 1);
+      const long long j = base + (long long)r * Lp + c;
+      sm[e] = sample ? integrand(P, j) : x[j];
     }
     __syncthreads();
-    for (int span = Rn; span >= 2; span >>= 1) {
-      const int half = span >> 1;
-      const int stride_tw = Rn / span;
+    // radix-2 stages; the last two have trivial twiddles (1, and -i)
+    for (int lh = R - 1; lh >= 2; --lh) {
+      const int half = 1 << lh;
+      const int stride_tw = Rn >> (lh + 1);
       for (int bf = threadIdx.x; bf < (Rn >> 1) * cols; bf += blockDim.x) {
-        const int c = bf % cols, j = bf / cols;
-        const int g = j / half, i = j - g * half;
-        const int r0 = g * span + i, r1 = r0 + half;
+        const int c = bf & (cols - 1), j = bf >> lc;
+        const int g = j >> lh, i = j & (half - 1);
+        const int r0 = (g << (lh + 1)) + i, r1 = r0 + half;
         const cd a = sm[r0 * cols + c], bb = sm[r1 * cols + c];
         sm[r0 * cols + c] = cadd(a, bb);
         sm[r1 * cols + c] = cmul(csub(a, bb), tw[i * stride_tw]);
       }
       __syncthreads();
     }
+    if (R >= 2) {
+      // span 4: twiddles 1 and exp(-i pi / 2) = -i
+      for (int bf = threadIdx.x; bf < (Rn >> 1) * cols; bf += blockDim.x) {
+        const int c = bf & (cols - 1), j = bf >> lc;
+        const int g = j >> 1, i = j & 1;
+        const int r0 = (g << 2) + i, r1 = r0 + 2;
+        const cd a = sm[r0 * cols + c], bb = sm[r1 * cols + c];
+        sm[r0 * cols + c] = cadd(a, bb);
+        const cd d = csub(a, bb);
+        sm[r1 * cols + c] = i ? mkc(d.y, -d.x) : d;
+      }
+      __syncthreads();
+    }
+    if (R >= 1) {
+      // span 2: twiddle 1
+      for (int bf = threadIdx.x; bf < (Rn >> 1) * cols; bf += blockDim.x) {
+        const int c = bf & (cols - 1), j = bf >> lc;
+        const int r0 = j << 1, r1 = r0 + 1;
+        const cd a = sm[r0 * cols + c], bb = sm[r1 * cols + c];
+        sm[r0 * cols + c] = cadd(a, bb);
+        sm[r1 * cols + c] = csub(a, bb);
+      }
+      __syncthreads();
+    }
     for (int e = threadIdx.x; e < Rn * cols; e += blockDim.x) {
-      const int k = e / cols, c = e - k * cols;
+      const int k = e >> lc, c = e & (cols - 1);
       const int kr = (int)(__brev((unsigned)k) >> (32 - R));
       const cd v = sm[kr * cols + c];
-      const long long s = s0 + c;
-      const long long t = (s * k) & (L - 1);
-      x[base + (long long)k * Lp + c] = (t == 0) ? v : cmul(v, unit_root(t, L));
+      x[base + (long long)k * Lp + c] = cmul(v, cmul(t_hi[c * 16 + (k >> 4)], t_lo[c * 16 + (k & 15)]));
     }
   }
 }

@@ -1475,7 +1475,9 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
       const InstParams& P = prm[k];
       const long long M = 1LL << P.n;
       cd* x = reinterpret_cast<cd*>(xb);
-      {
+      // the dense route samples inside its first FFT pass; the statevector
+      // route normalises the samples first
+      if (mode == 2) {
         PhaseScope ps(ctx, PH_DENSE_SAMPLE);
         k_dense_sample<<<ctx->num_sms * 8, kThreads, 0, ctx->stream>>>(P, x, M);
       }
@@ -1500,12 +1502,13 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
         const int R = dig[pp];
         const long long Lp = L >> R;
         const int cols = (int)std::min<long long>(Lp, std::max(1, 4096 >> R));
-        const size_t smem = sizeof(cd) * ((size_t)(1 << R) * cols + (1 << R));
+        const size_t smem = sizeof(cd) * ((size_t)(1 << R) * cols + (1 << R) + 32 * (size_t)cols);
         const long long nblk = (M / L) * (Lp / cols);
         const int grid = (int)std::min<long long>(nblk, (long long)ctx->num_sms * 8);
         {
-          PhaseScope ps(ctx, PH_DENSE_FFT);
-          k_fft_pass<<<grid, kThreads, smem, ctx->stream>>>(x, M, Lp, R, cols);
+          const bool sample = (pp == 0 && mode != 2);
+          PhaseScope ps(ctx, sample ? PH_DENSE_SAMPLE : PH_DENSE_FFT);
+          k_fft_pass<<<grid, kThreads, smem, ctx->stream>>>(x, M, Lp, R, cols, P, sample ? 1 : 0);
         }
         CK(cudaGetLastError());
         L = Lp;
