@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the oracle check of a sample of the timed output")
+    ap.add_argument("--no-config2", action="store_true",
+                    help="skip the single-instance Heston sweep over n (TT-SFFT 16..40, dense 16..32)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default first-tier carves instead of tuning them for the batch first")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
@@ -471,6 +473,10 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
     if not args.no_dense and rank == 0:
         dense = dense_baseline(pricer, problems, strikes, torch, dev, fp64_peak)
 
+    sweep = None
+    if not args.no_config2 and rank == 0 and not mixed:
+        sweep = config2_sweep(pricer, torch, dev)
+
     cpu = None
     if pool is not None and rank == 0 and not args.no_cpu:
         rate, one_rate, n_inst, skipped, wall, timed = oracle_sample(pool, problems, strikes,
@@ -523,6 +529,7 @@ def run_ours(args, rank, world, local_rank, pool, ncores):
         "graph_replay": graph,
         "cpu_baseline": cpu,
         "dense_fft": dense,
+        "config2_sweep": sweep,
     }
     pricer.close()
     return line
@@ -585,6 +592,57 @@ def ctypes_sizeof_problem():
     import ctypes
     from paper_2607_28435_b300 import sfft
     return ctypes.sizeof(sfft.SfftProblem)
+
+
+def config2_sweep(pricer, torch, dev, reps=3):
+    """The single Heston instance of the sweep configuration (kappa 1.5768,
+    theta 0.0398, sigma_v 0.5751, rho -0.5711, v0 0.0175, r 0.025, T 1, tol
+    1e-12) at n = 16..40: TT-SFFT time per call (best of reps, CUDA events,
+    operators cached) with the profiler's split into the integrand build and
+    the core (zip-up, rounding, readout; the paper's "Core" time), and the
+    dense-FFT route at n <= 32. The crossover is the smallest n from which
+    the TT-SFFT call is faster than the dense one."""
+    from paper_2607_28435_b300 import sfft, workloads as wl
+    rows = []
+    for n in range(16, 41):
+        p = wl.config2_heston(n)
+        st = sfft.strike_window(p)
+        pr = torch.empty(max(st[2], 1), dtype=torch.float64, device=dev)
+        lk = torch.empty_like(pr)
+        pricer.price_batch([p], [st], pr, lk)  # builds the operator of this n
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pricer.price_batch([p], [st], pr, lk)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        pricer.profile(True)
+        pricer.profile_read(reset=True)
+        pricer.price_batch([p], [st], pr, lk)
+        torch.cuda.synchronize()
+        ph = pricer.profile_read(reset=True)
+        pricer.profile(False)
+        row = {"n": n, "tt_ms": best, "tt_build_ms": ph["probe"]["ms"] + ph["build"]["ms"] + ph["cross"]["ms"],
+               "tt_core_ms": ph["zipup"]["ms"] + ph["round"]["ms"] + ph["readout"]["ms"], "strikes": st[2]}
+        if n <= 32:
+            pricer.dense_price_batch([p], [st], pr, lk)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pricer.dense_price_batch([p], [st], pr, lk)
+            e1.record()
+            torch.cuda.synchronize()
+            row["dense_ms"] = e0.elapsed_time(e1)
+        rows.append(row)
+    cross = next((r["n"] for r in rows if "dense_ms" in r and r["tt_ms"] < r["dense_ms"]), None)
+    core_cross = next((r["n"] for r in rows if "dense_ms" in r and r["tt_core_ms"] < r["dense_ms"]), None)
+    return {"rows": rows, "crossover_n_total": cross, "crossover_n_core": core_cross,
+            "how": "one Heston instance (the sweep configuration), strikes |log K/S0| <= 1.5; TT-SFFT best of "
+                   f"{reps} calls with the operator cached, profiler phases from one more call; dense-FFT "
+                   "route one timed call after a warm one"}
 
 
 def dense_baseline(pricer, problems, strikes, torch, dev, fp64_peak):
