@@ -331,13 +331,22 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
             sy *= inv;
             G2 = fma(sx, sx, sy * sy);
           }
-          const double r = sqrt(fma(D, D, 4.0 * G2));
-          const double w = copysign(2.0, D) / (fabs(D) + r);  // t = w |g|
-          const double c = rsqrt(fma(w * w, G2, 1.0));
-          const double cw = c * w;
+          // Rotation with tangent t = w |g|, w = 2 sign(D) / h, where
+          // u = D^2 + 4 |g|^2, r = sqrt(u), h = |D| + r. Since
+          // 1 + w^2 |g|^2 = 2 r / h, with q = 1 / sqrt(2 r h):
+          //   c = 1 / sqrt(1 + t^2) = h q,   c w = 2 sign(D) q,
+          //   w |g|^2 = 2 sign(D) |g|^2 / h = 4 sign(D) |g|^2 r q^2,
+          // two reciprocal square roots and no division
+          const double u = fma(D, D, 4.0 * G2);
+          const double r = u * rsqrt(u);
+          const double h = fabs(D) + r;
+          const double qq = rsqrt(2.0 * r * h);
+          const double c = h * qq;
+          const double cw = copysign(2.0 * qq, D);
           const double spx = cw * sx, spy = -cw * sy;           // sp = c w conj(g)
           // w|g|^2 in true units (w G2 carries one factor of the scaling)
-          const double dn = (big > 1e140) ? w * G2 * big : w * G2;
+          const double wg2 = copysign(4.0 * G2 * r * qq * qq, D);
+          const double dn = (big > 1e140) ? wg2 * big : wg2;
           for (int i = sub; i < p; i += G) {
             const cd x = ca[i], y = cb[i];
             ca[i] = mkc(fma(c, x.x, -fma(spx, y.x, -spy * y.y)), fma(c, x.y, -fma(spx, y.y, spy * y.x)));
