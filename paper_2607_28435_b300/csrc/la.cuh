@@ -238,8 +238,10 @@ static __device__ void form_q(const cd* W, int ld, int h, int kq, const cd* taus
 // sp = c t conj(g)/|g| the update is a <- c a - sp b, b <- conj(sp) a + c b.
 // (Rutishauser's rotation with the phase of g moved onto the new b; b is
 // then a singular direction up to a unit factor, which no caller depends on.)
-// A sweep whose rotations were all below 1e-8 relative ends the iteration:
-// cyclic Jacobi converges quadratically, so it leaves the pairs near 1e-16.
+// A sweep in which no rotated pair had |g|^2 > big2 alpha beta (big2 = 1e-8,
+// couplings below 1e-4, unless the caller passes another) ends the
+// iteration: cyclic Jacobi converges quadratically, so it leaves the pairs
+// near big2.
 // Returns the number of sweeps used, or -1 if max_sweeps did not reach
 // convergence.
 __device__ __forceinline__ int jacobi_group_log2(int npair, int p) {
@@ -257,7 +259,7 @@ __device__ __forceinline__ int jacobi_group_log2(int npair, int p) {
   return best;
 }
 
-static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int* sh_flag) {
+static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int* sh_flag, double big2 = 1e-8) {
   const int lane = lane_id(), warp = warp_id();
   if (m < 2) return 0;
   const int mp = m + (m & 1);
@@ -355,7 +357,7 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
           if (sub == 0) {
             cn2[a] = fmax(al - dn, 0.0);
             cn2[b] = be + dn;
-            atomicOr(sh_flag, (g2 > 1e-8 * ab) ? 7 : (g2 > 1e-20 * ab) ? 3 : 1);
+            atomicOr(sh_flag, (g2 > big2 * ab) ? 7 : (g2 > 1e-20 * ab) ? 3 : 1);
           }
         }
       }
@@ -363,8 +365,9 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
     }
     const int any = *sh_flag;
     __syncthreads();
-    // every rotation of this sweep was below 1e-4 relative: Jacobi's quadratic
-    // convergence leaves every pair near 1e-8 / (relative gap) after it. The
+    // every rotation of this sweep was below sqrt(big2) relative (1e-4 by
+    // default): Jacobi's quadratic convergence leaves every pair near big2 /
+    // (relative gap) after it. The
     // rotations are unitary, so A V = [columns] stays exact whatever is left;
     // the residual only makes the kept columns orthogonal to ~1e-8, and their
     // norms (the singular values used for truncation) accurate to ~1e-16
@@ -380,9 +383,10 @@ __host__ __device__ inline size_t ts_svd_smem_bytes(int p, int hb) {
 }
 
 struct TsSvd {
-  int m;          // number of singular triplets = min(q, p)
+  int m;          // number of singular triplets = min(q, p) (pq_svd: the QR rank kept)
   int sweeps;     // Jacobi sweeps (-1: not converged)
   double flops;   // algorithmic FP64 flops of this factorisation
+  double tail2;   // squared norm dropped before the SVD (pq_svd; 0 for ts_svd)
 };
 
 // Algorithmic FP64 flop counts (complex multiply-add = 8 real flops), in
@@ -427,15 +431,20 @@ __host__ __device__ inline double flops_gemm(long long m, long long n, long long
 struct RowBasis {
   int k;
   double flops;
+  double tail2;  // ||R[k:, k:]||_F^2 at the stop: the squared norm of the dropped rows
 };
 
 static __device__ RowBasis pivqr_trunc(cd* A, int lda, int m, int ncol, double delta_rel, int kmax, cd* taus,
-                                       double* cn, int* perm) {
+                                       double* cn, int* perm, double delta_abs2 = -1.0) {
+  // delta_abs2 >= 0 replaces the relative threshold by an absolute one:
+  // stop once ||R[k:, k:]||_F^2 <= delta_abs2
   __shared__ int ctl;  // 1 once the rank is found
+  __shared__ double tail_sh;
   const int lane = lane_id(), warp = warp_id();
   RowBasis out;
   out.k = 1;
   out.flops = 0.0;
+  out.tail2 = 0.0;
   // exact column norms
   for (int j = warp; j < ncol; j += n_warps()) {
     const cd* cj = A + (size_t)j * lda;
@@ -451,7 +460,7 @@ static __device__ RowBasis pivqr_trunc(cd* A, int lda, int m, int ncol, double d
   double total = 0.0;
   for (int j = lane; j < ncol; j += 32) total += cn[j];
   total = warp_sum(total);
-  const double delta2 = delta_rel < 0.0 ? -1.0 : delta_rel * delta_rel * total;
+  const double delta2 = delta_abs2 >= 0.0 ? delta_abs2 : delta_rel < 0.0 ? -1.0 : delta_rel * delta_rel * total;
   const int kstop = min(min(m, ncol), kmax);
   for (int k = 0;; ++k) {
     if (warp == 0) {
@@ -499,11 +508,15 @@ static __device__ RowBasis pivqr_trunc(cd* A, int lda, int m, int ncol, double d
         const cd tau = hh_reflector_warp(A + (size_t)k * lda, k, m);
         if (lane == 0) taus[k] = tau;
       }
-      if (lane == 0) ctl = stop ? 1 : 0;
+      if (lane == 0) {
+        ctl = stop ? 1 : 0;
+        tail_sh = tr;
+      }
     }
     __syncthreads();
     if (ctl) {
       out.k = max(k, 1);
+      out.tail2 = tail_sh;
       break;
     }
     const cd tau = taus[k];
@@ -571,6 +584,36 @@ static __device__ int stream_qr(const cd* Z, long long q, int p, int ldz, cd* W,
 // device fault; every kernel reads it at each factorisation.
 static __device__ int la_jacobi_cap = 60;
 
+// After Hestenes' method on the m columns of V (p rows, leading dim p): the
+// column norms are the singular values; sort them descending (stable by
+// index) into sig[0..m) and normalise the columns in the same order. W:
+// smem scratch of p * (m + 1) elements.
+static __device__ void svd_finish(cd* V, int p, int m, cd* W, double* sig) {
+  double* nrm = reinterpret_cast<double*>(W);
+  for (int c = warp_id(); c < m; c += n_warps()) {
+    double s = 0.0;
+    for (int i = lane_id(); i < p; i += 32) s += cabs2(V[(size_t)c * p + i]);
+    s = warp_sum(s);
+    if (lane_id() == 0) nrm[c] = sqrt(s);
+  }
+  __syncthreads();
+  cd* Vs = W + p;  // after the norms
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    int rank = 0;
+    const double sc = nrm[c];
+    for (int o = 0; o < m; ++o) {
+      const double so = nrm[o];
+      rank += (so > sc) || (so == sc && o < c);
+    }
+    sig[rank] = sc;
+    const double inv = sc > 1e-290 ? 1.0 / sc : 0.0;
+    for (int i = 0; i < p; ++i) Vs[(size_t)rank * p + i] = cscale(V[(size_t)c * p + i], inv);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < p * m; idx += blockDim.x) V[idx] = Vs[idx];
+  __syncthreads();
+}
+
 static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, int wcap, cd* V,
                         double* sig, cd* taus, int* sh_flag) {
   const int hb = wcap / p - p;
@@ -599,31 +642,8 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
     }
     out.flops = f + flops_hestenes(p, m, out.sweeps < 0 ? cap : out.sweeps) + (double)(4 * p * m);
   }
-  // column norms
-  double* nrm = reinterpret_cast<double*>(W);  // W is free now
-  for (int c = warp_id(); c < m; c += n_warps()) {
-    double s = 0.0;
-    for (int i = lane_id(); i < p; i += 32) s += cabs2(V[(size_t)c * p + i]);
-    s = warp_sum(s);
-    if (lane_id() == 0) nrm[c] = sqrt(s);
-  }
-  __syncthreads();
-  // sort descending (stable by index), normalise into W after the norms
-  cd* Vs = W + p;  // p*m elements, fits in (p+hb)*p - p
-  for (int c = threadIdx.x; c < m; c += blockDim.x) {
-    int rank = 0;
-    const double sc = nrm[c];
-    for (int o = 0; o < m; ++o) {
-      const double so = nrm[o];
-      rank += (so > sc) || (so == sc && o < c);
-    }
-    sig[rank] = sc;
-    const double inv = sc > 1e-290 ? 1.0 / sc : 0.0;
-    for (int i = 0; i < p; ++i) Vs[(size_t)rank * p + i] = cscale(V[(size_t)c * p + i], inv);
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < p * m; idx += blockDim.x) V[idx] = Vs[idx];
-  __syncthreads();
+  out.tail2 = 0.0;
+  svd_finish(V, p, m, W, sig);
   return out;
 }
 
@@ -638,6 +658,54 @@ __device__ __forceinline__ int trunc_rank(const double* sig, int m, double delta
     if (tail <= d2) k = i; else break;
   }
   return max(k, 1);
+}
+
+// As trunc_rank with tail2 already dropped: the smallest k >= 1 with
+// tail2 + sum_{i >= k} sig_i^2 <= delta^2.
+__device__ __forceinline__ int trunc_rank_tail(const double* sig, int m, double delta, double tail2) {
+  double tail = tail2;
+  const double d2 = delta * delta;
+  int k = m;
+  for (int i = m - 1; i >= 0; --i) {
+    tail = fma(sig[i], sig[i], tail);
+    if (tail <= d2) k = i; else break;
+  }
+  return max(k, 1);
+}
+
+// Dominant right singular vectors of A (q x p, column-major in smem, leading
+// dim lda; overwritten). A Householder QR with column pivoting, A P = Q R,
+// stops at the first k' whose dropped rows have ||R[k':, k':]||_F^2 <= pre2;
+// Hestenes' method then takes the SVD of the kept rows, B = R[:k', :] P^T
+// (k' x p): the columns of L = B^H (p x k') are orthogonalised, and their
+// norms and directions are the singular values and right singular vectors of
+// B. Since A^H A = B^H B + (dropped)^H (dropped), the singular values satisfy
+// sig_i(B) <= sig_i(A), and for every k
+//   sum_{i>=k} sig_i(A)^2 <= sum_{i>=k} sig_i(B)^2 + tail2 <= that + pre2,
+// so truncating B's SVD with the dropped norm tail2 counted against the
+// budget keeps the error bound of a truncated SVD of A, at a rank at most one
+// interval of pre2 above the optimal one. Output as ts_svd (m = k'), with
+// tail2 returned. big2: the squared relative rotation size below which a
+// sweep ends the Jacobi iteration (see hestenes). Smem: V (p x k'), sig and
+// perm (p entries), taus (min(q, p)).
+static __device__ TsSvd pq_svd(cd* A, int lda, int q, int p, double pre2, cd* V, double* sig, cd* taus,
+                               int* perm, int* sh_flag, double big2 = 1e-8) {
+  const RowBasis rb = pivqr_trunc(A, lda, q, p, -1.0, min(q, p), taus, sig, perm, pre2);
+  const int m = rb.k;
+  // L[perm[j], i] = conj(R[i, j]) for j >= i (R upper trapezoidal in pivoted order)
+  for (int idx = threadIdx.x; idx < p * m; idx += blockDim.x) {
+    const int i = idx / p, j = idx - i * p;
+    V[(size_t)i * p + perm[j]] = (j >= i) ? cconj(A[(size_t)j * lda + i]) : mkc(0.0, 0.0);
+  }
+  __syncthreads();
+  TsSvd out;
+  out.m = m;
+  const int cap = la_jacobi_cap;
+  out.sweeps = hestenes(V, p, p, m, cap, sh_flag, big2);
+  out.flops = rb.flops + flops_hestenes(p, m, out.sweeps < 0 ? cap : out.sweeps) + (double)(4 * p * m);
+  out.tail2 = rb.tail2;
+  svd_finish(V, p, m, A, sig);
+  return out;
 }
 
 // CTA-wide argmax of |x_i|^2 over i < len with x given by a functor; ties go

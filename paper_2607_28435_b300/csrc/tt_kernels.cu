@@ -641,9 +641,19 @@ __global__ void k_mpo_interp(int n, int P, cd* W, int core_stride,
 // ---------------------------------------------------------------------------
 // Right-to-left step at site s, X = G_s as r_s x (d r_{s+1}) = U S V^H:
 // the SVD of Z = X^H gives U and S; with k kept, Y = Z U_k = V_k S_k is
-// re-orthonormalised by QR, Y = Q_V R_V, so that X ~= (U_k R_V^H) Q_V^H exactly
-// up to the truncation, with Q_V^H right-orthonormal to machine precision
-// (no division by small singular values).
+// orthonormalised by QR, Y = Q_V R_V, and X ~= (X Q_V) Q_V^H: G_s becomes
+// Q_V^H, right-orthonormal to machine precision, and X Q_V moves into
+// G_{s-1} (no division by small singular values). The projection onto
+// span(Q_V) is exact whatever the orthogonality of U_k, so the error is the
+// truncated tail plus the coupling of kept to dropped directions times the
+// dropped singular values; the Jacobi iteration may therefore stop once its
+// rotations fall below 1e-2 relative.
+// The SVD of Z is taken after a column-pivoted QR that drops trailing rows of
+// squared norm at most delta^2 / 64 (pq_svd): Hestenes' method then runs on
+// the k' kept rows only, and the dropped norm counts against the truncation
+// budget, so the error bound is that of the plain truncated SVD and the rank
+// exceeds the plain SVD's only where its tail lies within delta^2 / 64 of
+// delta^2.
 __global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count, int* counter, const int* n_arr, int d,
                            int left_orth,
                            const double* tol_arr, const int* maxrank_arr,
@@ -660,6 +670,7 @@ __global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count,
   // ranks of the instance in flight: thread 0 updates them between barriers,
   // every thread reads them, so they live in shared memory
   __shared__ int r[SFFT_MAXN_DEV + 1];
+  __shared__ int perm_s[SFFT_SLOT_RANK_DEV];  // column order of the pivoted QR
   const int count_ = dcount ? *dcount : count;
   double fl = 0.0;
   WORK_LOOP_BEGIN(list, count_, counter)
@@ -731,14 +742,22 @@ __global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count,
         cd* Zt = tmp;
         cd* Y = tmp + (size_t)q * r0;
         cd* QV = Y + (size_t)q * r0;
+        // Z row-major into the scratch (for Y below) and column-major into W
+        // (leading dim pmax + hb >= d r1 = q), where the SVD factors it
+        const int ldw = pmax + hb;
         for (int idx = threadIdx.x; idx < q * r0; idx += blockDim.x) {
-          const int row = idx / r0, a = idx - row * r0;
-          Zt[idx] = cconj(Gs[(size_t)a * q + row]);
+          const int a = idx / q, row = idx - a * q;
+          const cd z = cconj(Gs[idx]);
+          Zt[(size_t)row * r0 + a] = z;
+          sm.W[(size_t)a * ldw + row] = z;
         }
         __syncthreads();
-        TsSvd sv = ts_svd(Zt, q, r0, r0, sm.W, (pmax + hb) * pmax, sm.V, sm.sig, sm.tau, sm.flag);
+        // the pivoted-QR prefilter may drop a norm of up to delta^2 / 64 before
+        // the SVD; the truncation counts it against the budget
+        TsSvd sv = pq_svd(sm.W, ldw, q, r0, delta * delta * (1.0 / 64.0), sm.V, sm.sig, sm.tau, perm_s,
+                          sm.flag, 1e-4);
         if (sv.sweeps < 0) st = SFFT_ENOCONV_DEV;
-        int k = trunc_rank(sm.sig, sv.m, delta);
+        int k = trunc_rank_tail(sm.sig, sv.m, delta, sv.tail2);
         if (k > rmax) {
           st = SFFT_ERANK_DEV;
           k = rmax;
@@ -759,12 +778,14 @@ __global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count,
           const int c = idx / q, row = idx - c * q;
           Gs[idx] = cconj(QV[(size_t)c * q + row]);
         }
-        // T1 = U_k R_V^H (r0 x kk) into Y (free now), then Gp <- Gp T1
+        // T1 = X Q_V (r0 x kk) into Y (free now), then Gp <- Gp T1: the rows
+        // of X are projected onto span(Q_V) exactly, so the result does not
+        // depend on how orthogonal the Jacobi vectors U_k are
         for (int idx = threadIdx.x; idx < r0 * kk; idx += blockDim.x) {
           const int a = idx / kk, c = idx - a * kk;
+          const cd* qc = QV + (size_t)c * q;
           cd acc = mkc(0.0, 0.0);
-          // (R_V^H)[j, c] = conj(R_V[c, j]), nonzero for j >= c
-          for (int j = c; j < k; ++j) acc = cfma(sm.V[(size_t)j * r0 + a], cconj(sm.W[(size_t)j * q + c]), acc);
+          for (int row = 0; row < q; ++row) acc = cfma(cconj(Zt[(size_t)row * r0 + a]), qc[row], acc);
           Y[idx] = acc;
         }
         __syncthreads();
@@ -781,7 +802,7 @@ __global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count,
         if (threadIdx.x == 0) r[s] = kk;
         __syncthreads();
         fl += sv.flops + flops_gemm(q, r0, k) + flops_qr(q, k) + flops_formq(q, kk) +
-              flops_gemm(r0, kk, k) + flops_gemm(rows, kk, r0);
+              flops_gemm(r0, kk, q) + flops_gemm(rows, kk, r0);
       }
     }
     for (int i = threadIdx.x; i <= n; i += blockDim.x) rg[i] = r[i];
