@@ -146,22 +146,35 @@ static __device__ void hh_apply_norms(const cd* v, int k, int h, cd t, cd* A, in
 // returned tau is valid in every lane. The sum of squares is taken unscaled;
 // only when it would leave the safe range (entries below ~1e-140 or above
 // ~1e140) is the column rescaled by its largest modulus first.
-static __device__ cd hh_reflector_warp(cd* col, int k, int h) {
+// tot_known >= 0 is the caller's exact squared norm of col[k..h) (a pivoted
+// QR carries it for every column), which replaces the warp's own sum; a
+// column with x = 0 then gets the reflector beta = -a0 instead of H = I,
+// which is as exact. In the safe range beta and 1/beta come from one
+// reciprocal square root.
+static __device__ cd hh_reflector_warp(cd* col, int k, int h, double tot_known = -1.0) {
   const int lane = lane_id();
   // the pivot is read by lane 0 only and broadcast, so lane 0 may overwrite
   // it below without racing the other lanes
   cd a0 = (lane == 0) ? col[k] : mkc(0.0, 0.0);
   a0.x = __shfl_sync(0xffffffffu, a0.x, 0);
   a0.y = __shfl_sync(0xffffffffu, a0.y, 0);
-  double ss = 0.0;
-  for (int i = k + 1 + lane; i < h; i += 32) ss = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, ss));
-  ss = warp_sum(ss);
-  if (ss == 0.0 && a0.y == 0.0) return mkc(0.0, 0.0);  // H = I
-  const double tot = cabs2(a0) + ss;
-  double beta;
+  double tot;
+  if (tot_known >= 0.0) {
+    tot = tot_known;
+    if (tot == 0.0) return mkc(0.0, 0.0);  // a zero column: H = I
+  } else {
+    double ss = 0.0;
+    for (int i = k + 1 + lane; i < h; i += 32) ss = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, ss));
+    ss = warp_sum(ss);
+    if (ss == 0.0 && a0.y == 0.0) return mkc(0.0, 0.0);  // H = I
+    tot = cabs2(a0) + ss;
+  }
+  double beta, rb;
   cd scal;
   if (tot > 1e-280 && tot < 1e280) {
-    beta = -copysign(sqrt(tot), a0.x);
+    const double rs = rsqrt(tot);
+    beta = -copysign(tot * rs, a0.x);
+    rb = -copysign(rs, a0.x);  // 1 / beta
     const cd d = mkc(a0.x - beta, a0.y);  // |d| >= |beta|: no cancellation
     const double rd = 1.0 / cabs2(d);
     scal = mkc(d.x * rd, -d.y * rd);
@@ -177,8 +190,8 @@ static __device__ cd hh_reflector_warp(cd* col, int k, int h) {
     const cd a0s = cscale(a0, inv);
     beta = -copysign(amax * sqrt(cabs2(a0s) + s), a0.x);
     scal = cdiv(mkc(1.0, 0.0), mkc(a0.x - beta, a0.y));
+    rb = 1.0 / beta;
   }
-  const double rb = 1.0 / beta;
   const cd tau = mkc((beta - a0.x) * rb, -a0.y * rb);
   for (int i = k + 1 + lane; i < h; i += 32) col[i] = cmul(col[i], scal);
   if (lane == 0) col[k] = mkc(beta, 0.0);
@@ -464,21 +477,25 @@ static __device__ RowBasis pivqr_trunc(cd* A, int lda, int m, int ncol, double d
   const int kstop = min(min(m, ncol), kmax);
   for (int k = 0;; ++k) {
     if (warp == 0) {
-      // trailing norm ||R[k:, k:]||^2 and the pivot column
-      double tr = 0.0, best = -1.0;
+      // trailing norm ||R[k:, k:]||^2 and the pivot column. The norms are
+      // >= 0, so their bit patterns order like the values: the argmax runs
+      // on integers (ties to the lowest index), off the FP64 pipe
+      double tr = 0.0;
+      long long best = -1;
       int bi = 0x7fffffff;
       for (int j = k + lane; j < ncol; j += 32) {
         const double v = cn[j];
         tr += v;
-        if (v > best) {
-          best = v;
+        const long long key = __double_as_longlong(v);
+        if (key > best) {
+          best = key;
           bi = j;
         }
       }
       tr = warp_sum(tr);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) {
           best = ov;
@@ -505,7 +522,7 @@ static __device__ RowBasis pivqr_trunc(cd* A, int lda, int m, int ncol, double d
           }
         }
         __syncwarp();
-        const cd tau = hh_reflector_warp(A + (size_t)k * lda, k, m);
+        const cd tau = hh_reflector_warp(A + (size_t)k * lda, k, m, cn[k]);
         if (lane == 0) taus[k] = tau;
       }
       if (lane == 0) {
