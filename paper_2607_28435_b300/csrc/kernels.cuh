@@ -66,12 +66,15 @@ struct RoundSmem {
 };
 // Shared memory of k_zipup: 8-row panel blocks at 64 columns and a
 // 64 x (rank cap + 1) basis block, small enough for two CTAs per SM.
-inline RoundSmem zip_smem(bool small = false) {
-  // small: W only (70 x 64; the explicit Q is formed in T's spent columns),
-  // three CTAs per SM (with the kernel's 85-register bound)
+// small: W only, wrows x 64 elements (hb = wrows - 64 may be negative; the
+// explicit Q is formed in T's spent columns, else in global scratch). At
+// wrows = 32 (32 KB) six 128-thread CTAs share an SM (with the kernel's
+// 85-register bound); the tensor-core variant stages its operand tiles in W
+// and takes wrows = 70 at 256 threads, three per SM.
+inline RoundSmem zip_smem(bool small = false, int wrows = 70) {
   RoundSmem r;
   r.pmax = LA_MAXP;
-  r.hb = small ? 6 : 8;
+  r.hb = small ? wrows - LA_MAXP : 8;
   r.vcap = small ? 1 : LA_MAXP * (SFFT_SLOT_RANK_DEV + 1);
   r.bytes = sizeof(cd) * ((size_t)(r.pmax + r.hb) * r.pmax + r.vcap + r.pmax) + sizeof(double) * r.pmax + 320;
   return r;

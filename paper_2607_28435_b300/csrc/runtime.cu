@@ -694,16 +694,19 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   ctx->defer_heads[0] = defer_build;
   ctx->defer_heads[1] = defer_cross;
   ctx->defer_heads[2] = defer_zip;
-  const RoundSmem zs1 = zip_smem(true);
+  const bool mixed = ctx->precision == SFFT_PRECISION_MIXED;
+  // tier 1 of the FP64 path: 128-thread CTAs with a 32 x 64 panel block, six
+  // per SM; the tensor-core variant keeps 256 threads and a 70 x 64 block
+  const int zthreads1 = mixed ? kThreads : kThreadsSmall;
+  const RoundSmem zs1 = zip_smem(true, mixed ? 70 : 32);
   const RoundSmem zs = zip_smem();
   // mixed precision: tier 1 runs each site's MPO contraction on the tensor
   // cores; tier 2 (rare, the full carve) stays FP64
-  const bool mixed = ctx->precision == SFFT_PRECISION_MIXED;
   // The occupancy calculator reports one CTA per SM for any kernel that
   // allocates tensor memory; the hardware co-schedules as many as their
   // allocations fit (128 of the SM's 512 columns each here), so the tensor-
   // core zip-up takes the FP64 kernel's occupancy, capped at four per SM.
-  int zbps = blocks_per_sm((const void*)k_zipup, zs1.bytes);
+  int zbps = blocks_per_sm((const void*)k_zipup, zs1.bytes, zthreads1);
   if (mixed) zbps = std::min(zbps, 4);
   if (ctx->cur.zip_ctas > 0) zbps = std::min(zbps, ctx->cur.zip_ctas);
   const int zg1 = std::min(cnt, ctx->num_sms * zbps);
@@ -712,7 +715,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     return s;
   {
     PhaseScope ps(ctx, PH_ZIPUP);
-    (mixed ? k_zipup_tc : k_zipup)<<<zg1, kThreads, zs1.bytes, ctx->stream>>>(
+    (mixed ? k_zipup_tc : k_zipup)<<<zg1, zthreads1, zs1.bytes, ctx->stream>>>(
         all_dev, cnt, ctr + 3, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
         reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
         SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),

@@ -1175,14 +1175,10 @@ __device__ __forceinline__ void zipup_body(const int* list, int count, int* coun
           CH[(size_t)zperm[i] * k + c] = (c <= i) ? cconj(Tp[(size_t)i * p + c]) : mkc(0.0, 0.0);
         }
         __syncthreads();
-        // 2 k p <= 2 * 33 * 64 fits the smallest carve (70 x 64); V backs it
-        // up; a panel in global memory leaves all of W to Q
-        cd* Qd = gdirect ? sm.W : (2 * k * p <= wcap) ? sm.W + (size_t)p * k : (has_v ? sm.V : nullptr);
-        if (!Qd) {
-          defer_instance(defer, inst);
-          deferred = true;
-          break;
-        }
+        // Q goes behind T's kept columns when W holds both, else in V, else
+        // in the CTA's global scratch Z (unused when T sits in W); a panel in
+        // global memory leaves all of W to Q
+        cd* Qd = gdirect ? sm.W : (2 * k * p <= wcap) ? sm.W + (size_t)p * k : (has_v ? sm.V : Z);
         form_q(Tp, p, p, k, sm.tau, Qd, p);
         for (int idx = threadIdx.x; idx < p * k; idx += blockDim.x) {
           const int row = idx / k, cc = idx - row * k;
