@@ -272,7 +272,38 @@ __device__ __forceinline__ int jacobi_group_log2(int npair, int p) {
   return best;
 }
 
-static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int* sh_flag, double big2 = 1e-8) {
+// x 2^(1023 - eb) as a float (eb: a biased FP64 exponent >= that of |x|),
+// built from the bit fields with integer operations, truncated toward zero;
+// values below the float range (and zero) give 0.
+__device__ __forceinline__ float scaled_f32(double x, int eb) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  const int ef = ex - eb + 127;
+  if (ex == 0 || ef <= 0) return 0.0f;
+  return __uint_as_float((unsigned int)(b >> 32 & 0x80000000ull) | ((unsigned int)ef << 23) |
+                         (unsigned int)((b >> 29) & 0x7fffffull));
+}
+// f 2^(eb - 1023) as a double, exactly, by integer operations (f normal, the
+// result in range; zero and subnormal f give 0).
+__device__ __forceinline__ double f32_unscaled(float f, int eb) {
+  const unsigned int fb = __float_as_uint(f);
+  const int ef = (int)((fb >> 23) & 0xff);
+  if (ef == 0) return 0.0;
+  return __longlong_as_double((long long)(((unsigned long long)(fb & 0x80000000u) << 32) |
+                                          ((unsigned long long)(ef - 127 + eb) << 52) |
+                                          ((unsigned long long)(fb & 0x7fffffu) << 29)));
+}
+
+// F32ROT: the rotation parameters in FP32 from the pair's data scaled by a
+// power of two (integer bit operations: no FP64 instruction), the rotation
+// applied in FP64. c and s then carry FP32 rounding, so each rotation is
+// unitary to ~1e-7 and leaves ~1e-7 of the coupling: the column norms (the
+// singular values) are accurate to ~1e-6 relative, and the columns span the
+// dominant subspaces to within ~1e-7 of the dropped singular values. Only a
+// caller that projects onto the subspace exactly (pq_svd in the rounding)
+// uses it; the FP64 form keeps the exact-unitarity guarantee for the rest.
+template <bool F32ROT>
+static __device__ int hestenes_t(cd* L, int ld, int p, int m, int max_sweeps, int* sh_flag, double big2) {
   const int lane = lane_id(), warp = warp_id();
   if (m < 2) return 0;
   const int mp = m + (m & 1);
@@ -334,7 +365,37 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
         const double al = cn2[a], be = cn2[b];
         const double g2 = fma(gx, gx, gy * gy);
         const double ab = al * be;
-        if (g2 > tol2 * ab && g2 > 1e-290) {
+        if (F32ROT && g2 > tol2 * ab && g2 > 1e-290) {
+          // the same formulas as below, in FP32 on data scaled so that
+          // max(al, be) lies in [1, 2); both are >= 0, so their bit patterns
+          // order like their values
+          const long long kb = max(__double_as_longlong(al), __double_as_longlong(be));
+          const int eb = (int)(kb >> 52);
+          const float alf = scaled_f32(al, eb), bef = scaled_f32(be, eb);
+          const float gxf = scaled_f32(gx, eb), gyf = scaled_f32(gy, eb);
+          const float Df = bef - alf;
+          const float G2f = fmaf(gxf, gxf, gyf * gyf);
+          if (G2f > 0.0f) {
+            const float uf = fmaf(Df, Df, 4.0f * G2f);
+            const float rf = uf * rsqrtf(uf);
+            const float hf = fabsf(Df) + rf;
+            const float qf = rsqrtf(2.0f * rf * hf);
+            const float cwf = copysignf(2.0f * qf, Df);
+            const double c = f32_unscaled(hf * qf, 1023);
+            const double spx = f32_unscaled(cwf * gxf, 1023), spy = f32_unscaled(-cwf * gyf, 1023);
+            const double dn = f32_unscaled(copysignf(4.0f * G2f * rf * qf * qf, Df), eb);
+            for (int i = sub; i < p; i += G) {
+              const cd x = ca[i], y = cb[i];
+              ca[i] = mkc(fma(c, x.x, -fma(spx, y.x, -spy * y.y)), fma(c, x.y, -fma(spx, y.y, spy * y.x)));
+              cb[i] = mkc(fma(c, y.x, fma(spx, x.x, spy * x.y)), fma(c, y.y, fma(spx, x.y, -spy * x.x)));
+            }
+            if (sub == 0) {
+              cn2[a] = fmax(al - dn, 0.0);
+              cn2[b] = be + dn;
+              atomicOr(sh_flag, (g2 > big2 * ab) ? 7 : (g2 > 1e-20 * ab) ? 3 : 1);
+            }
+          }
+        } else if (!F32ROT && g2 > tol2 * ab && g2 > 1e-290) {
           // t, c and sp are invariant under a common scaling of al, be, g;
           // rescale only when the squares below could overflow
           double D = be - al, G2 = g2, sx = gx, sy = gy;
@@ -388,6 +449,10 @@ static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int*
     if (sweep == max_sweeps - 1) return (any & 2) ? -1 : max_sweeps;
   }
   return -1;
+}
+
+static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int* sh_flag, double big2 = 1e-8) {
+  return hestenes_t<false>(L, ld, p, m, max_sweeps, sh_flag, big2);
 }
 
 // Shared-memory layout needed by ts_svd for p columns and row blocks of hb.
@@ -718,7 +783,7 @@ static __device__ TsSvd pq_svd(cd* A, int lda, int q, int p, double pre2, cd* V,
   TsSvd out;
   out.m = m;
   const int cap = la_jacobi_cap;
-  out.sweeps = hestenes(V, p, p, m, cap, sh_flag, big2);
+  out.sweeps = hestenes_t<true>(V, p, p, m, cap, sh_flag, big2);
   out.flops = rb.flops + flops_hestenes(p, m, out.sweeps < 0 ? cap : out.sweeps) + (double)(4 * p * m);
   out.tail2 = rb.tail2;
   svd_finish(V, p, m, A, sig);
