@@ -72,7 +72,7 @@ int64_t sfft_mlp_pack_bytes(const sfft_mlp *net);
 /* Write the packed weight image of net's bfloat16 W_l into `packed` (device,
  * sfft_mlp_pack_bytes(net) bytes, 16-byte aligned): layer 1 as [W_1 | W_1]
  * (the weights of the hi and lo input halves), every later layer as K-chunks
- * of 32 in the K-major operand layout of the tensor cores, the output layer's
+ * of 64 in the K-major operand layout of the tensor cores, the output layer's
  * single row padded with zero rows to 16. */
 sfft_status sfft_mlp_pack(const sfft_mlp *net, void *packed, void *stream);
 

@@ -39,8 +39,13 @@ namespace {
 constexpr int kRows = 128;         // rows per tile = tensor-memory lanes
 constexpr int kMaxW = 256;         // widest hidden layer (accumulator columns)
 constexpr int kMaxHidden = SFFT_MLP_MAX_LAYERS - 1;
-constexpr int kChunk = 32;         // K elements per weight stage
-constexpr int kStages = 3;
+constexpr int kChunk = 64;         // K elements per weight stage
+// The MMA thread waits on one stage barrier per chunk, and every such wait
+// between MMAs leaves the tensor pipe idle for ~180 cycles (measured on
+// B300): 64-wide chunks (four MMAs per wait) in two 32 KB stages beat 32-wide
+// ones in three 16 KB stages (0.866 against 0.940 ms for 2^20 queries); the
+// bulk copy of the next chunk still lands while the current one runs.
+constexpr int kStages = 2;
 constexpr int kEpiWarps = 16;   // eight per slot: two per lane quadrant, one per column half
 constexpr int kThreadsTc = 32 * (2 + kEpiWarps);
 constexpr int kOutRows = 16;    // the output layer's single row, padded to the smallest MMA width
@@ -90,6 +95,64 @@ __device__ __forceinline__ float gelu_f(float z) {
   return fmaf(-(a * t) * pl, e, fmaxf(z, 0.f));
 }
 
+// The same GELU on two activations held as a pair in one 64-bit register:
+// the products and the polynomial run as packed FP32 instructions
+// (fma/mul.rn.f32x2, one instruction for both lanes of the pair), the two
+// reciprocals, exponentials and maxima per element. The arithmetic and its
+// rounding are those of gelu_f (the sign of Q folded into the coefficients).
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t p, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
+}
+// a float constant in both halves (folded by the compiler)
+__device__ __forceinline__ uint64_t f2c(float f) {
+  const uint64_t b = __float_as_uint(f);
+  return (b << 32) | b;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ uint64_t gelu2(uint64_t z) {
+  const uint64_t a = z & 0x7FFFFFFF7FFFFFFFull;  // |z| in both halves
+  float d0, d1;
+  f2_unpack(f2_fma(f2c(0.23164188827f), a, f2c(1.0f)), d0, d1);
+  const uint64_t t = f2_pack(rcp_approx(d0), rcp_approx(d1));
+  // -P(t): the coefficients of gelu_f, negated
+  uint64_t pl = f2_fma(t, f2c(-0.5307027145f), f2c(0.7265760135f));
+  pl = f2_fma(t, pl, f2c(-0.7107068705f));
+  pl = f2_fma(t, pl, f2c(0.142248368f));
+  pl = f2_fma(t, pl, f2c(-0.127414796f));
+  float s0, s1;
+  f2_unpack(f2_mul(f2_mul(a, f2c(-0.72134752044448170f)), a), s0, s1);
+  const uint64_t e = f2_pack(ex2_approx(s0), ex2_approx(s1));
+  float z0, z1;
+  f2_unpack(z, z0, z1);
+  const uint64_t m = f2_pack(fmaxf(z0, 0.f), fmaxf(z1, 0.f));
+  // z Phi(z) = max(z, 0) - |z| t P(t) e
+  return f2_fma(f2_mul(f2_mul(a, t), pl), e, m);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&v);
@@ -99,7 +162,7 @@ __device__ __forceinline__ float bf16_hi(uint32_t p) { return __uint_as_float(p 
 __device__ __forceinline__ float bf16_round(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
 
 // Byte offset, in a layer's part of the packed weight image, of element
-// (n, k) of its W (N x K): chunk c = k / 32 holds N x min(32, K - 32 c)
+// (n, k) of its W (N x K): chunk c = k / 64 holds N x min(64, K - 64 c)
 // elements in the K-major operand layout.
 __device__ __forceinline__ long long packed_off(int n, int k, int N, int K) {
   const int c = k / kChunk, kc = min(kChunk, K - c * kChunk);
@@ -330,13 +393,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const float4 bb = *reinterpret_cast<const float4*>(bias + cb + 4 * i);
-            v[4 * i] += bb.x;
-            v[4 * i + 1] += bb.y;
-            v[4 * i + 2] += bb.z;
-            v[4 * i + 3] += bb.w;
-          }
 #pragma unroll
-          for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(gelu_f(v[2 * i]), gelu_f(v[2 * i + 1]));
+            for (int h = 0; h < 2; ++h) {
+              const int j = 2 * i + h;
+              const uint64_t zz = f2_add(f2_pack(v[2 * j], v[2 * j + 1]), h ? f2_pack(bb.z, bb.w) : f2_pack(bb.x, bb.y));
+              f2_unpack(zz, v[2 * j], v[2 * j + 1]);
+              float g0, g1;
+              f2_unpack(gelu2(zz), g0, g1);
+              pk[j] = pack_bf16(g0, g1);
+            }
+          }
           *reinterpret_cast<uint4*>(As + tc::kmajor_off(rloc, 2 * cb, 2 * N)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
           *reinterpret_cast<uint4*>(As + tc::kmajor_off(rloc, 2 * cb + 16, 2 * N)) =
               make_uint4(pk[4], pk[5], pk[6], pk[7]);
