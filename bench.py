@@ -658,9 +658,8 @@ def dense_baseline(pricer, problems, strikes, torch, dev, fp64_peak):
     """The dense-FFT Carr-Madan baseline on the same batch: one instance per
     n <= 32 (SFFT_DENSE_MAX_N) timed with CUDA events, the batch time
     assembled as sum_n count_n t_n (n = 33, 34 scaled from n = 32 as
-    M log M). At the largest n its phases are timed separately: the first
-    FFT pass with the sampling of the integrand fused in, the other FFT
-    passes, the gather."""
+    M log M). At n = 30 and the largest n its phases are timed separately:
+    the sampling of the integrand, the FFT passes, the gather."""
     by_n = {}
     for p, s in zip(problems, strikes):
         by_n.setdefault(p.n, []).append((p, s))
@@ -726,19 +725,19 @@ def dense_baseline(pricer, problems, strikes, torch, dev, fp64_peak):
                   "M log M from n = 32; phases at n = 30 and the largest n from the profiler; cuFFT (torch.fft) of the "
                   "same lengths up to n = 30 as an external reference"}
     for n, ph in sorted(phases.items()):
-        m, npass = 1 << n, (n + 7) // 8
+        m, npass = 1 << n, (n + 9) // 10  # passes of at most 2^10-point sub-transforms
         fft_ms = ph["dense_fft"]
         rec = dict(ph)
         if fft_ms:
-            # the passes after the first read and write 16 M bytes each and
-            # do their share of the radix-2 work 5 M log2 M
-            rec["fft_passes_hbm_gbs"] = 32.0 * m * (npass - 1) / (fft_ms * 1e-3) / 1e9
+            # every pass reads and writes 16 M bytes; the FFT work is 5 M log2 M
+            rec["fft_passes"] = npass
+            rec["fft_passes_hbm_gbs"] = 32.0 * m * npass / (fft_ms * 1e-3) / 1e9
             if fp64_peak:
-                rec["fft_passes_fp64_frac"] = 5.0 * m * n * (npass - 1) / npass / (fft_ms * 1e-3) / 1e9 / fp64_peak
+                rec["fft_passes_fp64_frac"] = 5.0 * m * n / (fft_ms * 1e-3) / 1e9 / fp64_peak
         if str(n) in cufft:
-            # all passes of our FFT (the first scaled from the others per pass) against cuFFT's Z2Z
-            rec["fft_all_passes_est_ms"] = fft_ms * npass / (npass - 1) if npass > 1 else None
+            # our FFT passes against cuFFT's Z2Z of the same length
             rec["cufft_z2z_ms"] = cufft[str(n)] * 1e3
+            rec["fft_over_cufft"] = fft_ms / (cufft[str(n)] * 1e3) if fft_ms else None
         out.setdefault("phases_ms", {})[str(n)] = rec
     return out
 

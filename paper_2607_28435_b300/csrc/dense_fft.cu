@@ -1,7 +1,7 @@
 // Dense-FFT Carr-Madan baseline (the FFT route of Sec. 4.1): every integrand
-// value x_j, j < M = 2^n, is evaluated inside the first pass of an in-place
-// M-point FFT that runs as a sequence of radix-2^R decimation-in-frequency
-// passes through shared memory, and the requested strikes are gathered and
+// value x_j, j < M = 2^n, is evaluated in index order, the in-place M-point
+// FFT runs as a sequence of ceil(n / 10) passes of 2^R-point transforms
+// (R <= 10) through shared memory, and the requested strikes are gathered and
 // priced (Eq. discretization_dft).
 //
 // Pass with sub-transform length L = 2^R * Lp: for every sub-transform b and
@@ -25,20 +25,58 @@ __device__ __forceinline__ cd unit_root(long long t, long long L) {
   return mkc(cs, -sn);
 }
 
-// With `sample` set (the first pass), the pass evaluates the integrand at its
-// indices instead of reading x: sampling is fused into the first pass, and
-// the array is written once, transformed. The twiddles exp(-2 pi i s k / L)
-// of a block come from two small tables per column, w^(16 kh) and w^kl with
-// k = 16 kh + kl and w = exp(-2 pi i s / L), each entry formed exactly from
-// its reduced integer argument, so a twiddle costs one complex product.
-__global__ void k_fft_pass(cd* x, long long M, long long Lp, int R, int cols, InstParams P, int sample) {
+// One pass of the transform. Each block takes `cols` adjacent offsets s of
+// one sub-transform b: the 2^R elements x[bL + s + r Lp] of every column go
+// to shared memory. The 2^R-point DFT of every
+// column then runs as decimation-in-frequency levels of radix 8 (three bits
+// each, in registers: one butterfly per thread, an exchange through shared
+// memory between levels) and a last level of radix 4 or 2. Level l with span
+// N splits its groups of N rows into the N/r butterflies n1: inputs at rows
+// n1 + (N/r) n2, outputs y_k2 = sum_n2 x_n2 w_r^(n2 k2) times w_N^(n1 k2)
+// back at rows n1 + (N/r) k2. Frequency k = k_0 + r_0 k_1 + r_0 r_1 k_2 + ...
+// then sits at row sum_l k_l (2^R / (r_0 ... r_l)) (digits reversed). Each
+// output is twiddled by exp(-2 pi i s k / L) and stored at bL + s + k Lp.
+// Twiddles: w_(2^R)^j for j < 2^R in a table built once per block of the
+// persistent grid; exp(-2 pi i s k / L) as the product of two 32-entry
+// tables per column, w^(32 k_hi) and w^(k_lo) with k = 32 k_hi + k_lo and
+// w = exp(-2 pi i s / L); every entry is formed exactly from its reduced
+// integer argument. Radix-8 butterfly: the three radix-2 steps of the
+// 8-point DFT, with w_8 = (1 - i)/sqrt 2 and w_8^3 as one sum and one scaling
+// per component and w_8^2 = -i as a swap.
+__device__ __forceinline__ cd mul_mi(cd a) { return mkc(a.y, -a.x); }  // a (-i)
+
+__device__ __forceinline__ void dft4(cd z0, cd z1, cd z2, cd z3, cd& o0, cd& o1, cd& o2, cd& o3) {
+  const cd s0 = cadd(z0, z2), d0 = csub(z0, z2), s1 = cadd(z1, z3), d1 = mul_mi(csub(z1, z3));
+  o0 = cadd(s0, s1);
+  o2 = csub(s0, s1);
+  o1 = cadd(d0, d1);
+  o3 = csub(d0, d1);
+}
+
+// 8-point DFT, natural order in and out; h = 1/sqrt(2)
+__device__ __forceinline__ void dft8(cd* a, double h) {
+  cd u[4], v[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    u[j] = cadd(a[j], a[j + 4]);
+    v[j] = csub(a[j], a[j + 4]);
+  }
+  v[1] = mkc((v[1].x + v[1].y) * h, (v[1].y - v[1].x) * h);    // w_8
+  v[2] = mul_mi(v[2]);                                        // w_8^2
+  v[3] = mkc((v[3].y - v[3].x) * h, -(v[3].x + v[3].y) * h);  // w_8^3
+  dft4(u[0], u[1], u[2], u[3], a[0], a[2], a[4], a[6]);
+  dft4(v[0], v[1], v[2], v[3], a[1], a[3], a[5], a[7]);
+}
+
+__global__ void __launch_bounds__(256) k_fft_pass(cd* x, long long M, long long Lp, int R, int cols) {
   extern __shared__ double4 smem_raw[];
   cd* sm = reinterpret_cast<cd*>(smem_raw);
   const int Rn = 1 << R;
-  cd* tw = sm + (size_t)Rn * cols;
-  cd* t_lo = tw + Rn;            // [c][kl], 16 per column
-  cd* t_hi = t_lo + 16 * cols;   // [c][kh], 16 per column
+  cd* tw = sm + (size_t)Rn * cols;  // w_(2^R)^j
+  cd* t_lo = tw + Rn;               // [c][32]
+  cd* t_hi = t_lo + 32 * cols;      // [c][32]
   for (int i = threadIdx.x; i < Rn; i += blockDim.x) tw[i] = unit_root(i, Rn);
+  const double h = 0.70710678118654752440;  // 1/sqrt(2)
   const long long L = Lp * Rn;
   const long long per_sub = Lp / cols;
   const int lc = __ffs(cols) - 1;  // cols is a power of two
@@ -48,63 +86,76 @@ __global__ void k_fft_pass(cd* x, long long M, long long Lp, int R, int cols, In
     const long long s0 = (blk - b * per_sub) * cols;
     const long long base = b * L + s0;
     __syncthreads();
-    for (int e = threadIdx.x; e < 32 * cols; e += blockDim.x) {
-      const int c = e >> 5, j = e & 15;
+    for (int e = threadIdx.x; e < 64 * cols; e += blockDim.x) {
+      const int c = e >> 6, j = e & 31;
       const long long s = s0 + c;
-      if ((e & 31) < 16)
-        t_lo[c * 16 + j] = unit_root((s * j) & (L - 1), L);
+      if ((e & 63) < 32)
+        t_lo[c * 32 + j] = unit_root((s * j) & (L - 1), L);
       else
-        t_hi[c * 16 + j] = unit_root((s * 16 * j) & (L - 1), L);
+        t_hi[c * 32 + j] = unit_root((s * 32 * j) & (L - 1), L);
     }
     for (int e = threadIdx.x; e < Rn * cols; e += blockDim.x) {
       const int r = e >> lc, c = e & (cols - 1);
       const long long j = base + (long long)r * Lp + c;
-      sm[e] = sample ? integrand(P, j) : x[j];
+      sm[e] = x[j];
     }
     __syncthreads();
-    // radix-2 stages; the last two have trivial twiddles (1, and -i)
-    for (int lh = R - 1; lh >= 2; --lh) {
-      const int half = 1 << lh;
-      const int stride_tw = Rn >> (lh + 1);
-      for (int bf = threadIdx.x; bf < (Rn >> 1) * cols; bf += blockDim.x) {
-        const int c = bf & (cols - 1), j = bf >> lc;
-        const int g = j >> lh, i = j & (half - 1);
-        const int r0 = (g << (lh + 1)) + i, r1 = r0 + half;
-        const cd a = sm[r0 * cols + c], bb = sm[r1 * cols + c];
-        sm[r0 * cols + c] = cadd(a, bb);
-        sm[r1 * cols + c] = cmul(csub(a, bb), tw[i * stride_tw]);
+    int span = Rn, bits = R;
+    while (bits > 0) {
+      const int rb = bits >= 3 ? 3 : bits;
+      const int q = span >> rb;            // stride between a butterfly's inputs
+      const int lq = __ffs(q) - 1;
+      const int tstep = Rn / span;         // w_span^m = tw[m tstep]
+      const int nbf = (Rn >> rb) * cols;
+      for (int t = threadIdx.x; t < nbf; t += blockDim.x) {
+        const int c = t & (cols - 1), u = t >> lc;
+        const int n1 = u & (q - 1);
+        const int row0 = ((u >> lq) * span) + n1;
+        cd a[8];
+        if (rb == 3) {
+#pragma unroll
+          for (int n2 = 0; n2 < 8; ++n2) a[n2] = sm[(size_t)(row0 + n2 * q) * cols + c];
+          dft8(a, h);
+          if (q > 1) {
+#pragma unroll
+            for (int k2 = 1; k2 < 8; ++k2) a[k2] = cmul(a[k2], tw[(n1 * k2 * tstep) & (Rn - 1)]);
+          }
+#pragma unroll
+          for (int k2 = 0; k2 < 8; ++k2) sm[(size_t)(row0 + k2 * q) * cols + c] = a[k2];
+        } else if (rb == 2) {
+#pragma unroll
+          for (int n2 = 0; n2 < 4; ++n2) a[n2] = sm[(size_t)(row0 + n2 * q) * cols + c];
+          dft4(a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7]);
+          if (q > 1) {
+#pragma unroll
+            for (int k2 = 1; k2 < 4; ++k2) a[4 + k2] = cmul(a[4 + k2], tw[(n1 * k2 * tstep) & (Rn - 1)]);
+          }
+#pragma unroll
+          for (int k2 = 0; k2 < 4; ++k2) sm[(size_t)(row0 + k2 * q) * cols + c] = a[4 + k2];
+        } else {
+          const cd a0 = sm[(size_t)row0 * cols + c], a1 = sm[(size_t)(row0 + q) * cols + c];
+          sm[(size_t)row0 * cols + c] = cadd(a0, a1);
+          const cd d = csub(a0, a1);
+          sm[(size_t)(row0 + q) * cols + c] = (q > 1) ? cmul(d, tw[(n1 * tstep) & (Rn - 1)]) : d;
+        }
       }
       __syncthreads();
-    }
-    if (R >= 2) {
-      // span 4: twiddles 1 and exp(-i pi / 2) = -i
-      for (int bf = threadIdx.x; bf < (Rn >> 1) * cols; bf += blockDim.x) {
-        const int c = bf & (cols - 1), j = bf >> lc;
-        const int g = j >> 1, i = j & 1;
-        const int r0 = (g << 2) + i, r1 = r0 + 2;
-        const cd a = sm[r0 * cols + c], bb = sm[r1 * cols + c];
-        sm[r0 * cols + c] = cadd(a, bb);
-        const cd d = csub(a, bb);
-        sm[r1 * cols + c] = i ? mkc(d.y, -d.x) : d;
-      }
-      __syncthreads();
-    }
-    if (R >= 1) {
-      // span 2: twiddle 1
-      for (int bf = threadIdx.x; bf < (Rn >> 1) * cols; bf += blockDim.x) {
-        const int c = bf & (cols - 1), j = bf >> lc;
-        const int r0 = j << 1, r1 = r0 + 1;
-        const cd a = sm[r0 * cols + c], bb = sm[r1 * cols + c];
-        sm[r0 * cols + c] = cadd(a, bb);
-        sm[r1 * cols + c] = csub(a, bb);
-      }
-      __syncthreads();
+      span = q;
+      bits -= rb;
     }
     for (int e = threadIdx.x; e < Rn * cols; e += blockDim.x) {
       const int k = e >> lc, c = e & (cols - 1);
-      const int kr = (int)(__brev((unsigned)k) >> (32 - R));
-      const cd v = sm[kr * cols + c];
-      x[base + (long long)k * Lp + c] = cmul(v, cmul(t_hi[c * 16 + (k >> 4)], t_lo[c * 16 + (k & 15)]));
+      // row of frequency k: its digits (radix 8, then 4 or 2) reversed
+      int p = 0, rem = k, sp = Rn, bl = R;
+      while (bl > 0) {
+        const int rb = bl >= 3 ? 3 : bl;
+        sp >>= rb;
+        p += (rem & ((1 << rb) - 1)) * sp;
+        rem >>= rb;
+        bl -= rb;
+      }
+      const cd v = sm[(size_t)p * cols + c];
+      x[base + (long long)k * Lp + c] = cmul(v, cmul(t_hi[c * 32 + (k >> 5)], t_lo[c * 32 + (k & 31)]));
     }
   }
 }

@@ -125,8 +125,7 @@ __global__ void k_dfma_peak(double* out, int iters);
 
 // dense-FFT baseline
 __global__ void k_dense_sample(InstParams prm, cd* x, long long M);
-__global__ void k_fft_pass(cd* x, long long M, long long Lp, int R, int cols_per_block, InstParams prm,
-                           int sample);
+__global__ void k_fft_pass(cd* x, long long M, long long Lp, int R, int cols_per_block);
 __global__ void k_dense_gather(InstParams prm, const cd* y, int n, const int* digits, int ndig,
                                long long l_begin, int tbits, int q, double* prices, double* logk);
 // statevector emulation of the QFT route

@@ -1478,9 +1478,10 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
       const InstParams& P = prm[k];
       const long long M = 1LL << P.n;
       cd* x = reinterpret_cast<cd*>(xb);
-      // the dense route samples inside its first FFT pass; the statevector
-      // route normalises the samples first
-      if (mode == 2) {
+      // all samples first, in index order, so that every FFT pass is the
+      // transform alone (fused into the first pass they cost the same); the
+      // statevector route then normalises them
+      {
         PhaseScope ps(ctx, PH_DENSE_SAMPLE);
         k_dense_sample<<<ctx->num_sms * 8, kThreads, 0, ctx->stream>>>(P, x, M);
       }
@@ -1493,7 +1494,8 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
         k_scale_unit<<<ctx->num_sms * 8, kThreads, 0, ctx->stream>>>(x, M, nrm_part + nparts);
         CK(cudaGetLastError());
       }
-      const int npass = (P.n + 7) / 8;
+      // passes of at most 2^10-point sub-transforms, digits as even as possible
+      const int npass = (P.n + 9) / 10;
       std::vector<int> dig(npass);
       int left = P.n;
       for (int pp = 0; pp < npass; ++pp) {
@@ -1504,14 +1506,14 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
       for (int pp = 0; pp < npass; ++pp) {
         const int R = dig[pp];
         const long long Lp = L >> R;
-        const int cols = (int)std::min<long long>(Lp, std::max(1, 4096 >> R));
-        const size_t smem = sizeof(cd) * ((size_t)(1 << R) * cols + (1 << R) + 32 * (size_t)cols);
+        const int cols = (int)std::min<long long>(Lp, std::max(1, 2048 >> R));
+        const size_t smem = sizeof(cd) * ((size_t)(1 << R) * cols + (1 << R) + 64 * (size_t)cols);
         const long long nblk = (M / L) * (Lp / cols);
-        const int grid = (int)std::min<long long>(nblk, (long long)ctx->num_sms * 8);
+        const int grid =
+            (int)std::min<long long>(nblk, (long long)ctx->num_sms * blocks_per_sm((const void*)k_fft_pass, smem));
         {
-          const bool sample = (pp == 0 && mode != 2);
-          PhaseScope ps(ctx, sample ? PH_DENSE_SAMPLE : PH_DENSE_FFT);
-          k_fft_pass<<<grid, kThreads, smem, ctx->stream>>>(x, M, Lp, R, cols, P, sample ? 1 : 0);
+          PhaseScope ps(ctx, PH_DENSE_FFT);
+          k_fft_pass<<<grid, kThreads, smem, ctx->stream>>>(x, M, Lp, R, cols);
         }
         CK(cudaGetLastError());
         L = Lp;
