@@ -36,6 +36,9 @@ __device__ __forceinline__ cd unit_root(long long t, long long L) {
 // back at rows n1 + (N/r) k2. Frequency k = k_0 + r_0 k_1 + r_0 r_1 k_2 + ...
 // then sits at row sum_l k_l (2^R / (r_0 ... r_l)) (digits reversed). Each
 // output is twiddled by exp(-2 pi i s k / L) and stored at bL + s + k Lp.
+// The last pass (Lp = 1) has no inter-pass twiddle and contiguous
+// sub-transforms: there a block's columns are `cols` consecutive
+// sub-transforms b, loaded and stored in index order.
 // Twiddles: w_(2^R)^j for j < 2^R in a table built once per block of the
 // persistent grid; exp(-2 pi i s k / L) as the product of two 32-entry
 // tables per column, w^(32 k_hi) and w^(k_lo) with k = 32 k_hi + k_lo and
@@ -78,15 +81,16 @@ __global__ void __launch_bounds__(256) k_fft_pass(cd* x, long long M, long long 
   for (int i = threadIdx.x; i < Rn; i += blockDim.x) tw[i] = unit_root(i, Rn);
   const double h = 0.70710678118654752440;  // 1/sqrt(2)
   const long long L = Lp * Rn;
-  const long long per_sub = Lp / cols;
+  const bool last = Lp == 1;
+  const long long per_sub = last ? 1 : Lp / cols;
   const int lc = __ffs(cols) - 1;  // cols is a power of two
-  const long long nblk = (M / L) * per_sub;
+  const long long nblk = last ? (M / L) / cols : (M / L) * per_sub;
   for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    const long long b = blk / per_sub;
-    const long long s0 = (blk - b * per_sub) * cols;
+    const long long b = last ? blk * cols : blk / per_sub;
+    const long long s0 = last ? 0 : (blk - b * per_sub) * cols;
     const long long base = b * L + s0;
     __syncthreads();
-    for (int e = threadIdx.x; e < 64 * cols; e += blockDim.x) {
+    for (int e = threadIdx.x; e < (last ? 0 : 64 * cols); e += blockDim.x) {
       const int c = e >> 6, j = e & 31;
       const long long s = s0 + c;
       if ((e & 63) < 32)
@@ -95,9 +99,13 @@ __global__ void __launch_bounds__(256) k_fft_pass(cd* x, long long M, long long 
         t_hi[c * 32 + j] = unit_root((s * 32 * j) & (L - 1), L);
     }
     for (int e = threadIdx.x; e < Rn * cols; e += blockDim.x) {
-      const int r = e >> lc, c = e & (cols - 1);
-      const long long j = base + (long long)r * Lp + c;
-      sm[e] = x[j];
+      if (last) {
+        const int c = e >> R, r = e & (Rn - 1);  // x[base + c Rn + r] = x[base + e]
+        sm[(size_t)r * cols + c] = x[base + e];
+      } else {
+        const int r = e >> lc, c = e & (cols - 1);
+        sm[e] = x[base + (long long)r * Lp + c];
+      }
     }
     __syncthreads();
     int span = Rn, bits = R;
@@ -144,7 +152,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(cd* x, long long M, long long 
       bits -= rb;
     }
     for (int e = threadIdx.x; e < Rn * cols; e += blockDim.x) {
-      const int k = e >> lc, c = e & (cols - 1);
+      const int k = last ? (e & (Rn - 1)) : (e >> lc), c = last ? (e >> R) : (e & (cols - 1));
       // row of frequency k: its digits (radix 8, then 4 or 2) reversed
       int p = 0, rem = k, sp = Rn, bl = R;
       while (bl > 0) {
@@ -155,7 +163,10 @@ __global__ void __launch_bounds__(256) k_fft_pass(cd* x, long long M, long long 
         bl -= rb;
       }
       const cd v = sm[(size_t)p * cols + c];
-      x[base + (long long)k * Lp + c] = cmul(v, cmul(t_hi[c * 32 + (k >> 5)], t_lo[c * 32 + (k & 31)]));
+      if (last)
+        x[base + e] = v;
+      else
+        x[base + (long long)k * Lp + c] = cmul(v, cmul(t_hi[c * 32 + (k >> 5)], t_lo[c * 32 + (k & 31)]));
     }
   }
 }

@@ -1506,9 +1506,11 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
       for (int pp = 0; pp < npass; ++pp) {
         const int R = dig[pp];
         const long long Lp = L >> R;
-        const int cols = (int)std::min<long long>(Lp, std::max(1, 2048 >> R));
+        // columns per block: adjacent offsets s, or in the last pass (Lp = 1)
+        // adjacent sub-transforms
+        const int cols = (int)std::min<long long>(Lp == 1 ? (M >> R) : Lp, std::max(1, 2048 >> R));
         const size_t smem = sizeof(cd) * ((size_t)(1 << R) * cols + (1 << R) + 64 * (size_t)cols);
-        const long long nblk = (M / L) * (Lp / cols);
+        const long long nblk = Lp == 1 ? (M / L) / cols : (M / L) * (Lp / cols);
         const int grid =
             (int)std::min<long long>(nblk, (long long)ctx->num_sms * blocks_per_sm((const void*)k_fft_pass, smem));
         {
