@@ -1438,19 +1438,12 @@ static sfft_status price_common(sfft_ctx* ctx, const sfft_problem* probs, int32_
     tb_v.push_back(tbits[i]);
     q_v.push_back(q[i]);
   }
-  // prices of rejected instances are NaN
-  {
-    std::vector<std::pair<long long, int>> bad;
-    for (int i = 0; i < count; ++i)
-      if (host_status[i] != SFFT_OK && q[i] > 0) bad.push_back({out_off[i], q[i]});
-    if (!bad.empty()) {
-      std::vector<double> nanv(65536, NAN);
-      for (auto& bq : bad)
-        CK(cudaMemcpyAsync(prices + bq.first, nanv.data(), sizeof(double) * bq.second,
-                           cudaMemcpyHostToDevice, ctx->stream));
-      CK(cudaStreamSynchronize(ctx->stream));
-    }
-  }
+  // prices of rejected instances are NaN: every byte 0xFF makes the double
+  // 0xFFFFFFFFFFFFFFFF, a quiet NaN, for any q (a rejected q may exceed
+  // SFFT_MAX_STRIKES)
+  for (int i = 0; i < count; ++i)
+    if (host_status[i] != SFFT_OK && q[i] > 0)
+      CK(cudaMemsetAsync(prices + out_off[i], 0xFF, sizeof(double) * (size_t)q[i], ctx->stream));
   const int cnt = (int)prm.size();
   if (cnt == 0) return finish_status(ctx, count, valid, host_status, nullptr, inst_status, info, nullptr, nullptr);
   sfft_status s;

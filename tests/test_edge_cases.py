@@ -74,6 +74,14 @@ def test_strike_set_at_the_limit(pricer):
     with pytest.raises(sfft.SfftError) as ei:
         pricer.price_batch([g], [(0, 1, sfft.MAX_STRIKES + 1)])
     assert ei.value.status == sfft.SFFT_EINVAL
+    # a rejected strike count far over the limit: NaN prices of that length
+    # (no host buffer of the limit's size is involved), the rest of the batch priced
+    lb, sd, _ = cm.strike_window(g)
+    for fn in (pricer.price_batch, pricer.dense_price_batch):
+        c, _, st, _ = fn([g, g], [(0, 1, 1 << 19), (lb, sd, 4)], raise_on_error=False)
+        assert list(st) == [sfft.SFFT_EINVAL, 0]
+        c = c.cpu().numpy()
+        assert np.all(np.isnan(c[:1 << 19])) and np.all(np.isfinite(c[1 << 19:]))
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 4])
