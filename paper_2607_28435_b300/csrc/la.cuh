@@ -18,6 +18,35 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
 __device__ __forceinline__ int n_warps() { return blockDim.x >> 5; }
 
+// x 2^(1023 - eb) as a float (eb: a biased FP64 exponent >= that of |x|),
+// built from the bit fields with integer operations, truncated toward zero;
+// values below the float range (and zero) give 0.
+__device__ __forceinline__ float scaled_f32(double x, int eb) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  const int ef = ex - eb + 127;
+  if (ex == 0 || ef <= 0) return 0.0f;
+  return __uint_as_float((unsigned int)(b >> 32 & 0x80000000ull) | ((unsigned int)ef << 23) |
+                         (unsigned int)((b >> 29) & 0x7fffffull));
+}
+// f 2^(eb - 1023) as a double, exactly, by integer operations (f normal, the
+// result in range; zero and subnormal f give 0).
+__device__ __forceinline__ double f32_unscaled(float f, int eb) {
+  const unsigned int fb = __float_as_uint(f);
+  const int ef = (int)((fb >> 23) & 0xff);
+  if (ef == 0) return 0.0;
+  return __longlong_as_double((long long)(((unsigned long long)(fb & 0x80000000u) << 32) |
+                                          ((unsigned long long)(ef - 127 + eb) << 52) |
+                                          ((unsigned long long)(fb & 0x7fffffu) << 29)));
+}
+
+// The biased exponent eb of a power of two 2^(eb - 1023) >= sqrt(x), x >= 0
+// (from the bit fields; 1023 for x = 0).
+__device__ __forceinline__ int sqrt_exp_bound(double x) {
+  const int e2 = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+  return e2 == 0 ? 1023 : 1023 + ((e2 - 1022 + 1) >> 1);
+}
+
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -96,11 +125,19 @@ static __device__ void hh_apply(const cd* v, int k, int h, cd t, cd* A, int lda,
 }
 
 // As hh_apply with t = conj(tau), and also returns through post(j, c_j[k],
-// ||c_j[k+1..h)||^2) the exact squared norm of the updated rows below the
-// pivot, summed over the group's lanes (the column norms a pivoted QR needs).
-template <class Post>
+// ||c_j[k+1..h)||^2) the squared norm of the updated rows below the pivot,
+// summed over the group's lanes (the column norms a pivoted QR needs). It is
+// recomputed from the updated entries, not downdated, and formed in FP32:
+// cn[j] = ||c_j[k..h)||^2 before the update bounds every entry after it (the
+// reflector preserves that norm), so the entries scaled by the power of two
+// 2^(1023 - eb) >= 1 / sqrt(cn[j]) convert to floats of modulus <= 1 by
+// integer bit operations, and their squares add in FP32 (relative error
+// ~1e-6, entries below 2^-126 of the bound dropped); one FP64 scaling per
+// column restores the units. No FP64 instruction per entry. With F32NORM
+// false the squares add in FP64 (two FMAs per entry) and the norms are exact.
+template <bool F32NORM, class Post>
 static __device__ void hh_apply_norms(const cd* v, int k, int h, cd t, cd* A, int lda, int j0, int j1,
-                                      Post post) {
+                                      Post post, const double* cn) {
   const int ncols = j1 - j0;
   if (ncols <= 0) return;
   const int lg = hh_group_log2(ncols, h - k - 1);
@@ -113,6 +150,7 @@ static __device__ void hh_apply_norms(const cd* v, int k, int h, cd t, cd* A, in
     const int g = g0 + (lane >> lg);
     const bool act = g < ncols;
     cd* c = A + (size_t)(j0 + (act ? g : 0)) * lda;
+    const int eb = act ? sqrt_exp_bound(cn[j0 + g]) : 1023;
     cd dot = (act && sl == 0) ? c[k] : mkc(0.0, 0.0);
     if (act)
       for (int i = k + 1 + sl; i < h; i += S) dot = cfmac(v[i], c[i], dot);
@@ -120,7 +158,8 @@ static __device__ void hh_apply_norms(const cd* v, int k, int h, cd t, cd* A, in
       dot.x += __shfl_xor_sync(0xffffffffu, dot.x, o);
       dot.y += __shfl_xor_sync(0xffffffffu, dot.y, o);
     }
-    double nn = 0.0;
+    float nf32 = 0.f;
+    double nf64 = 0.0;
     cd ck = mkc(0.0, 0.0);
     if (act) {
       const cd f = cmul(t, dot);
@@ -132,11 +171,21 @@ static __device__ void hh_apply_norms(const cd* v, int k, int h, cd t, cd* A, in
       for (int i = k + 1 + sl; i < h; i += S) {
         const cd u = cfma(v[i], nf, c[i]);
         c[i] = u;
-        nn = fma(u.x, u.x, fma(u.y, u.y, nn));
+        if (F32NORM) {
+          const float ux = scaled_f32(u.x, eb), uy = scaled_f32(u.y, eb);
+          nf32 = fmaf(ux, ux, fmaf(uy, uy, nf32));
+        } else {
+          nf64 = fma(u.x, u.x, fma(u.y, u.y, nf64));
+        }
       }
     }
-    for (int o = S >> 1; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-    if (act && sl == 0) post(j0 + g, ck, nn);
+    for (int o = S >> 1; o > 0; o >>= 1) {
+      if (F32NORM)
+        nf32 += __shfl_xor_sync(0xffffffffu, nf32, o);
+      else
+        nf64 += __shfl_xor_sync(0xffffffffu, nf64, o);
+    }
+    if (act && sl == 0) post(j0 + g, ck, F32NORM ? scalbn((double)nf32, 2 * (eb - 1023)) : nf64);
   }
 }
 
@@ -270,28 +319,6 @@ __device__ __forceinline__ int jacobi_group_log2(int npair, int p) {
     }
   }
   return best;
-}
-
-// x 2^(1023 - eb) as a float (eb: a biased FP64 exponent >= that of |x|),
-// built from the bit fields with integer operations, truncated toward zero;
-// values below the float range (and zero) give 0.
-__device__ __forceinline__ float scaled_f32(double x, int eb) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7ff);
-  const int ef = ex - eb + 127;
-  if (ex == 0 || ef <= 0) return 0.0f;
-  return __uint_as_float((unsigned int)(b >> 32 & 0x80000000ull) | ((unsigned int)ef << 23) |
-                         (unsigned int)((b >> 29) & 0x7fffffull));
-}
-// f 2^(eb - 1023) as a double, exactly, by integer operations (f normal, the
-// result in range; zero and subnormal f give 0).
-__device__ __forceinline__ double f32_unscaled(float f, int eb) {
-  const unsigned int fb = __float_as_uint(f);
-  const int ef = (int)((fb >> 23) & 0xff);
-  if (ef == 0) return 0.0;
-  return __longlong_as_double((long long)(((unsigned long long)(fb & 0x80000000u) << 32) |
-                                          ((unsigned long long)(ef - 127 + eb) << 52) |
-                                          ((unsigned long long)(fb & 0x7fffffu) << 29)));
 }
 
 // F32ROT: the rotation parameters in FP32 from the pair's data scaled by a
@@ -512,6 +539,12 @@ struct RowBasis {
   double tail2;  // ||R[k:, k:]||_F^2 at the stop: the squared norm of the dropped rows
 };
 
+// F32NORM: the trailing column norms in FP32 (hh_apply_norms), for panels
+// tall enough that their per-entry FP64 cost matters; the reflector then sums
+// its own column, the carried norms serving only the pivot choice and the
+// stop (decisions within ~1e-6 of the threshold may move). Otherwise the norms
+// are exact and the reflector takes its column's norm from them.
+template <bool F32NORM = false>
 static __device__ RowBasis pivqr_trunc(cd* A, int lda, int m, int ncol, double delta_rel, int kmax, cd* taus,
                                        double* cn, int* perm, double delta_abs2 = -1.0) {
   // delta_abs2 >= 0 replaces the relative threshold by an absolute one:
@@ -587,7 +620,8 @@ static __device__ RowBasis pivqr_trunc(cd* A, int lda, int m, int ncol, double d
           }
         }
         __syncwarp();
-        const cd tau = hh_reflector_warp(A + (size_t)k * lda, k, m, cn[k]);
+        const cd tau = F32NORM ? hh_reflector_warp(A + (size_t)k * lda, k, m)
+                               : hh_reflector_warp(A + (size_t)k * lda, k, m, cn[k]);
         if (lane == 0) taus[k] = tau;
       }
       if (lane == 0) {
@@ -603,8 +637,8 @@ static __device__ RowBasis pivqr_trunc(cd* A, int lda, int m, int ncol, double d
     }
     const cd tau = taus[k];
     if (tau.x != 0.0 || tau.y != 0.0) {
-      hh_apply_norms(A + (size_t)k * lda, k, m, cconj(tau), A, lda, k + 1, ncol,
-                     [&](int j, cd, double nn) { cn[j] = nn; });
+      hh_apply_norms<F32NORM>(A + (size_t)k * lda, k, m, cconj(tau), A, lda, k + 1, ncol,
+                              [&](int j, cd, double nn) { cn[j] = nn; }, cn);
     } else {
       // H = I: rows below k are unchanged; drop row k from the norms
       for (int j = k + 1 + threadIdx.x; j < ncol; j += blockDim.x) {

@@ -1167,7 +1167,7 @@ __device__ __forceinline__ void zipup_body(const int* list, int count, int* coun
         // carry is CH = Z B = (R[:k] P^T)^H, read from R first; then T's
         // columns k.. are free and the explicit Q = B (the output core) is
         // formed there, behind the reflectors (else in V)
-        const RowBasis rbz = pivqr_trunc(Tp, p, p, q, ztol, SFFT_SLOT_RANK_DEV + 1, sm.tau, zcn, zperm);
+        const RowBasis rbz = pivqr_trunc<true>(Tp, p, p, q, ztol, SFFT_SLOT_RANK_DEV + 1, sm.tau, zcn, zperm);
         int k = rbz.k;
         if (k > SFFT_SLOT_RANK_DEV) {
           st = SFFT_ERANK_DEV;
