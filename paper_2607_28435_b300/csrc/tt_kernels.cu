@@ -1276,11 +1276,12 @@ __global__ void k_readout(const int* list, int count, int* counter, const InstPa
     const long long u_last = lb + ((long long)(q - 1) << tbits[inst]);
     double* pr = prices + out_off[inst];
     double* lk = logk + out_off[inst];
+    const double ls0 = log(prm.S0);
     if (status[inst] != 0 || q <= 0) {
       for (int i = threadIdx.x; i < q; i += blockDim.x) {
         pr[i] = __longlong_as_double(0x7ff8000000000000ULL);
         const long long u = lb + ((long long)i << tbits[inst]);
-        lk[i] = log(prm.S0) + prm.k0 + prm.dk * (double)u;
+        lk[i] = ls0 + prm.k0 + prm.dk * (double)u;
       }
       continue;
     }
@@ -1361,18 +1362,28 @@ __global__ void k_readout(const int* list, int count, int* counter, const InstPa
     // narrow one.
     bool out_of_bounds = false;
     const float s0f = (float)prm.S0, discf = (float)prm.disc, band0 = 1e-6f * s0f;
+    // price = S0 f sgn Re(y_u) with f = e^{-alpha k'} sqrt(M) c (price_factor;
+    // c = 1/pi on the Simpson grid, dv/(2 pi) on the symmetric one). A thread's
+    // strikes are spaced by blockDim 2^t grid points, so after one exponential
+    // each next e^{-alpha k'} is the previous one times a fixed ratio (at most
+    // 16 products: a few ulps)
+    const double sqM = ldexp(1.0, n / 2) * ((n & 1) ? 1.4142135623730951 : 1.0);
+    const double fscale =
+        prm.S0 * sqM * (prm.quad == Q_SIMPSON ? 0.3183098861837907 : prm.dv * 0.15915494309189535);
+    const double ratio = exp(-prm.alpha * prm.dk * (double)((long long)blockDim.x << tbits[inst]));
+    double ea = 0.0;
     for (int i = threadIdx.x; i < q; i += blockDim.x) {
       const long long u = lb + ((long long)i << tbits[inst]);
       const int c = (int)((u >> t) & ((1 << h) - 1));
       const long long pi = (sh < n) ? ((u >> sh) - pbase) : 0;
       cd acc = mkc(0.0, 0.0);
       for (int a = 0; a < rmid; ++a) acc = cfma(Lv[c * SFFT_SLOT_RANK_DEV + a], R0[pi * rmid + a], acc);
-      double sgn;
-      const double f = price_factor(prm, u, &sgn);
-      const double price = prm.S0 * f * sgn * acc.x;
       const double km = prm.k0 + prm.dk * (double)u;
+      ea = (i == (int)threadIdx.x) ? exp(-prm.alpha * km) : ea * ratio;
+      const double sgn = (prm.quad == Q_SIMPSON || !(u & 1)) ? 1.0 : -1.0;
+      const double price = fscale * ea * sgn * acc.x;
       pr[i] = price;
-      lk[i] = log(prm.S0) + km;
+      lk[i] = ls0 + km;
       const float pf = (float)price, kf = (float)km;
       const float lower = fmaxf(s0f * (1.0f - expf(kf) * discf), 0.0f);
       if (!(pf >= lower - band0 && pf <= s0f + band0)) {
