@@ -38,6 +38,8 @@ enum { PH_PROBE = 0, PH_BUILD = 1, PH_ZIPUP = 2, PH_ROUND = 3, PH_READOUT = 4, P
 __global__ void k_sample(const InstParams* P, const long long* j, long long count, cd* x);
 __global__ void k_support_probe(const InstParams* P, int count, double probe_tol, int m_min,
                                 int* m_out);
+// instances by decreasing sum_s r_s^2 of their TT ranks (work order)
+__global__ void k_cost_order(const int* ranks_all, const int* n_arr, int count, int* order);
 __global__ void k_build_lists(const int* m_arr, const int* n_arr, int count, int svd_max_bits,
                               int* svd_list, int* cross_list, int* counts);
 __global__ void k_integrand_ttsvd(const InstParams* P, const int* m_arr, const int* list, int count,

@@ -694,6 +694,18 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   ctx->defer_heads[0] = defer_build;
   ctx->defer_heads[1] = defer_cross;
   ctx->defer_heads[2] = defer_zip;
+  // work orders by decreasing sum_s r_s^2 (k_cost_order): the zip-up's from
+  // the integrand ranks, the rounding's from the zip-up output ranks
+  int *zip_order, *round_order;
+  if ((s = ensure(ctx, "zip_order", sizeof(int) * cnt, &p))) return s;
+  zip_order = reinterpret_cast<int*>(p);
+  if ((s = ensure(ctx, "round_order", sizeof(int) * cnt, &p))) return s;
+  round_order = reinterpret_cast<int*>(p);
+  {
+    PhaseScope ps(ctx, PH_ZIPUP);
+    k_cost_order<<<1, 1024, 0, ctx->stream>>>(b.a_ranks, b.n_arr, cnt, zip_order);
+  }
+  CK(cudaGetLastError());
   const bool mixed = ctx->precision == SFFT_PRECISION_MIXED;
   // tier 1 of the FP64 path: 128-thread CTAs with a 32 x 64 panel block, six
   // per SM; the tensor-core variant keeps 256 threads and a 70 x 64 block
@@ -716,7 +728,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   {
     PhaseScope ps(ctx, PH_ZIPUP);
     (mixed ? k_zipup_tc : k_zipup)<<<zg1, zthreads1, zs1.bytes, ctx->stream>>>(
-        all_dev, cnt, ctr + 3, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
+        zip_order, cnt, ctr + 3, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
         reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
         SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
         SFFT_ZIP_SCRATCH, b.status, zs1.hb, acc_ptr(ctx), zs1.vcap, defer_zip, nullptr, ctx->cur.zip_q,
@@ -732,6 +744,11 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
         SFFT_ZIP_SCRATCH, b.status, zs.hb, acc_ptr(ctx), zs.vcap, nullptr, defer_zip, LA_MAXQ, ctx->cur.zip_w);
   }
   CK(cudaGetLastError());
+  {
+    PhaseScope ps(ctx, PH_ROUND);
+    k_cost_order<<<1, 1024, 0, ctx->stream>>>(b.b_ranks, b.n_arr, cnt, round_order);
+  }
+  CK(cudaGetLastError());
   // tier 1: ranks up to kSmallRoundR in 128-thread CTAs; tier 2: the rest
   const RoundSmem rs1 = round_smem(2, false, std::min(ctx->cur.round_r, kSmallRoundR));
   const RoundSmem rs2 = round_smem(2, false);
@@ -743,7 +760,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   {
     PhaseScope ps(ctx, PH_ROUND);
     k_tt_round<<<grid1, kThreadsSmall, rs1.bytes, ctx->stream>>>(
-        all_dev, cnt, ctr + 4, b.n_arr, 2, 0, b.tol_arr, b.maxr_arr, b.B, b.a_off, SFFT_CORE_STRIDE_D2,
+        round_order, cnt, ctr + 4, b.n_arr, 2, 0, b.tol_arr, b.maxr_arr, b.B, b.a_off, SFFT_CORE_STRIDE_D2,
         b.b_ranks, reinterpret_cast<cd*>(p), SFFT_ROUND_SCRATCH, b.status, rs1.hb, acc_ptr(ctx), PH_ROUND,
         rs1.pmax, rs1.vcap, defer_round, nullptr);
   }
