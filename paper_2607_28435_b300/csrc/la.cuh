@@ -730,16 +730,33 @@ static __device__ void svd_finish(cd* V, int p, int m, cd* W, double* sig) {
   __syncthreads();
 }
 
+// pre2 >= 0 (with perm, p ints of smem) adds pq_svd's prefilter on R: a
+// column-pivoted QR of R drops trailing rows of squared norm <= pre2
+// (returned in tail2, for the caller's truncation to count) and Hestenes'
+// method runs on the k' kept rows only (m = k').
 static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, int wcap, cd* V,
-                        double* sig, cd* taus, int* sh_flag) {
+                        double* sig, cd* taus, int* sh_flag, double pre2 = -1.0, int* perm = nullptr) {
   const int hb = wcap / p - p;
   int ldw;
   const int nR = stream_qr(Z, q, p, ldz, W, wcap, taus, &ldw);
-  const int m = nR;
-  // L = R^H (p x m) into V
-  for (int idx = threadIdx.x; idx < p * m; idx += blockDim.x) {
-    const int c = idx / p, i = idx - c * p;
-    V[(size_t)c * p + i] = (i >= c) ? cconj(W[(size_t)i * ldw + c]) : mkc(0.0, 0.0);
+  int m = nR;
+  double tail2 = 0.0, fpre = 0.0;
+  if (pre2 >= 0.0 && perm) {
+    const RowBasis rb = pivqr_trunc(W, ldw, nR, p, -1.0, nR, taus, sig, perm, pre2);
+    m = rb.k;
+    tail2 = rb.tail2;
+    fpre = rb.flops;
+    // L[perm[j], i] = conj(R2[i, j]) for j >= i (R2 the pivoted QR's rows)
+    for (int idx = threadIdx.x; idx < p * m; idx += blockDim.x) {
+      const int i = idx / p, j = idx - i * p;
+      V[(size_t)i * p + perm[j]] = (j >= i) ? cconj(W[(size_t)j * ldw + i]) : mkc(0.0, 0.0);
+    }
+  } else {
+    // L = R^H (p x m) into V
+    for (int idx = threadIdx.x; idx < p * m; idx += blockDim.x) {
+      const int c = idx / p, i = idx - c * p;
+      V[(size_t)c * p + i] = (i >= c) ? cconj(W[(size_t)i * ldw + c]) : mkc(0.0, 0.0);
+    }
   }
   __syncthreads();
   TsSvd out;
@@ -756,9 +773,9 @@ static __device__ TsSvd ts_svd(const cd* Z, long long q, int p, int ldz, cd* W, 
       carried = carried + b < p ? carried + b : p;
       rows -= b;
     }
-    out.flops = f + flops_hestenes(p, m, out.sweeps < 0 ? cap : out.sweeps) + (double)(4 * p * m);
+    out.flops = f + fpre + flops_hestenes(p, m, out.sweeps < 0 ? cap : out.sweeps) + (double)(4 * p * m);
   }
-  out.tail2 = 0.0;
+  out.tail2 = tail2;
   svd_finish(V, p, m, W, sig);
   return out;
 }

@@ -278,6 +278,8 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, pmax, hb);
   const int wcap = (pmax + hb) * pmax;
+  __shared__ int perm_b[LA_MAXP];
+  __shared__ double red_b[32];
   const int count_ = dcount ? *dcount : count;
   double fl = 0.0, evals = 0.0;
   WORK_LOOP_BEGIN(list, count_, counter)
@@ -299,7 +301,10 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
     cd* O = bufB;
     long long q = Mb >> 1;
     int rprev = 1;
-    double delta = 0.0;
+    // truncation budget per bond from the block's norm; each SVD may first
+    // drop a part of squared norm <= delta^2 / 64 by pivoted QR (ts_svd's
+    // prefilter), counted against the budget
+    const double delta = prm.tol * sqrt(cta_norm2(bufA, Mb, red_b)) / sqrt((double)max(n - 1, 1));
     int site = n - 1;
     bool deferred = false;
     for (int t = 0; t < m; ++t, --site) {
@@ -320,14 +325,9 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
         __syncthreads();
         break;
       }
-      TsSvd sv = ts_svd(Z, q, p, p, sm.W, wcap, sm.V, sm.sig, sm.tau, sm.flag);
+      TsSvd sv = ts_svd(Z, q, p, p, sm.W, wcap, sm.V, sm.sig, sm.tau, sm.flag, delta * delta * (1.0 / 64.0), perm_b);
       if (sv.sweeps < 0) st = SFFT_ENOCONV_DEV;
-      if (t == 0) {
-        double s2 = 0.0;
-        for (int i = 0; i < sv.m; ++i) s2 += sm.sig[i] * sm.sig[i];
-        delta = prm.tol * sqrt(s2) / sqrt((double)max(n - 1, 1));
-      }
-      int k = trunc_rank(sm.sig, sv.m, delta);
+      int k = trunc_rank_tail(sm.sig, sv.m, delta, sv.tail2);
       if (k > rmax) {
         st = SFFT_ERANK_DEV;
         k = rmax;
