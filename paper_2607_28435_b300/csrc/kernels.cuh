@@ -19,6 +19,12 @@
 #define SFFT_ZIP_SUMS_DEV ((SFFT_ZIP_CH_DEV + SFFT_ZIP_D_DEV + SFFT_ZIP_SUM_AW) / 2)
 #define SFFT_ZIP_SCRATCH (SFFT_ZIP_CH_DEV + SFFT_ZIP_D_DEV + SFFT_ZIP_Z_DEV + SFFT_ZIP_SUMS_DEV)
 #define SFFT_ROUND_SCRATCH (5 * SFFT_CORE_STRIDE_D4)
+// zip-up of the delta prefix, one block per cached MPO: the output cores of
+// sites 0..n-1 (stride SFFT_CORE_STRIDE_D2), then the carry after each site
+// (stride SFFT_ZIP_CARRY_STRIDE: MPO rank x carried rank, both <= the slot rank)
+#define SFFT_ZIP_CARRY_STRIDE (SFFT_SLOT_RANK_DEV * SFFT_SLOT_RANK_DEV)
+#define SFFT_ZPRE_CARRY_BASE ((long long)SFFT_MAXN_DEV * SFFT_CORE_STRIDE_D2)
+#define SFFT_ZPRE_BLOCK (SFFT_ZPRE_CARRY_BASE + (long long)SFFT_MAXN_DEV * SFFT_ZIP_CARRY_STRIDE)
 #define READOUT_TREE_BITS 5                   // low bits expanded as a tree in the readout
 #define SFFT_READOUT_SCRATCH (2 * 2112 * SFFT_SLOT_RANK_DEV)
 #define SFFT_MPO_NODES 24                     // Chebyshev nodes of the MPO construction
@@ -46,7 +52,7 @@ __global__ void k_integrand_ttsvd(const InstParams* P, const int* m_arr, const i
                                   int* counter, cd* scratch,
                                   long long scratch_stride, cd* tt, const long long* tt_off,
                                   int core_stride, int* ranks_all, int* status, int hb, double* acc,
-                                  int pmax, int* defer, const int* dcount);
+                                  int pmax, int* defer, const int* dcount, int* zpre_t);
 __global__ void k_integrand_cross(const InstParams* P, const int* list, int count, int* counter,
                                   cd* scratch, long long scratch_stride, cd* tt,
                                   const long long* tt_off, int core_stride, int* ranks_all,
@@ -93,6 +99,18 @@ inline RoundSmem round_smem(int d, bool left_orth = true, int pmax = SFFT_SLOT_R
   r.bytes = sizeof(cd) * ((size_t)(r.pmax + r.hb) * r.pmax + r.vcap + r.pmax) + sizeof(double) * r.pmax + 320;
   return r;
 }
+// The zip-up over sites whose integrand cores are the rank-one delta_{lam,0}
+// (the sites above a TT-SVD block) depends on the MPO alone. It is run once
+// per cached MPO on an all-delta TT (carry_out set: the carry after every
+// site is kept) and then copied into each instance's zip-up, which starts at
+// the first site of its block. All pointers may be null (no prefix).
+struct ZipPrefix {
+  const int* t;           // per instance: sites taken from the prefix (0: none)
+  const long long* off;   // per instance: offset of its MPO's prefix block (< 0: none)
+  const int* ranks;       // per instance, SFFT_MAXN_DEV + 1 each: the prefix's output ranks
+  const cd* pool;         // prefix blocks (SFFT_ZPRE_BLOCK complex each)
+  cd* carry_out;          // precompute: the pool, whose carries the launch writes
+};
 __global__ void k_zipup(const int* list, int count, int* counter, const int* n_arr,
                         const double* tol_arr, const int* maxrank_arr,
                         const cd* A, const long long* a_off, const int* a_ranks_all,
@@ -100,7 +118,7 @@ __global__ void k_zipup(const int* list, int count, int* counter, const int* n_a
                         const long long* b_off, int* b_ranks_all, int core_stride_a,
                         int core_stride_w, int core_stride_b, cd* scratch,
                         long long scratch_stride, int* status, int hb, double* acc, int vcap, int* defer,
-                        const int* dcount, int qmax1, int wlim);
+                        const int* dcount, int qmax1, int wlim, ZipPrefix zp);
 // The same with the MPO contraction of each site on the tensor cores (tcgen05,
 // FP32 operands as three bfloat16 pieces, FP32 accumulation) wherever one
 // 128-row tile holds it; the QR steps stay FP64.
@@ -111,7 +129,7 @@ __global__ void k_zipup_tc(const int* list, int count, int* counter, const int* 
                            const long long* b_off, int* b_ranks_all, int core_stride_a,
                            int core_stride_w, int core_stride_b, cd* scratch,
                            long long scratch_stride, int* status, int hb, double* acc, int vcap, int* defer,
-                           const int* dcount, int qmax1, int wlim);
+                           const int* dcount, int qmax1, int wlim, ZipPrefix zp);
 // Jacobi sweep limit of the SVDs in the TT kernels (test hook; default 60),
 // enqueued on `stream`. The value is taken from pageable host memory before
 // the call returns; not for use while the stream is being captured.

@@ -57,6 +57,10 @@ struct MpoEntry {
   double tol;
   long long off;  // complex offset in the MPO pool
   std::vector<int> ranks;
+  // zip-up of the delta prefix (k_zipup on an all-delta TT): block offset in
+  // the prefix pool (-1: not available) and its output ranks
+  long long zoff = -1;
+  std::vector<int> zranks;
 };
 
 }  // namespace
@@ -73,6 +77,8 @@ struct sfft_ctx {
   DevBuf mpo_pool;
   DevBuf mpo_ranks_dev;  // (SFFT_MAX_N+1) per cached MPO
   int mpo_slots = 0;
+  DevBuf zpre_pool;       // SFFT_ZPRE_BLOCK complex per MPO slot
+  DevBuf zpre_ranks_dev;  // (SFFT_MAX_N+1) per MPO slot
   std::deque<MpoEntry> mpos;  // stable addresses across push_back
   // batch workspaces (grow only)
   std::map<std::string, DevBuf> bufs;
@@ -94,6 +100,7 @@ struct sfft_ctx {
     int zip_ctas = 0;    // zip-up: CTAs per SM (0: as many as fit)
   } t1;
   bool t1_hooked = false;  // SFFT_TIER1 set: its limits win over any tuning
+  bool zpre_on = true;     // zip-up of the delta prefix taken from the MPO cache
   // tuned first-tier configurations by batch signature (sfft_autotune), the
   // one in force for the current call, and a forced one while tuning
   std::map<std::string, Tier1> tune;
@@ -411,12 +418,29 @@ sfft_status build_mpos(sfft_ctx* ctx, const std::vector<std::pair<int, double>>&
                          cudaMemcpyDeviceToDevice, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));
     }
+    void* zp = nullptr;
+    void* zr = nullptr;
+    CK(cudaMalloc(&zp, sizeof(cd) * SFFT_ZPRE_BLOCK * nslots));
+    CK(cudaMalloc(&zr, sizeof(int) * (SFFT_MAX_N + 1) * nslots));
+    if (ctx->mpo_slots) {
+      CK(cudaMemcpyAsync(zp, ctx->zpre_pool.p, sizeof(cd) * SFFT_ZPRE_BLOCK * ctx->mpo_slots,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(zr, ctx->zpre_ranks_dev.p, sizeof(int) * (SFFT_MAX_N + 1) * ctx->mpo_slots,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
     ctx->mpo_pool.release();
     ctx->mpo_ranks_dev.release();
+    ctx->zpre_pool.release();
+    ctx->zpre_ranks_dev.release();
     ctx->mpo_pool.p = np;
     ctx->mpo_pool.bytes = sizeof(cd) * slot * nslots;
     ctx->mpo_ranks_dev.p = nr;
     ctx->mpo_ranks_dev.bytes = sizeof(int) * (SFFT_MAX_N + 1) * nslots;
+    ctx->zpre_pool.p = zp;
+    ctx->zpre_pool.bytes = sizeof(cd) * SFFT_ZPRE_BLOCK * nslots;
+    ctx->zpre_ranks_dev.p = zr;
+    ctx->zpre_ranks_dev.bytes = sizeof(int) * (SFFT_MAX_N + 1) * nslots;
     ctx->mpo_slots = nslots;
   }
   cd* pool = reinterpret_cast<cd*>(ctx->mpo_pool.p);
@@ -462,21 +486,68 @@ sfft_status build_mpos(sfft_ctx* ctx, const std::vector<std::pair<int, double>>&
         rs.vcap, nullptr, nullptr);
   }
   CK(cudaGetLastError());
-  std::vector<int> rr((size_t)(SFFT_MAX_N + 1) * nm);
-  CK(cudaMemcpyAsync(rr.data(), rk + (size_t)(SFFT_MAX_N + 1) * first, sizeof(int) * rr.size(),
-                     cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  for (int k = 0; k < nm; ++k) {
-    MpoEntry e;
-    e.idx = first + k;
-    e.n = miss[k].first;
-    e.tol = miss[k].second;
-    e.off = off_v[e.idx];
-    e.ranks.assign(rr.begin() + (size_t)(SFFT_MAX_N + 1) * k, rr.begin() + (size_t)(SFFT_MAX_N + 1) * (k + 1));
-    for (int i = 0; i <= e.n; ++i)
-      if (e.ranks[i] < 1 || e.ranks[i] > SFFT_SLOT_RANK_DEV)
-        return set_err(ctx, SFFT_ERANK, "MPO rank %d at bond %d", e.ranks[i], i);
-    ctx->mpos.push_back(e);
+  // the zip-up of each new MPO with the all-delta TT (ranks 1, cores (1, 0)):
+  // the prefix of every TT-SVD instance's zip-up, with the carry after each
+  // site; full carve, one CTA per MPO, no profiling counters
+  cd* zpool = reinterpret_cast<cd*>(ctx->zpre_pool.p);
+  int* zrk = reinterpret_cast<int*>(ctx->zpre_ranks_dev.p);
+  {
+    std::vector<cd> delta((size_t)2 * SFFT_MAX_N);
+    for (int i = 0; i < SFFT_MAX_N; ++i) {
+      delta[2 * i] = make_double2(1.0, 0.0);
+      delta[2 * i + 1] = make_double2(0.0, 0.0);
+    }
+    std::vector<long long> zero_off(tot, 0), zoff_v(tot);
+    for (int i = 0; i < tot; ++i) zoff_v[i] = SFFT_ZPRE_BLOCK * i;
+    std::vector<int> ones((size_t)(SFFT_MAX_N + 1) * tot, 1), zst(tot, 0);
+    cd* delta_d;
+    long long *zero_d, *zoff_d;
+    int *ones_d, *zst_d;
+    if ((s = upload(ctx, "zpre_delta", delta, &delta_d)) || (s = upload(ctx, "zpre_zero", zero_off, &zero_d)) ||
+        (s = upload(ctx, "zpre_off", zoff_v, &zoff_d)) || (s = upload(ctx, "zpre_ones", ones, &ones_d)) ||
+        (s = upload(ctx, "zpre_status", zst, &zst_d)))
+      return s;
+    const RoundSmem zs = zip_smem();
+    const int zg = std::min(nm, ctx->num_sms * blocks_per_sm((const void*)k_zipup, zs.bytes));
+    if ((s = ensure(ctx, "zpre_scratch", sizeof(cd) * (size_t)SFFT_ZIP_SCRATCH * zg, &p))) return s;
+    cd* zscr = reinterpret_cast<cd*>(p);
+    if ((s = ensure(ctx, "zpre_counter", sizeof(int), &p))) return s;
+    int* zctr = reinterpret_cast<int*>(p);
+    CK(cudaMemsetAsync(zctr, 0, sizeof(int), ctx->stream));
+    ZipPrefix zp{nullptr, zoff_d, nullptr, nullptr, zpool};
+    {
+      PhaseScope ps(ctx, PH_MPO);
+      k_zipup<<<zg, kThreads, zs.bytes, ctx->stream>>>(
+          list_d, nm, zctr, n_d, tol_d, maxr_d, delta_d, zero_d, ones_d, pool, off_d, rk, zpool, zoff_d, zrk,
+          2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, zscr, SFFT_ZIP_SCRATCH, zst_d, zs.hb, nullptr, zs.vcap,
+          nullptr, nullptr, LA_MAXQ, 1 << 30, zp);
+    }
+    CK(cudaGetLastError());
+    std::vector<int> zr_h((size_t)(SFFT_MAX_N + 1) * nm), zst_h(nm);
+    CK(cudaMemcpyAsync(zr_h.data(), zrk + (size_t)(SFFT_MAX_N + 1) * first, sizeof(int) * zr_h.size(),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(zst_h.data(), zst_d + first, sizeof(int) * nm, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<int> rr((size_t)(SFFT_MAX_N + 1) * nm);
+    CK(cudaMemcpyAsync(rr.data(), rk + (size_t)(SFFT_MAX_N + 1) * first, sizeof(int) * rr.size(),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < nm; ++k) {
+      MpoEntry e;
+      e.idx = first + k;
+      e.n = miss[k].first;
+      e.tol = miss[k].second;
+      e.off = off_v[e.idx];
+      e.ranks.assign(rr.begin() + (size_t)(SFFT_MAX_N + 1) * k, rr.begin() + (size_t)(SFFT_MAX_N + 1) * (k + 1));
+      for (int i = 0; i <= e.n; ++i)
+        if (e.ranks[i] < 1 || e.ranks[i] > SFFT_SLOT_RANK_DEV)
+          return set_err(ctx, SFFT_ERANK, "MPO rank %d at bond %d", e.ranks[i], i);
+      if (zst_h[k] == 0) {
+        e.zoff = zoff_v[e.idx];
+        e.zranks.assign(zr_h.begin() + (size_t)(SFFT_MAX_N + 1) * k,
+                        zr_h.begin() + (size_t)(SFFT_MAX_N + 1) * (k + 1));
+      }
+      ctx->mpos.push_back(e);
+    }
   }
   return SFFT_OK;
 }
@@ -484,6 +555,7 @@ sfft_status build_mpos(sfft_ctx* ctx, const std::vector<std::pair<int, double>>&
 // Device-side state of one batch of valid instances through the TT path.
 struct Batch {
   int count = 0;
+  std::vector<int> n_host;  // grid exponent of each valid instance
   InstParams* P = nullptr;
   int* n_arr = nullptr;
   double* tol_arr = nullptr;
@@ -496,6 +568,9 @@ struct Batch {
   int* b_ranks = nullptr;
   long long* w_off = nullptr;
   int* w_ranks = nullptr;
+  int* zpre_t = nullptr;          // delta sites above each instance's TT-SVD block
+  long long* zpre_off = nullptr;  // its MPO's prefix block (-1: none)
+  int* zpre_ranks = nullptr;      // that prefix's ranks, per instance
   std::vector<int> mpo_max;
   int* all_list = nullptr;  // instances, largest n first
   int* counters = nullptr;  // work-queue counters of the launches
@@ -509,6 +584,8 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   b.count = cnt;
   sfft_status s;
   std::vector<int> n_arr(cnt), maxr(cnt);
+  b.n_host.resize(cnt);
+  for (int i = 0; i < cnt; ++i) b.n_host[i] = prm[i].n;
   std::vector<double> tol(cnt);
   std::vector<long long> off(cnt);
   long long tot = 0;
@@ -588,6 +665,12 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   defer_cross = reinterpret_cast<int*>(p);
   CK(cudaMemsetAsync(defer_build, 0, sizeof(int), ctx->stream));
   CK(cudaMemsetAsync(defer_round, 0, sizeof(int), ctx->stream));
+  // delta sites above each TT-SVD block (0 for the cross builder's instances)
+  int* zpre_t;
+  if ((s = ensure(ctx, "zpre_t", sizeof(int) * cnt, &p))) return s;
+  zpre_t = reinterpret_cast<int*>(p);
+  CK(cudaMemsetAsync(zpre_t, 0, sizeof(int) * cnt, ctx->stream));
+  b.zpre_t = zpre_t;
   CK(cudaMemsetAsync(defer_cross, 0, sizeof(int), ctx->stream));
   // TT-SVD builder: tier 1 panels up to kSmallP columns in 128-thread CTAs,
   // several per SM; tier 2 the full carve for the instances tier 1 handed on
@@ -651,13 +734,13 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     PhaseScope ps(ctx, PH_BUILD);
     k_integrand_ttsvd<<<bgrid1, kThreadsSmall, bsmem1, ctx->stream>>>(
         b.P, m_dev, svd_dev, cnt, ctr + 0, build_scratch, sstride, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
-        b.a_ranks, b.status, build_p1, acc_ptr(ctx), build_p1, defer_build, list_counts);
+        b.a_ranks, b.status, build_p1, acc_ptr(ctx), build_p1, defer_build, list_counts, zpre_t);
   }
   {
     PhaseScope ps(ctx, PH_BUILD);
     k_integrand_ttsvd<<<bgrid2, kThreads, smem, ctx->stream>>>(
         b.P, m_dev, defer_build + 1, 0, ctr + 7, build_scratch, sstride, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
-        b.a_ranks, b.status, kHb, acc_ptr(ctx), LA_MAXP, nullptr, defer_build);
+        b.a_ranks, b.status, kHb, acc_ptr(ctx), LA_MAXP, nullptr, defer_build, zpre_t);
   }
   const cudaError_t side_err = cudaGetLastError();
   ctx->stream = main_stream;
@@ -685,6 +768,19 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
   }
   if ((s = upload(ctx, "w_off", w_off, &b.w_off))) return s;
   if ((s = h2d(ctx, b.w_ranks, w_ranks.data(), sizeof(int) * w_ranks.size()))) return s;
+  // the zip-up of each MPO's delta prefix, taken by the TT-SVD instances
+  std::vector<long long> z_off(cnt);
+  std::vector<int> z_ranks((size_t)cnt * (SFFT_MAX_N + 1), 1);
+  for (int i = 0; i < cnt; ++i) {
+    const MpoEntry* e = (*mpos_in)[i];
+    z_off[i] = e->zoff;
+    if (e->zoff >= 0) std::copy(e->zranks.begin(), e->zranks.end(), z_ranks.begin() + (size_t)i * (SFFT_MAX_N + 1));
+  }
+  if ((s = upload(ctx, "zpre_off_b", z_off, &b.zpre_off))) return s;
+  if ((s = upload(ctx, "zpre_ranks_b", z_ranks, &b.zpre_ranks))) return s;
+  const ZipPrefix zpre = ctx->zpre_on ? ZipPrefix{b.zpre_t, b.zpre_off, b.zpre_ranks,
+                                                  reinterpret_cast<const cd*>(ctx->zpre_pool.p), nullptr}
+                                      : ZipPrefix{};
   // tier 1: W-only carve, three CTAs per SM; tier 2: the full carve for the
   // instances whose panels (with their explicit Q) outgrow it
   int* defer_zip;
@@ -732,7 +828,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
         reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
         SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
         SFFT_ZIP_SCRATCH, b.status, zs1.hb, acc_ptr(ctx), zs1.vcap, defer_zip, nullptr, ctx->cur.zip_q,
-        ctx->cur.zip_w);
+        ctx->cur.zip_w, zpre);
   }
   CK(cudaGetLastError());
   {
@@ -741,7 +837,8 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
         defer_zip + 1, 0, ctr + 9, b.n_arr, b.tol_arr, b.maxr_arr, b.A, b.a_off, b.a_ranks,
         reinterpret_cast<const cd*>(ctx->mpo_pool.p), b.w_off, b.w_ranks, b.B, b.a_off, b.b_ranks,
         SFFT_CORE_STRIDE_D2, SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(p),
-        SFFT_ZIP_SCRATCH, b.status, zs.hb, acc_ptr(ctx), zs.vcap, nullptr, defer_zip, LA_MAXQ, ctx->cur.zip_w);
+        SFFT_ZIP_SCRATCH, b.status, zs.hb, acc_ptr(ctx), zs.vcap, nullptr, defer_zip, LA_MAXQ, ctx->cur.zip_w,
+        zpre);
   }
   CK(cudaGetLastError());
   {
@@ -850,10 +947,13 @@ sfft_status finish_status(sfft_ctx* ctx, int count, const std::vector<int>& vali
   if (info && b) {
     for (size_t k = 0; k < valid_idx.size(); ++k) {
       const int i = valid_idx[k];
+      // the kernels write bonds 0..n of each instance's rank row; the rest of
+      // the row is not theirs
       const int* a = ar.data() + k * (SFFT_MAX_N + 1);
       const int* c = br.data() + k * (SFFT_MAX_N + 1);
-      info[i].int_rank = *std::max_element(a, a + SFFT_MAX_N + 1);
-      info[i].out_rank = *std::max_element(c, c + SFFT_MAX_N + 1);
+      const int nb = (k < b->n_host.size() ? b->n_host[k] : SFFT_MAX_N) + 1;
+      info[i].int_rank = *std::max_element(a, a + nb);
+      info[i].out_rank = *std::max_element(c, c + nb);
       if (mpos && (*mpos)[k]) {
         const auto& rr = (*mpos)[k]->ranks;
         info[i].mpo_rank = *std::max_element(rr.begin(), rr.end());
@@ -927,7 +1027,10 @@ void choose_tier1(sfft_ctx* ctx, const sfft_problem* probs, int count) {
 //   SFFT_FAULT="enoconv:<position>"  the builder result of that position among
 //     a call's valid instances is replaced by SFFT_ENOCONV
 // Several SFFT_FAULT items are separated by ';'.
+//   SFFT_ZPRE=0  every instance's zip-up runs from site 0 instead of taking its
+//     delta prefix from the MPO cache (tests compare the two)
 void read_test_hooks(sfft_ctx* ctx) {
+  if (const char* z = getenv("SFFT_ZPRE")) ctx->zpre_on = atoi(z) != 0;
   if (const char* t = getenv("SFFT_TIER1")) {
     ctx->t1_hooked = true;
     std::string str(t);
@@ -1392,7 +1495,7 @@ sfft_status sfft_tt_apply_qft(sfft_ctx* ctx, int32_t n, const int32_t* in_ranks,
       nullptr, 1, nullptr, nd, td, md, A, od, reinterpret_cast<int*>(ra), reinterpret_cast<const cd*>(ctx->mpo_pool.p), wd,
       reinterpret_cast<int*>(rw), B, od, reinterpret_cast<int*>(rb), SFFT_CORE_STRIDE_D2,
       SFFT_CORE_STRIDE_D4, SFFT_CORE_STRIDE_D2, reinterpret_cast<cd*>(scr), SFFT_ZIP_SCRATCH, sd, zs.hb,
-      nullptr, zs.vcap, nullptr, nullptr, LA_MAXQ, 1 << 30);
+      nullptr, zs.vcap, nullptr, nullptr, LA_MAXQ, 1 << 30, ZipPrefix{});
   CK(cudaGetLastError());
   const RoundSmem rs = round_smem(2, false);
   k_tt_round<<<1, kThreads, rs.bytes, ctx->stream>>>(nullptr, 1, nullptr, nd, 2, 0, td, md, B, od,

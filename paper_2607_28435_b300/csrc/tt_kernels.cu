@@ -272,9 +272,10 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
                                   cd* tt, const long long* tt_off,
                                   int core_stride, int* ranks_all,
                                   int* status, int hb, double* acc, int pmax, int* defer,
-                                  const int* dcount) {
+                                  const int* dcount, int* zpre_t) {
   // panels of at most pmax columns (carve sized by the launch); with defer
-  // set, instances that need wider panels go to the full-size launch
+  // set, instances that need wider panels go to the full-size launch.
+  // zpre_t (may be null) receives the number of delta sites above the block.
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, pmax, hb);
   const int wcap = (pmax + hb) * pmax;
@@ -364,6 +365,7 @@ __global__ void k_integrand_ttsvd(const InstParams* __restrict__ P, const int* m
       ranks[0] = 1;
       ranks[n] = 1;
       status[inst] = st;
+      if (zpre_t) zpre_t[inst] = n - m;
     }
     __syncthreads();
   WORK_LOOP_END
@@ -1037,7 +1039,7 @@ __device__ __forceinline__ void zipup_body(const int* list, int count, int* coun
                         int core_stride_a, int core_stride_w, int core_stride_b,
                         cd* scratch, long long scratch_stride,
                         int* status, int hb, double* acc, int vcap, int* defer, const int* dcount,
-                        int qmax1, int wlim) {
+                        int qmax1, int wlim, ZipPrefix zp) {
   // shared memory: W ((LA_MAXP + hb) x LA_MAXP) for the panel T and, in its
   // spent columns, the explicit Q; V (vcap elements) for the streaming
   // fallback of panels larger than W. A launch without V (vcap <= 1) hands
@@ -1104,8 +1106,29 @@ __device__ __forceinline__ void zipup_body(const int* list, int count, int* coun
     }
     __syncthreads();
     int rc = 1;
+    int s_begin = 0;
+    if (zp.t && zp.t[inst] > 0 && zp.off[inst] >= 0) {
+      // sites 0..t-1 carry the integrand's delta cores: their output cores
+      // and the carry after site t-1 come from the MPO's prefix block
+      const int t = zp.t[inst];
+      const cd* blk = zp.pool + zp.off[inst];
+      const int* pr = zp.ranks + (size_t)inst * (SFFT_MAXN_DEV + 1);
+      for (int s = 0; s < t; ++s) {
+        const int len = pr[s] * 2 * pr[s + 1];
+        const cd* src = blk + (size_t)s * SFFT_CORE_STRIDE_D2;
+        cd* dst = Bb + (size_t)s * core_stride_b;
+        for (int idx = threadIdx.x; idx < len; idx += blockDim.x) __stcs(dst + idx, src[idx]);
+      }
+      rc = pr[t];
+      const cd* csrc = blk + SFFT_ZPRE_CARRY_BASE + (size_t)(t - 1) * SFFT_ZIP_CARRY_STRIDE;
+      for (int idx = threadIdx.x; idx < rw[t] * rc; idx += blockDim.x) CH[idx] = csrc[idx];
+      if (threadIdx.x == 0)
+        for (int s = 1; s <= t; ++s) rb[s] = pr[s];
+      s_begin = t;
+      __syncthreads();
+    }
     bool deferred = false;
-    for (int s = 0; s < n; ++s) {
+    for (int s = s_begin; s < n; ++s) {
       const int rA0 = ra[s], rA1 = ra[s + 1], s0 = rw[s], s1 = rw[s + 1];
       {
         // a launch without V handles panels of up to LA_MAXQ columns (in W,
@@ -1228,6 +1251,9 @@ __device__ __forceinline__ void zipup_body(const int* list, int count, int* coun
         }
         if (threadIdx.x == 0) rb[s + 1] = k;
         __syncthreads();
+        if (zp.carry_out)
+          for (int idx = threadIdx.x; idx < q * k; idx += blockDim.x)
+            zp.carry_out[zp.off[inst] + SFFT_ZPRE_CARRY_BASE + (size_t)s * SFFT_ZIP_CARRY_STRIDE + idx] = CH[idx];
         fl += rbz.flops + flops_formq(p, k);
         rc = k;
         continue;
@@ -1250,6 +1276,9 @@ __device__ __forceinline__ void zipup_body(const int* list, int count, int* coun
       gemm_zv(Z, q, p, sm.W, k, CH);
       if (threadIdx.x == 0) rb[s + 1] = k;
       __syncthreads();
+      if (zp.carry_out)
+        for (int idx = threadIdx.x; idx < q * k; idx += blockDim.x)
+          zp.carry_out[zp.off[inst] + SFFT_ZPRE_CARRY_BASE + (size_t)s * SFFT_ZIP_CARRY_STRIDE + idx] = CH[idx];
       fl += rbz.flops + flops_gemm(q, p, k);
       rc = k;
     }
@@ -1277,11 +1306,11 @@ __device__ __forceinline__ void zipup_body(const int* list, int count, int* coun
       const cd *Wmpo, const long long *w_off, const int *w_ranks_all, cd *B, const long long *b_off, \
       int *b_ranks_all, int core_stride_a, int core_stride_w, int core_stride_b, cd *scratch,        \
       long long scratch_stride, int *status, int hb, double *acc, int vcap, int *defer,              \
-      const int *dcount, int qmax1, int wlim
+      const int *dcount, int qmax1, int wlim, ZipPrefix zp
 #define ZIPUP_ARGS                                                                                  \
   list, count, counter, n_arr, tol_arr, maxrank_arr, A, a_off, a_ranks_all, Wmpo, w_off, w_ranks_all, \
       B, b_off, b_ranks_all, core_stride_a, core_stride_w, core_stride_b, scratch, scratch_stride,    \
-      status, hb, acc, vcap, defer, dcount, qmax1, wlim
+      status, hb, acc, vcap, defer, dcount, qmax1, wlim, zp
 
 __global__ void __launch_bounds__(256, 3) k_zipup(ZIPUP_PARAMS) { zipup_body<false>(ZIPUP_ARGS); }
 __global__ void __launch_bounds__(256, 3) k_zipup_tc(ZIPUP_PARAMS) { zipup_body<true>(ZIPUP_ARGS); }

@@ -67,8 +67,12 @@ def test_config4_instances_against_the_oracle_and_the_fp64_path(pricers):
     ok = [i for i, s in enumerate(sm) if s == 0]
     assert len(ok) >= 55
     # the contraction ran on the tensor cores: sites were counted, and the
-    # prices differ from the FP64 path's in their last digits
-    assert prof["zipup"]["evals"] >= 30 * len(ok)
+    # prices differ from the FP64 path's in their last digits. The sites
+    # above a TT-SVD block (delta cores) come from the MPO's cached prefix,
+    # which is the same for every instance and computed once in FP64; each
+    # instance contracts its block's sites (support 2^6..2^14) on the tensor
+    # cores
+    assert prof["zipup"]["evals"] >= 5 * len(ok)
     a, b = cm_.cpu().numpy(), c64.cpu().numpy()
     offs = np.concatenate([[0], np.cumsum([q for _, _, q in strikes])])
     dev = np.array([np.max(np.abs(a[offs[i]:offs[i + 1]] - b[offs[i]:offs[i + 1]])) / probs[i].S0 for i in ok])
