@@ -57,14 +57,16 @@ __global__ void k_integrand_cross(const InstParams* P, const int* list, int coun
                                   cd* scratch, long long scratch_stride, cd* tt,
                                   const long long* tt_off, int core_stride, int* ranks_all,
                                   int* status, int hb, double* acc, int max_sweeps, int pmax,
-                                  int rcap, int* defer, const int* dcount);
+                                  int rcap, int* defer, const int* dcount, const int* m_arr,
+                                  int* zpre_t);
 __global__ void k_mpo_interp(int n, int P, cd* W, int core_stride, int* ranks);
 __global__ void k_tt_round(const int* list, int count, int* counter, const int* n_arr, int d,
                            int left_orth, const double* tol_arr,
                            const int* maxrank_arr, cd* tt, const long long* tt_off,
                            int core_stride, int* ranks_all, cd* scratch,
                            long long scratch_stride, int* status, int hb, double* acc, int phase,
-                           int pmax, int vcap, int* defer, const int* dcount);
+                           int pmax, int vcap, int* defer, const int* dcount,
+                           const int* site0_arr = nullptr);
 
 // Shared memory of k_tt_round for physical dimension d: panels of at most
 // SFFT_SLOT_RANK_DEV columns; W holds a (d r) x r block, V the explicit Q.

@@ -711,13 +711,14 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     k_integrand_cross<<<xgrid1, kThreadsSmall, xsmem1, ctx->stream>>>(
         b.P, cross_dev, cnt, ctr + 1, cross_scratch, 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2, b.a_ranks,
         b.status, xhb, acc_ptr(ctx), kCrossSweeps, xp, std::min(ctx->cur.cross_r, kCrossSmallR), defer_cross,
-        list_counts + 1);
+        list_counts + 1, m_dev, zpre_t);
   }
   {
     PhaseScope ps(ctx, PH_CROSS);
     k_integrand_cross<<<xgrid, kThreads, smem, ctx->stream>>>(
         b.P, defer_cross + 1, 0, ctr + 10, cross_scratch, 4096, b.A, b.a_off, SFFT_CORE_STRIDE_D2, b.a_ranks,
-        b.status, kHb, acc_ptr(ctx), kCrossSweeps, LA_MAXP, CROSS_RANK_CAP, nullptr, defer_cross);
+        b.status, kHb, acc_ptr(ctx), kCrossSweeps, LA_MAXP, CROSS_RANK_CAP, nullptr, defer_cross, m_dev,
+        zpre_t);
   }
   {
     // interpolatory cores -> right-orthonormal, truncated to tol
@@ -725,7 +726,7 @@ sfft_status run_tt_path(sfft_ctx* ctx, const std::vector<InstParams>& prm, Batch
     k_tt_round<<<xgrid_r, kThreads, xrs.bytes, ctx->stream>>>(
         cross_dev, cnt, ctr + 2, b.n_arr, 2, 1, b.tol_arr, b.maxr_arr, b.A, b.a_off, SFFT_CORE_STRIDE_D2,
         b.a_ranks, xround_scratch, SFFT_ROUND_SCRATCH, b.status, xrs.hb, acc_ptr(ctx), PH_CROSS, xrs.pmax,
-        xrs.vcap, nullptr, list_counts + 1);
+        xrs.vcap, nullptr, list_counts + 1, zpre_t);
   }
   const cudaError_t main_err = cudaGetLastError();
   cudaStream_t main_stream = ctx->stream;

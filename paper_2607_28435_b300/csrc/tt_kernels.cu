@@ -445,10 +445,13 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
                                   int* counter, cd* scratch, long long scratch_stride, cd* tt,
                                   const long long* tt_off, int core_stride, int* ranks_all,
                                   int* status, int hb, double* acc, int max_sweeps, int pmax,
-                                  int rcap, int* defer, const int* dcount) {
+                                  int rcap, int* defer, const int* dcount, const int* m_arr,
+                                  int* zpre_t) {
   // panels of at most pmax columns (carve sized by the launch); with defer
   // set, ranks are capped at rcap and an instance that needs more goes to the
-  // full-size launch before anything of it is written
+  // full-size launch before anything of it is written. m_arr (may be null):
+  // the support probe's block exponents; zpre_t (may be null) receives the
+  // number of delta sites above the block.
   extern __shared__ double4 smem_raw[];
   SvdSmem sm = carve_svd_smem(smem_raw, pmax, hb);
   __shared__ long long Iset[(SFFT_MAXN_DEV + 1) * CROSS_R];
@@ -464,14 +467,20 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
   const int count_ = dcount ? *dcount : count;
   WORK_LOOP_BEGIN(list, count_, counter)
     const InstParams prm = P[inst];
-    const int n = prm.n;
+    // the cross runs on the block of the m least significant bits (the
+    // support probe's); the n - m sites above it hold the rank-one
+    // delta_{lam,0}, as the TT-SVD builder leaves them. Below, n is the
+    // block's number of sites and j < 2^n the grid index.
+    const int n_full = prm.n;
+    const int n = m_arr ? min(max(m_arr[inst], 1), n_full) : n_full;
+    const int site0 = n_full - n;
     const int rmax_i = min(prm.max_rank, CROSS_R);
     const int rmax = defer ? min(rmax_i, rcap) : rmax_i;
     bool hand_off = false;
     const double ctol = 0.01 * prm.tol;
     int st = 0;
-    cd* base = tt + tt_off[inst];
-    int* rg = ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
+    cd* base = tt + tt_off[inst] + (size_t)site0 * core_stride;
+    int* rg = ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1) + site0;
     // initial right sets (seeds) and ranks
     for (int b = threadIdx.x; b <= n; b += blockDim.x) {
       const int L = n - b;
@@ -598,10 +607,17 @@ __global__ void k_integrand_cross(const InstParams* __restrict__ P, const int* l
       fl += flops_qr(N, rr) + flops_formq(N, kq);
     }
     for (int b = threadIdx.x; b <= n; b += blockDim.x) rg[b] = rk[b];
+    for (int s = threadIdx.x; s < site0; s += blockDim.x) {
+      cd* G = core_ptr(tt + tt_off[inst], core_stride, s);
+      G[0] = mkc(1.0, 0.0);
+      G[1] = mkc(0.0, 0.0);
+      rg[s - site0] = 1;
+    }
     if (threadIdx.x == 0) {
       rg[0] = 1;
       rg[n] = 1;
       status[inst] = max(status[inst], st);
+      if (zpre_t) zpre_t[inst] = site0;
     }
     __syncthreads();
   WORK_LOOP_END
@@ -702,7 +718,9 @@ __global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count,
                            int* ranks_all, cd* scratch,
                            long long scratch_stride, int* status, int hb,
                            double* acc, int phase, int pmax, int vcap, int* defer,
-                           const int* dcount) {
+                           const int* dcount, const int* site0_arr) {
+  // site0_arr (may be null): per instance, the first site rounded; the sites
+  // above it (rank-one delta cores) are left as they are
   // shared memory sized by the launch: panels of at most pmax columns, Q
   // blocks of vcap elements (see round_smem_bytes on the host)
   extern __shared__ double4 smem_raw[];
@@ -715,14 +733,17 @@ __global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count,
   const int count_ = dcount ? *dcount : count;
   double fl = 0.0;
   WORK_LOOP_BEGIN(list, count_, counter)
-    const int n = n_arr[inst];
+    // n: the sites rounded; the bond budget below counts every bond of the TT
+    const int n_full = n_arr[inst];
+    const int site0 = site0_arr ? min(max(site0_arr[inst], 0), n_full - 1) : 0;
+    const int n = n_full - site0;
     const double tol = tol_arr[inst];
     const int rmax = maxrank_arr[inst];
-    int* rg = ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1);
+    int* rg = ranks_all + (size_t)inst * (SFFT_MAXN_DEV + 1) + site0;
     __syncthreads();
     for (int i = threadIdx.x; i <= n; i += blockDim.x) r[i] = rg[i];
     __syncthreads();
-    cd* base = tt + tt_off[inst];
+    cd* base = tt + tt_off[inst] + (size_t)site0 * core_stride;
     cd* tmp = scratch + (size_t)blockIdx.x * scratch_stride;
     int st = 0;
     if (status && status[inst] != 0) continue;
@@ -773,7 +794,7 @@ __global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count,
     {
       cd* G = core_ptr(base, core_stride, n - 1);
       const double nn = cta_norm2(G, (long long)r[n - 1] * d * r[n], red);
-      const double delta = tol * sqrt(nn) / sqrt((double)max(n - 1, 1));
+      const double delta = tol * sqrt(nn) / sqrt((double)max(n_full - 1, 1));
       for (int s = n - 1; s >= 1; --s) {
         const int r0 = r[s], r1 = r[s + 1], rm = r[s - 1];
         cd* Gs = core_ptr(base, core_stride, s);
