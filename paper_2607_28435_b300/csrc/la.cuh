@@ -321,14 +321,16 @@ __device__ __forceinline__ int jacobi_group_log2(int npair, int p) {
   return best;
 }
 
-// F32ROT: the rotation parameters in FP32 from the pair's data scaled by a
-// power of two (integer bit operations: no FP64 instruction), the rotation
-// applied in FP64. c and s then carry FP32 rounding, so each rotation is
-// unitary to ~1e-7 and leaves ~1e-7 of the coupling: the column norms (the
-// singular values) are accurate to ~1e-6 relative, and the columns span the
-// dominant subspaces to within ~1e-7 of the dropped singular values. Only a
-// caller that projects onto the subspace exactly (pq_svd in the rounding)
-// uses it; the FP64 form keeps the exact-unitarity guarantee for the rest.
+// F32ROT: the pair's dot product a^H b, the rotation tests and the rotation
+// parameters in FP32, on the pair's data scaled by a power of two (integer
+// bit operations: no FP64 instruction); only the rotation itself and the
+// carried norms are applied in FP64. g then carries ~1e-7 of |a| |b| and c
+// and s FP32 rounding, so each rotation is unitary to ~1e-7 and leaves
+// ~1e-7 of the coupling: the column norms (the singular values) are
+// accurate to ~1e-6 relative, and the columns span the dominant subspaces
+// to within ~1e-6 of the dropped singular values. Only a caller that
+// projects onto the subspace exactly (pq_svd in the rounding) uses it; the
+// FP64 form keeps the exact-unitarity guarantee for the rest.
 template <bool F32ROT>
 static __device__ int hestenes_t(cd* L, int ld, int p, int m, int max_sweeps, int* sh_flag, double big2) {
   const int lane = lane_id(), warp = warp_id();
@@ -377,32 +379,38 @@ static __device__ int hestenes_t(cd* L, int ld, int p, int m, int max_sweeps, in
         }
         cd* ca = L + (size_t)a * ld;
         cd* cb = L + (size_t)b * ld;
-        double gx = 0.0, gy = 0.0;
-        if (live)
-          for (int i = sub; i < p; i += G) {
-            const cd x = ca[i], y = cb[i];
-            gx = fma(x.x, y.x, fma(x.y, y.y, gx));
-            gy = fma(x.x, y.y, fma(-x.y, y.x, gy));
-          }
-        for (int o = G >> 1; o > 0; o >>= 1) {
-          gx += __shfl_xor_sync(0xffffffffu, gx, o);
-          gy += __shfl_xor_sync(0xffffffffu, gy, o);
-        }
-        if (!live) continue;
-        const double al = cn2[a], be = cn2[b];
-        const double g2 = fma(gx, gx, gy * gy);
-        const double ab = al * be;
-        if (F32ROT && g2 > tol2 * ab && g2 > 1e-290) {
-          // the same formulas as below, in FP32 on data scaled so that
-          // max(al, be) lies in [1, 2); both are >= 0, so their bit patterns
-          // order like their values
+        if constexpr (F32ROT) {
+          // a^H b in FP32 on the pair's data scaled by 2^(1023 - es) >= 1 /
+          // (larger column norm), entries converted by integer operations:
+          // its error, ~1e-7 of |a| |b|, is the level the FP32 rotation
+          // parameters leave anyway, and the stop rule asks only for 1e-2.
+          // The tests below compare the squares on the scale 2^(2 (1023 - es)).
+          const double al = live ? cn2[a] : 0.0, be = live ? cn2[b] : 0.0;
           const long long kb = max(__double_as_longlong(al), __double_as_longlong(be));
-          const int eb = (int)(kb >> 52);
-          const float alf = scaled_f32(al, eb), bef = scaled_f32(be, eb);
-          const float gxf = scaled_f32(gx, eb), gyf = scaled_f32(gy, eb);
-          const float Df = bef - alf;
+          // norms outside about 1e+-130 would leave the float range: such a
+          // pair is not rotated (its scaled entries read as zero)
+          const int es = min(max(sqrt_exp_bound(__longlong_as_double(kb)), 600), 1440);
+          float gxf = 0.0f, gyf = 0.0f;
+          if (live)
+            for (int i = sub; i < p; i += G) {
+              const cd x = ca[i], y = cb[i];
+              const float xr = scaled_f32(x.x, es), xi = scaled_f32(x.y, es);
+              const float yr = scaled_f32(y.x, es), yi = scaled_f32(y.y, es);
+              gxf = fmaf(xr, yr, fmaf(xi, yi, gxf));
+              gyf = fmaf(xr, yi, fmaf(-xi, yr, gyf));
+            }
+          for (int o = G >> 1; o > 0; o >>= 1) {
+            gxf += __shfl_xor_sync(0xffffffffu, gxf, o);
+            gyf += __shfl_xor_sync(0xffffffffu, gyf, o);
+          }
+          if (!live) continue;
+          const int e2 = 2 * es - 1023;
+          const float alf = scaled_f32(al, e2), bef = scaled_f32(be, e2);
           const float G2f = fmaf(gxf, gxf, gyf * gyf);
-          if (G2f > 0.0f) {
+          const float abf = alf * bef;
+          if (G2f > (float)tol2 * abf && G2f > 0.0f) {
+            // the rotation of the FP64 branch below, in FP32
+            const float Df = bef - alf;
             const float uf = fmaf(Df, Df, 4.0f * G2f);
             const float rf = uf * rsqrtf(uf);
             const float hf = fabsf(Df) + rf;
@@ -410,7 +418,62 @@ static __device__ int hestenes_t(cd* L, int ld, int p, int m, int max_sweeps, in
             const float cwf = copysignf(2.0f * qf, Df);
             const double c = f32_unscaled(hf * qf, 1023);
             const double spx = f32_unscaled(cwf * gxf, 1023), spy = f32_unscaled(-cwf * gyf, 1023);
-            const double dn = f32_unscaled(copysignf(4.0f * G2f * rf * qf * qf, Df), eb);
+            const double dn = f32_unscaled(copysignf(4.0f * G2f * rf * qf * qf, Df), e2);
+            for (int i = sub; i < p; i += G) {
+              const cd x = ca[i], y = cb[i];
+              ca[i] = mkc(fma(c, x.x, -fma(spx, y.x, -spy * y.y)), fma(c, x.y, -fma(spx, y.y, spy * y.x)));
+              cb[i] = mkc(fma(c, y.x, fma(spx, x.x, spy * x.y)), fma(c, y.y, fma(spx, x.y, -spy * x.x)));
+            }
+            if (sub == 0) {
+              cn2[a] = fmax(al - dn, 0.0);
+              cn2[b] = be + dn;
+              atomicOr(sh_flag, (G2f > (float)big2 * abf) ? 7 : (G2f > 1e-20f * abf) ? 3 : 1);
+            }
+          }
+        } else {
+          double gx = 0.0, gy = 0.0;
+          if (live)
+            for (int i = sub; i < p; i += G) {
+              const cd x = ca[i], y = cb[i];
+              gx = fma(x.x, y.x, fma(x.y, y.y, gx));
+              gy = fma(x.x, y.y, fma(-x.y, y.x, gy));
+            }
+          for (int o = G >> 1; o > 0; o >>= 1) {
+            gx += __shfl_xor_sync(0xffffffffu, gx, o);
+            gy += __shfl_xor_sync(0xffffffffu, gy, o);
+          }
+          if (!live) continue;
+          const double al = cn2[a], be = cn2[b];
+          const double g2 = fma(gx, gx, gy * gy);
+          const double ab = al * be;
+          if (g2 > tol2 * ab && g2 > 1e-290) {
+            // t, c and sp are invariant under a common scaling of al, be, g;
+            // rescale only when the squares below could overflow
+            double D = be - al, G2 = g2, sx = gx, sy = gy;
+            const double big = fmax(al, be);
+            if (big > 1e140) {
+              const double inv = 1.0 / big;
+              D *= inv;
+              sx *= inv;
+              sy *= inv;
+              G2 = fma(sx, sx, sy * sy);
+            }
+            // Rotation with tangent t = w |g|, w = 2 sign(D) / h, where
+            // u = D^2 + 4 |g|^2, r = sqrt(u), h = |D| + r. Since
+            // 1 + w^2 |g|^2 = 2 r / h, with q = 1 / sqrt(2 r h):
+            //   c = 1 / sqrt(1 + t^2) = h q,   c w = 2 sign(D) q,
+            //   w |g|^2 = 2 sign(D) |g|^2 / h = 4 sign(D) |g|^2 r q^2,
+            // two reciprocal square roots and no division
+            const double u = fma(D, D, 4.0 * G2);
+            const double r = u * rsqrt(u);
+            const double h = fabs(D) + r;
+            const double qq = rsqrt(2.0 * r * h);
+            const double c = h * qq;
+            const double cw = copysign(2.0 * qq, D);
+            const double spx = cw * sx, spy = -cw * sy;           // sp = c w conj(g)
+            // w|g|^2 in true units (w G2 carries one factor of the scaling)
+            const double wg2 = copysign(4.0 * G2 * r * qq * qq, D);
+            const double dn = (big > 1e140) ? wg2 * big : wg2;
             for (int i = sub; i < p; i += G) {
               const cd x = ca[i], y = cb[i];
               ca[i] = mkc(fma(c, x.x, -fma(spx, y.x, -spy * y.y)), fma(c, x.y, -fma(spx, y.y, spy * y.x)));
@@ -421,44 +484,6 @@ static __device__ int hestenes_t(cd* L, int ld, int p, int m, int max_sweeps, in
               cn2[b] = be + dn;
               atomicOr(sh_flag, (g2 > big2 * ab) ? 7 : (g2 > 1e-20 * ab) ? 3 : 1);
             }
-          }
-        } else if (!F32ROT && g2 > tol2 * ab && g2 > 1e-290) {
-          // t, c and sp are invariant under a common scaling of al, be, g;
-          // rescale only when the squares below could overflow
-          double D = be - al, G2 = g2, sx = gx, sy = gy;
-          const double big = fmax(al, be);
-          if (big > 1e140) {
-            const double inv = 1.0 / big;
-            D *= inv;
-            sx *= inv;
-            sy *= inv;
-            G2 = fma(sx, sx, sy * sy);
-          }
-          // Rotation with tangent t = w |g|, w = 2 sign(D) / h, where
-          // u = D^2 + 4 |g|^2, r = sqrt(u), h = |D| + r. Since
-          // 1 + w^2 |g|^2 = 2 r / h, with q = 1 / sqrt(2 r h):
-          //   c = 1 / sqrt(1 + t^2) = h q,   c w = 2 sign(D) q,
-          //   w |g|^2 = 2 sign(D) |g|^2 / h = 4 sign(D) |g|^2 r q^2,
-          // two reciprocal square roots and no division
-          const double u = fma(D, D, 4.0 * G2);
-          const double r = u * rsqrt(u);
-          const double h = fabs(D) + r;
-          const double qq = rsqrt(2.0 * r * h);
-          const double c = h * qq;
-          const double cw = copysign(2.0 * qq, D);
-          const double spx = cw * sx, spy = -cw * sy;           // sp = c w conj(g)
-          // w|g|^2 in true units (w G2 carries one factor of the scaling)
-          const double wg2 = copysign(4.0 * G2 * r * qq * qq, D);
-          const double dn = (big > 1e140) ? wg2 * big : wg2;
-          for (int i = sub; i < p; i += G) {
-            const cd x = ca[i], y = cb[i];
-            ca[i] = mkc(fma(c, x.x, -fma(spx, y.x, -spy * y.y)), fma(c, x.y, -fma(spx, y.y, spy * y.x)));
-            cb[i] = mkc(fma(c, y.x, fma(spx, x.x, spy * x.y)), fma(c, y.y, fma(spx, x.y, -spy * x.x)));
-          }
-          if (sub == 0) {
-            cn2[a] = fmax(al - dn, 0.0);
-            cn2[b] = be + dn;
-            atomicOr(sh_flag, (g2 > big2 * ab) ? 7 : (g2 > 1e-20 * ab) ? 3 : 1);
           }
         }
       }
