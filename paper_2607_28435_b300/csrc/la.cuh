@@ -321,10 +321,10 @@ __device__ __forceinline__ int jacobi_group_log2(int npair, int p) {
   return best;
 }
 
-// F32ROT: the pair's dot product a^H b, the rotation tests and the rotation
-// parameters in FP32, on the pair's data scaled by a power of two (integer
-// bit operations: no FP64 instruction); only the rotation itself and the
-// carried norms are applied in FP64. g then carries ~1e-7 of |a| |b| and c
+// F32ROT: the column norms, the pair's dot product a^H b, the rotation tests
+// and the rotation parameters in FP32, on data scaled by powers of two
+// (integer bit operations: no FP64 instruction); only the rotation itself
+// is applied in FP64. g then carries ~1e-7 of |a| |b| and c
 // and s FP32 rounding, so each rotation is unitary to ~1e-7 and leaves
 // ~1e-7 of the coupling: the column norms (the singular values) are
 // accurate to ~1e-6 relative, and the columns span the dominant subspaces
@@ -356,9 +356,27 @@ static __device__ int hestenes_t(cd* L, int ld, int p, int m, int max_sweeps, in
     if (threadIdx.x == 0) *sh_flag = 0;
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
       const cd* col = L + (size_t)c * ld;
-      double s = 0.0;
-      for (int i = 0; i < p; ++i) s = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, s));
-      cn2[c] = s;
+      if constexpr (F32ROT) {
+        // to FP32 accuracy, which is all the FP32 rotation parameters use:
+        // the entries scaled by 2^(1023 - ec), ec the largest exponent among
+        // them, summed in FP32 (no FP64 instruction)
+        int ec = 0;
+        for (int i = 0; i < p; ++i) {
+          ec = max(ec, (int)((__double_as_longlong(col[i].x) >> 52) & 0x7ff));
+          ec = max(ec, (int)((__double_as_longlong(col[i].y) >> 52) & 0x7ff));
+        }
+        ec = min(max(ec + 1, 600), 1440);
+        float sf = 0.0f;
+        for (int i = 0; i < p; ++i) {
+          const float xr = scaled_f32(col[i].x, ec), xi = scaled_f32(col[i].y, ec);
+          sf = fmaf(xr, xr, fmaf(xi, xi, sf));
+        }
+        cn2[c] = f32_unscaled(sf, 2 * ec - 1023);
+      } else {
+        double s = 0.0;
+        for (int i = 0; i < p; ++i) s = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, s));
+        cn2[c] = s;
+      }
     }
     __syncthreads();
     for (int t = 0; t < mp - 1; ++t) {
@@ -418,15 +436,16 @@ static __device__ int hestenes_t(cd* L, int ld, int p, int m, int max_sweeps, in
             const float cwf = copysignf(2.0f * qf, Df);
             const double c = f32_unscaled(hf * qf, 1023);
             const double spx = f32_unscaled(cwf * gxf, 1023), spy = f32_unscaled(-cwf * gyf, 1023);
-            const double dn = f32_unscaled(copysignf(4.0f * G2f * rf * qf * qf, Df), e2);
+            // the carried norms, alpha - w|g|^2 and beta + w|g|^2, on the same scale
+            const float dnf = copysignf(4.0f * G2f * rf * qf * qf, Df);
             for (int i = sub; i < p; i += G) {
               const cd x = ca[i], y = cb[i];
               ca[i] = mkc(fma(c, x.x, -fma(spx, y.x, -spy * y.y)), fma(c, x.y, -fma(spx, y.y, spy * y.x)));
               cb[i] = mkc(fma(c, y.x, fma(spx, x.x, spy * x.y)), fma(c, y.y, fma(spx, x.y, -spy * x.x)));
             }
             if (sub == 0) {
-              cn2[a] = fmax(al - dn, 0.0);
-              cn2[b] = be + dn;
+              cn2[a] = f32_unscaled(fmaxf(alf - dnf, 0.0f), e2);
+              cn2[b] = f32_unscaled(bef + dnf, e2);
               atomicOr(sh_flag, (G2f > (float)big2 * abf) ? 7 : (G2f > 1e-20f * abf) ? 3 : 1);
             }
           }
