@@ -352,11 +352,29 @@ static __device__ int hestenes_t(cd* L, int ld, int p, int m, int max_sweeps, in
   // beta + w|g|^2 (so the rounds only need a^H b); the singular values the
   // callers use come from the columns themselves after the last sweep
   __shared__ double cn2[LA_MAXP];
+  // F32ROT: column c is kept as dsc[c] times the stored column, so that a
+  // rotation's factor c folds into dsc and the stored update takes two
+  // complex FMAs per entry; dsc is folded back before returning
+  __shared__ float dsc[LA_MAXP];
+  if constexpr (F32ROT) {
+    for (int c = threadIdx.x; c < m; c += blockDim.x) dsc[c] = 1.0f;
+    __syncthreads();
+  }
+  int ret = -1;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) *sh_flag = 0;
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
-      const cd* col = L + (size_t)c * ld;
+      cd* col = L + (size_t)c * ld;
       if constexpr (F32ROT) {
+        // a scale below 2^-20 is folded into the column (rare: many large
+        // rotations of one column)
+        float dc = dsc[c];
+        if (dc < 0x1p-20f) {
+          const double d = f32_unscaled(dc, 1023);
+          for (int i = 0; i < p; ++i) col[i] = cscale(col[i], d);
+          dc = 1.0f;
+          dsc[c] = dc;
+        }
         // to FP32 accuracy, which is all the FP32 rotation parameters use:
         // the entries scaled by 2^(1023 - ec), ec the largest exponent among
         // them, summed in FP32 (no FP64 instruction)
@@ -371,7 +389,7 @@ static __device__ int hestenes_t(cd* L, int ld, int p, int m, int max_sweeps, in
           const float xr = scaled_f32(col[i].x, ec), xi = scaled_f32(col[i].y, ec);
           sf = fmaf(xr, xr, fmaf(xi, xi, sf));
         }
-        cn2[c] = f32_unscaled(sf, 2 * ec - 1023);
+        cn2[c] = f32_unscaled(sf * dc * dc, 2 * ec - 1023);
       } else {
         double s = 0.0;
         for (int i = 0; i < p; ++i) s = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, s));
@@ -404,10 +422,14 @@ static __device__ int hestenes_t(cd* L, int ld, int p, int m, int max_sweeps, in
           // parameters leave anyway, and the stop rule asks only for 1e-2.
           // The tests below compare the squares on the scale 2^(2 (1023 - es)).
           const double al = live ? cn2[a] : 0.0, be = live ? cn2[b] : 0.0;
-          const long long kb = max(__double_as_longlong(al), __double_as_longlong(be));
-          // norms outside about 1e+-130 would leave the float range: such a
-          // pair is not rotated (its scaled entries read as zero)
-          const int es = min(max(sqrt_exp_bound(__longlong_as_double(kb)), 600), 1440);
+          const float da = live ? dsc[a] : 1.0f, db = live ? dsc[b] : 1.0f;
+          // the stored entries are bounded by 2^(es - 1023): the true norms'
+          // bounds over the scales (whose exponents are <= 0). Norms outside
+          // about 1e+-130 would leave the float range: such a pair is not
+          // rotated (its scaled entries read as zero)
+          const int eda = ((__float_as_int(da) >> 23) & 0xff) - 127;
+          const int edb = ((__float_as_int(db) >> 23) & 0xff) - 127;
+          const int es = min(max(max(sqrt_exp_bound(al) - eda, sqrt_exp_bound(be) - edb), 600), 1440);
           float gxf = 0.0f, gyf = 0.0f;
           if (live)
             for (int i = sub; i < p; i += G) {
@@ -422,6 +444,9 @@ static __device__ int hestenes_t(cd* L, int ld, int p, int m, int max_sweeps, in
             gyf += __shfl_xor_sync(0xffffffffu, gyf, o);
           }
           if (!live) continue;
+          // g of the true columns, on the scale 2^(2 (1023 - es))
+          gxf *= da * db;
+          gyf *= da * db;
           const int e2 = 2 * es - 1023;
           const float alf = scaled_f32(al, e2), bef = scaled_f32(be, e2);
           const float G2f = fmaf(gxf, gxf, gyf * gyf);
@@ -433,19 +458,28 @@ static __device__ int hestenes_t(cd* L, int ld, int p, int m, int max_sweeps, in
             const float rf = uf * rsqrtf(uf);
             const float hf = fabsf(Df) + rf;
             const float qf = rsqrtf(2.0f * rf * hf);
-            const float cwf = copysignf(2.0f * qf, Df);
-            const double c = f32_unscaled(hf * qf, 1023);
-            const double spx = f32_unscaled(cwf * gxf, 1023), spy = f32_unscaled(-cwf * gyf, 1023);
+            // a' = c (a - t b), b' = c (b + conj(t) a) with t = w conj(g),
+            // w = 2 sign(D) / h = 4 sign(D) r q^2; on the stored columns
+            // a~' = a~ - t1 b~, b~' = b~ + t2 a~ with t1 = t db / da,
+            // t2 = conj(t) da / db, and the factor c moves into the scales
+            const float cf = hf * qf;
+            const float wf = copysignf(4.0f * rf * qf * qf, Df);
+            const float txf = wf * gxf, tyf = -wf * gyf;
+            const float r1 = db / da, r2 = da / db;
+            const double t1x = f32_unscaled(txf * r1, 1023), t1y = f32_unscaled(tyf * r1, 1023);
+            const double t2x = f32_unscaled(txf * r2, 1023), t2y = f32_unscaled(-tyf * r2, 1023);
             // the carried norms, alpha - w|g|^2 and beta + w|g|^2, on the same scale
             const float dnf = copysignf(4.0f * G2f * rf * qf * qf, Df);
             for (int i = sub; i < p; i += G) {
               const cd x = ca[i], y = cb[i];
-              ca[i] = mkc(fma(c, x.x, -fma(spx, y.x, -spy * y.y)), fma(c, x.y, -fma(spx, y.y, spy * y.x)));
-              cb[i] = mkc(fma(c, y.x, fma(spx, x.x, spy * x.y)), fma(c, y.y, fma(spx, x.y, -spy * x.x)));
+              ca[i] = mkc(fma(-t1x, y.x, fma(t1y, y.y, x.x)), fma(-t1x, y.y, fma(-t1y, y.x, x.y)));
+              cb[i] = mkc(fma(t2x, x.x, fma(-t2y, x.y, y.x)), fma(t2x, x.y, fma(t2y, x.x, y.y)));
             }
             if (sub == 0) {
               cn2[a] = f32_unscaled(fmaxf(alf - dnf, 0.0f), e2);
               cn2[b] = f32_unscaled(bef + dnf, e2);
+              dsc[a] = da * cf;
+              dsc[b] = db * cf;
               atomicOr(sh_flag, (G2f > (float)big2 * abf) ? 7 : (G2f > 1e-20f * abf) ? 3 : 1);
             }
           }
@@ -516,10 +550,24 @@ static __device__ int hestenes_t(cd* L, int ld, int p, int m, int max_sweeps, in
     // rotations are unitary, so A V = [columns] stays exact whatever is left;
     // the residual only makes the kept columns orthogonal to ~1e-8, and their
     // norms (the singular values used for truncation) accurate to ~1e-16
-    if (!(any & 4)) return sweep + 1;
-    if (sweep == max_sweeps - 1) return (any & 2) ? -1 : max_sweeps;
+    if (!(any & 4)) {
+      ret = sweep + 1;
+      break;
+    }
+    if (sweep == max_sweeps - 1) {
+      ret = (any & 2) ? -1 : max_sweeps;
+      break;
+    }
   }
-  return -1;
+  if constexpr (F32ROT) {
+    // the true columns: each stored column times its scale
+    for (int idx = threadIdx.x; idx < m * p; idx += blockDim.x) {
+      const int c = idx / p, i = idx - c * p;
+      L[(size_t)c * ld + i] = cscale(L[(size_t)c * ld + i], f32_unscaled(dsc[c], 1023));
+    }
+    __syncthreads();
+  }
+  return ret;
 }
 
 static __device__ int hestenes(cd* L, int ld, int p, int m, int max_sweeps, int* sh_flag, double big2 = 1e-8) {
