@@ -711,7 +711,7 @@ __global__ void k_mpo_interp(int n, int P, cd* W, int core_stride,
 // budget, so the error bound is that of the plain truncated SVD and the rank
 // exceeds the plain SVD's only where its tail lies within delta^2 / 64 of
 // delta^2.
-__global__ void __launch_bounds__(256, 4) k_tt_round(const int* list, int count, int* counter, const int* n_arr, int d,
+__global__ void __maxnreg__(72) k_tt_round(const int* list, int count, int* counter, const int* n_arr, int d,
                            int left_orth,
                            const double* tol_arr, const int* maxrank_arr,
                            cd* tt, const long long* tt_off, int core_stride,
