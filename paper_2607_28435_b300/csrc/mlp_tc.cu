@@ -80,7 +80,9 @@ __device__ __forceinline__ float rcp_approx(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ float gelu_f(float z) {
+// The scalar form, which gelu2 below evaluates on pairs (kept as its
+// specification; the kernels call gelu2).
+[[maybe_unused]] __device__ __forceinline__ float gelu_f(float z) {
   // with a = |z|: 1 + p x = 1 + (p / sqrt 2) a and exp(-x^2) = 2^(-a^2 log2(e) / 2);
   // the coefficients carry the factor 1/2 of Q
   const float a = fabsf(z);
